@@ -1,0 +1,405 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these re-types an oracle formula: each compares the oracle with a published value, a
+hand-evaluated closed form, a library routine, an invariant (symmetry, positive
+semi-definiteness, compact support), brute force, or finite differences.  A dropped term, a
+wrong sign or index, or a transposed operand anywhere in the oracle fails one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2512_06143_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _hyper(orc, w):
+    return orc.Hyper(**w["hyper"])
+
+
+# ---------------------------------------------------------------------------------------
+# SplitMix64 probes (published reference outputs)
+# ---------------------------------------------------------------------------------------
+def test_splitmix64_published_vectors(orc):
+    G = 0x9E3779B97F4A7C15
+    M = 2 ** 64 - 1
+    rows = [l.split() for l in open(os.path.join(GOLD, "splitmix64.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 2
+    for r in rows:
+        s0 = int(r[0])
+        for k, v in enumerate(r[1:]):
+            assert orc.splitmix64((s0 + k * G) & M) == int(v)
+
+
+def test_rademacher_probes_definition(orc):
+    # z[i, s-1] = 1 - 2 * (top bit of splitmix64(seed ^ (s << 32 | i))); values +-1 only,
+    # balanced, independent of n (indexed by the original point index).
+    z = orc.probes(1000, 8, 12345)
+    assert set(np.unique(z)) == {-1.0, 1.0}
+    assert abs(z.mean()) < 0.05
+    z2 = orc.probes(500, 8, 12345)
+    assert np.array_equal(z[:500], z2)
+    seed, s, i = 12345, 3, 17
+    top = orc.splitmix64(seed ^ ((s << 32) + i)) >> 63
+    assert z[i, s - 1] == (1.0 - 2.0 * top)
+    assert not np.array_equal(orc.probes(100, 4, 1), orc.probes(100, 4, 2))
+
+
+# ---------------------------------------------------------------------------------------
+# Wendland tapers: eq. (wendland) and the C2 reading
+# ---------------------------------------------------------------------------------------
+def test_wendland_hand_values(orc):
+    rows = [l.split() for l in open(os.path.join(GOLD, "wendland_values.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) >= 9
+    for kind, d, t, num, den in rows:
+        got = float(orc.phi(int(kind), int(d), float(t)))
+        assert got == pytest.approx(int(num) / int(den), rel=1e-15, abs=0), (kind, d, t)
+
+
+@pytest.mark.parametrize("kind,d", [(0, 1), (0, 2), (0, 3), (0, 4), (1, 1), (1, 2), (1, 3)])
+def test_wendland_support_and_endpoints(orc, kind, d):
+    assert float(orc.phi(kind, d, 0.0)) == 1.0
+    for t in [1.0, 1.0 + 1e-12, 1.5, 10.0]:
+        assert float(orc.phi(kind, d, t)) == 0.0
+        assert float(orc.dphi(kind, d, t)) == 0.0
+    # order of vanishing at t = 1: C2 (d<=3) ~ 5 e^4, C2 (d=4) ~ 6 e^5, eq. (wendland) ~ 66 e^8
+    e = 1e-3
+    if kind == 1:
+        lead, p = 66.0, 8
+    elif d <= 3:
+        lead, p = 5.0, 4
+    else:
+        lead, p = 6.0, 5
+    assert float(orc.phi(kind, d, 1 - e)) / e ** p == pytest.approx(lead, rel=0.02)
+    # phi decreases on [0, 1)
+    ts = np.linspace(0, 0.999, 400)
+    v = orc.phi(kind, d, ts)
+    assert np.all(np.diff(v) < 0)
+
+
+@pytest.mark.parametrize("kind,d", [(0, 2), (0, 4), (1, 3)])
+def test_wendland_derivative_matches_finite_differences(orc, kind, d):
+    h = 1e-6
+    for t in np.linspace(0.01, 0.99, 37):
+        fd = (float(orc.phi(kind, d, t + h)) - float(orc.phi(kind, d, t - h))) / (2 * h)
+        assert float(orc.dphi(kind, d, t)) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    assert float(orc.dphi(kind, d, 0.0)) == 0.0   # even function of |x - x'|: smooth at 0
+
+
+@pytest.mark.parametrize("kind,d", [(0, 1), (0, 2), (0, 3), (0, 4), (1, 2), (1, 3)])
+def test_wendland_gram_is_positive_semidefinite(orc, kind, d):
+    rng = np.random.default_rng(d + 10 * kind)
+    X = rng.random((150, d))
+    r = 0.6
+    D = np.sqrt(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)) / r
+    G = orc.phi(kind, d, D)
+    w = np.linalg.eigvalsh(G)
+    assert w.min() >= -1e-12 * w.max()
+
+
+# ---------------------------------------------------------------------------------------
+# Bump functions: eq. (bump)
+# ---------------------------------------------------------------------------------------
+def _bump_hyper(orc, d=3, beta=1.3):
+    return orc.Hyper(d=d, r=0.1, sigma2=1e-3, centers=np.array([[0.2, 0.4, 0.6][:d], [0.5] * d]),
+                     radii=np.array([0.3, 0.45]), amps=np.array([1.7, 0.6]), beta=beta)
+
+
+def test_bump_closed_forms(orc):
+    h = _bump_hyper(orc)
+    c0 = np.array([0.2, 0.4, 0.6])
+    b = orc.bumps(h, c0)
+    assert b[0] == pytest.approx(1.7, rel=1e-15)                 # b(c) = a
+    # s = 1/2  ->  b = a exp(beta (1 - 2)) = a e^{-beta}
+    x = c0 + np.array([0.3 * math.sqrt(0.5), 0.0, 0.0])
+    assert orc.bumps(h, x)[0] == pytest.approx(1.7 * math.exp(-1.3), rel=1e-13)
+    # zero on and beyond the support boundary s >= 1
+    assert orc.bumps(h, c0 + np.array([0.3, 0.0, 0.0]))[0] == 0.0
+    assert orc.bumps(h, c0 + np.array([0.0, 0.31, 0.0]))[0] == 0.0
+    # smooth decay to 0 as s -> 1
+    near = orc.bumps(h, c0 + np.array([0.3 * math.sqrt(1 - 1e-3), 0, 0]))[0]
+    assert 0.0 < near < 1e-300 or near < 1e-200
+
+
+def test_bump_derivatives_match_finite_differences(orc):
+    h = _bump_hyper(orc)
+    rng = np.random.default_rng(3)
+    hs = 1e-6
+    for _ in range(12):
+        x = np.array([0.2, 0.4, 0.6]) + rng.normal(0, 0.1, 3)
+        b, db = orc.bumps(h, x, with_grad=True)
+        for l in range(h.L):
+            for p in range(h.d + 2):
+                def val(delta):
+                    c = h.centers.copy()
+                    rr = h.radii.copy()
+                    aa = h.amps.copy()
+                    if p < h.d:
+                        c[l, p] += delta
+                    elif p == h.d:
+                        rr[l] += delta
+                    else:
+                        aa[l] += delta
+                    hh = orc.Hyper(d=h.d, r=h.r, sigma2=h.sigma2, centers=c, radii=rr, amps=aa, beta=h.beta)
+                    return orc.bumps(hh, x)[l]
+                fd = (val(hs) - val(-hs)) / (2 * hs)
+                assert db[l, p] == pytest.approx(fd, rel=1e-5, abs=1e-9), (l, p)
+
+
+# ---------------------------------------------------------------------------------------
+# Kernel: product of a Wendland taper and the rank-L bump kernel (Sec. 3.1, 3.3, Thm 1)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("d,kind", [(1, 0), (2, 0), (3, 1), (4, 0)])
+def test_kernel_symmetric_psd_compact(orc, d, kind):
+    w = W.random_small(5 + d, 260, d, L=3, kind=kind, r=0.35)
+    h = _hyper(orc, w)
+    A = orc.dense_A(w["X"], h)
+    K = A - h.sigma2 * np.eye(A.shape[0])
+    assert np.array_equal(K, K.T)                                   # symmetric, bit for bit
+    ev = np.linalg.eigvalsh(K)
+    assert ev.min() >= -1e-11 * max(ev.max(), 1.0)                  # Theorem 1: PSD
+    X = w["X"]
+    D = np.sqrt(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))
+    assert np.all(K[D > h.r * (1 + 1e-9)] == 0.0)                   # zero beyond the support
+
+
+def test_stationary_special_case(orc):
+    # L = 1, beta = 0, rho larger than the data's diameter, amplitude a:
+    # the bump factor is the constant a^2 and K is a plain Wendland taper a^2 phi(|x-x'|/r).
+    rng = np.random.default_rng(11)
+    X = rng.random((120, 2))
+    a = 1.7
+    h = orc.Hyper(d=2, r=0.3, sigma2=0.0, centers=np.array([[0.5, 0.5]]), radii=np.array([10.0]),
+                  amps=np.array([a]), beta=0.0)
+    D = np.sqrt(((X[:, None, :] - X[None, :, :]) ** 2).sum(-1))
+    K = orc.dense_A(X, h)
+    np.testing.assert_allclose(K, a * a * orc.phi(0, 2, D / 0.3), rtol=1e-14, atol=1e-15)
+    # all amplitudes 0 with w0 = 1 gives the taper itself
+    h0 = orc.Hyper(d=2, r=0.3, sigma2=0.0, centers=np.array([[0.5, 0.5]]), radii=np.array([0.2]),
+                   amps=np.array([0.0]), w0=1.0)
+    np.testing.assert_allclose(orc.dense_A(X, h0), orc.phi(0, 2, D / 0.3), rtol=1e-14, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------
+# Assembly: structural pattern, strict support, brute force == tree candidates
+# ---------------------------------------------------------------------------------------
+def test_pattern_on_exact_grid(orc):
+    # 2-D grid with spacing 1/8 and r = 1/4: every squared distance is an exact binary
+    # fraction, so the strict test (d2 < r^2) excludes the pairs at distance exactly 1/4.
+    g = np.arange(6) / 8.0
+    X = np.array([[a, b] for a in g for b in g])
+    h = orc.Hyper(d=2, r=0.25, sigma2=1e-2, centers=np.array([[0.3, 0.3]]), radii=np.array([0.5]),
+                  amps=np.array([1.0]))
+    csr = orc.assemble(X, h, "brute")
+    # neighbours of an interior point (i, j) with (di^2 + dj^2) < 4: offsets with
+    # |di|,|dj| <= 1, plus (+-1, 0)... counted by hand: (0,0), 4 x (1,0), 4 x (1,1)  -> 9;
+    # (2,0) is at distance exactly 1/4 -> excluded.
+    counts = np.diff(csr.rowptr).reshape(6, 6)
+    assert counts[2, 2] == 9 and counts[3, 3] == 9
+    assert counts[0, 0] == 4                      # corner: itself, (1,0), (0,1), (1,1)
+    assert counts[0, 2] == 6                      # edge
+    assert csr.nnz == 16 * 9 + 4 * 4 + 16 * 6
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_pattern_against_library_distances(orc, d):
+    from scipy.spatial.distance import cdist
+    w = W.random_small(20 + d, 900, d, clustered=(d == 3))
+    h = _hyper(orc, w)
+    csr = orc.assemble(w["X"], h, "brute")
+    n = w["X"].shape[0]
+    Dl = cdist(w["X"], w["X"])
+    M = np.zeros((n, n), bool)
+    rows = np.repeat(np.arange(n), np.diff(csr.rowptr))
+    M[rows, csr.col] = True
+    assert np.all(np.diag(M))
+    assert np.array_equal(M, M.T)
+    off = ~np.eye(n, dtype=bool)
+    assert np.all(M[(Dl < h.r * (1 - 1e-12)) & off])
+    assert not np.any(M[(Dl > h.r * (1 + 1e-12)) & off])
+    # columns strictly ascending within each row
+    for i in range(0, n, 37):
+        c = csr.col[csr.rowptr[i]:csr.rowptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_tree_assembly_equals_brute_force(orc, d):
+    w = W.random_small(40 + d, 3000, d, clustered=True)
+    h = _hyper(orc, w)
+    a = orc.assemble(w["X"], h, "brute")
+    b = orc.assemble(w["X"], h, "tree")
+    assert np.array_equal(a.rowptr, b.rowptr)
+    assert np.array_equal(a.col, b.col)
+    assert np.array_equal(a.val, b.val)
+    rows = [0, 17, 1234, 2999]
+    for i, (c, v) in zip(rows, orc.rows_brute(w["X"], h, rows)):
+        assert np.array_equal(c, a.col[a.rowptr[i]:a.rowptr[i + 1]])
+        assert np.array_equal(v, a.val[a.rowptr[i]:a.rowptr[i + 1]])
+
+
+def test_duplicate_points_and_values(orc):
+    rng = np.random.default_rng(2)
+    X = rng.random((50, 2))
+    X[10] = X[3]
+    w = dict(X=X)
+    h = orc.Hyper(d=2, r=0.2, sigma2=1e-3, centers=np.array([[0.5, 0.5]]), radii=np.array([0.6]),
+                  amps=np.array([1.0]))
+    A = orc.dense_A(X, h)
+    assert A[3, 10] == pytest.approx(A[3, 3] - 1e-3, rel=1e-12) and A[10, 3] == A[3, 10]
+    csr = orc.assemble(X, h, "brute")
+    Ad = np.zeros_like(A)
+    rows = np.repeat(np.arange(50), np.diff(csr.rowptr))
+    Ad[rows, csr.col] = csr.val
+    assert np.array_equal(Ad, A)
+    # values: K_ij = phi(|x_i - x_j| / r) * (sum_l b_l(x_i) b_l(x_j)) from the scalar pieces
+    i, j = 3, int(csr.col[csr.rowptr[3] + 1])
+    dist = float(np.sqrt(((X[i] - X[j]) ** 2).sum()))
+    ref = float(orc.phi(0, 2, dist / 0.2)) * float(orc.bumps(h, X[i]) @ orc.bumps(h, X[j]))
+    assert A[i, j] == pytest.approx(ref, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------------------
+# LML (Sec. 3): exact dense path against the library's Gaussian log-density
+# ---------------------------------------------------------------------------------------
+def test_lml_exact_equals_gaussian_logpdf(orc):
+    from scipy.stats import multivariate_normal
+    w = W.random_small(7, 400, 2, L=2, sigma2=1e-2)
+    h = _hyper(orc, w)
+    e = orc.lml_exact(w["X"], w["y"], h)
+    ref = multivariate_normal(mean=np.zeros(400), cov=e["A"], allow_singular=False).logpdf(w["y"])
+    assert e["lml"] == pytest.approx(ref, rel=1e-11)
+    sign, ld = np.linalg.slogdet(e["A"])
+    assert sign == 1.0 and e["logdet"] == pytest.approx(ld, rel=1e-12)
+    assert np.linalg.norm(e["A"] @ e["a"] - w["y"]) <= 1e-10 * np.linalg.norm(w["y"])
+
+
+# ---------------------------------------------------------------------------------------
+# Krylov pieces
+# ---------------------------------------------------------------------------------------
+def test_cg_solves_and_matches_library(orc):
+    w = W.random_small(8, 800, 3, L=3, sigma2=1e-2)
+    h = _hyper(orc, w)
+    csr = orc.assemble(w["X"], h, "brute")
+    s = 1 / np.sqrt(csr.diag())
+    Ah = csr.scaled(s)
+    rng = np.random.default_rng(0)
+    B = rng.normal(size=(800, 3))
+    Xs, steps, al, be, st = orc.cg(Ah, B, tol=1e-12, kmax=5)
+    dense = np.zeros((800, 800))
+    rows = np.repeat(np.arange(800), np.diff(Ah.rowptr))
+    dense[rows, Ah.col] = Ah.val
+    ref = np.linalg.solve(dense, B)
+    np.testing.assert_allclose(Xs, ref, rtol=1e-8, atol=1e-9 * np.abs(ref).max())
+    assert st == 0 and np.all(steps > 0)
+
+
+def test_cg_lanczos_relation_matches_explicit_lanczos(orc):
+    # Both produce the Lanczos tridiagonal of Ah for q1 = z/|z| (exact arithmetic identity);
+    # in FP64 the leading entries agree to rounding.
+    w = W.random_small(9, 1500, 2, L=3, sigma2=1e-2)
+    h = _hyper(orc, w)
+    csr = orc.assemble(w["X"], h, "brute")
+    Ah = csr.scaled(1 / np.sqrt(csr.diag()))
+    z = orc.probes(1500, 2, 5)
+    _, _, al, be, _ = orc.cg(Ah, z, tol=0.0, maxit=12, kmax=12)
+    T = orc.lanczos(Ah, z / math.sqrt(1500), 12)
+    for c in range(2):
+        dg, off = orc.tridiag_from_cg(al[c], be[c])
+        np.testing.assert_allclose(dg, T[c][0], rtol=1e-9)
+        np.testing.assert_allclose(off, T[c][1], rtol=1e-9)
+
+
+def _block_matrix(orc, nb, blocks):
+    # block-diagonal CSR with the same small SPD block repeated
+    bs = blocks.shape[0]
+    n = nb * bs
+    rowptr = np.arange(n + 1, dtype=np.int64) * bs
+    col = np.concatenate([np.tile(np.arange(bs), bs) + b * bs for b in range(nb)]).astype(np.int32)
+    val = np.tile(blocks.ravel(), nb).astype(np.float64)
+    return orc.CSR(n, rowptr, col, val), n
+
+
+def test_slq_exact_with_few_distinct_eigenvalues(orc):
+    # 2x2 blocks [[2,1],[1,2]] have eigenvalues {1, 3}: Lanczos terminates after 2 steps and
+    # the Gauss quadrature is exact: q^T log(M) q for every start vector q.
+    M, n = _block_matrix(orc, 300, np.array([[2.0, 1.0], [1.0, 2.0]]))
+    z = orc.probes(n, 3, 9)
+    T = orc.lanczos(M, z / math.sqrt(n), 50)
+    lam, V = np.linalg.eigh(np.array([[2.0, 1.0], [1.0, 2.0]]))
+    logB = V @ np.diag(np.log(lam)) @ V.T
+    for c in range(3):
+        assert len(T[c][0]) <= 3
+        q = z[:, c].reshape(-1, 2)
+        exact = float(np.einsum("bi,ij,bj->", q, logB, q))
+        assert n * orc.gauss_quadrature_log(*T[c]) / n == pytest.approx(exact / n, rel=1e-10)
+    # and on a diagonal matrix with 4 distinct values
+    dvals = np.tile([0.5, 1.0, 2.0, 7.0], 250)
+    D = orc.CSR(1000, np.arange(1001, dtype=np.int64), np.arange(1000, dtype=np.int32), dvals)
+    zz = orc.probes(1000, 1, 4)[:, 0]
+    Td = orc.lanczos(D, zz[:, None] / math.sqrt(1000), 20)[0]
+    assert 1000 * orc.gauss_quadrature_log(*Td) == pytest.approx(float(np.sum(np.log(dvals))), rel=1e-10)
+
+
+def test_gauss_quadrature_matches_library_eigen(orc):
+    rng = np.random.default_rng(1)
+    dg = rng.uniform(1, 3, 30)
+    off = rng.uniform(0.1, 0.5, 29)
+    T = np.diag(dg) + np.diag(off, 1) + np.diag(off, -1)
+    from scipy.linalg import logm
+    assert orc.gauss_quadrature_log(dg, off) == pytest.approx(float(np.real(logm(T))[0, 0]), rel=1e-10)
+
+
+def test_slq_logdet_close_to_exact(orc):
+    w = W.random_small(12, 2000, 2, L=3, sigma2=1e-2)
+    h = _hyper(orc, w)
+    e = orc.lml_exact(w["X"], w["y"], h)
+    s = orc.lml_slq(w["X"], w["y"], h, m=64, k=60, seed=3, grad=False)
+    se = float(np.std(s["probe_quadrature"]) / math.sqrt(64))
+    assert abs(s["logdet"] - e["logdet"]) <= 4 * se + 1e-9 * abs(e["logdet"])
+    assert s["quad"] == pytest.approx(e["quad"], rel=1e-8)
+    assert s["relres"] <= 1e-9
+    s2 = orc.lml_slq(w["X"], w["y"], h, m=64, k=60, seed=3, grad=False, tridiag="cg")
+    assert s2["logdet"] == pytest.approx(s["logdet"], rel=1e-6)
+
+
+# ---------------------------------------------------------------------------------------
+# Gradient: exact (dense inverse) vs central finite differences; Hutchinson algebra
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("d,kind,w0", [(2, 0, 0.0), (3, 1, 0.0), (1, 0, 0.5), (4, 0, 0.0)])
+def test_exact_gradient_matches_central_fd(orc, d, kind, w0):
+    w = W.random_small(30 + d, 220, d, L=2, kind=kind, w0=w0, sigma2=5e-3, r={1: 0.05, 2: 0.2, 3: 0.35, 4: 0.5}[d])
+    h = _hyper(orc, w)
+    g = orc.grad_exact(w["X"], w["y"], h)
+    fd = orc.lml_fd_grad(w["X"], w["y"], h, step=1e-5)
+    scale = np.abs(fd).max()
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9 * max(scale, 1.0) + 1e-9)
+    assert np.abs(g).max() > 0
+
+
+def test_hutchinson_contraction_with_unit_probes_is_exact(orc):
+    # With the n unit vectors as probes (scaled by sqrt(n) to undo the 1/m average) the
+    # Hutchinson trace is exact, so the contraction equals the dense-inverse gradient.
+    w = W.random_small(33, 150, 2, L=2, sigma2=5e-3, r=0.2)
+    h = _hyper(orc, w)
+    e = orc.lml_exact(w["X"], w["y"], h)
+    n = 150
+    Ainv = np.linalg.inv(e["A"])
+    csr = orc.assemble(w["X"], h, "brute")
+    g_dense = orc.grad_contract(w["X"], h, csr, e["a"], Wd=Ainv)
+    g_hutch = orc.grad_contract(w["X"], h, csr, e["a"], U=math.sqrt(n) * Ainv, V=math.sqrt(n) * np.eye(n))
+    np.testing.assert_allclose(g_hutch, g_dense, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(g_dense, orc.grad_exact(w["X"], w["y"], h), rtol=1e-12)
+
+
+def test_hutchinson_gradient_is_unbiased(orc):
+    w = W.random_small(34, 300, 2, L=2, sigma2=5e-3, r=0.12)
+    h = _hyper(orc, w)
+    g = orc.grad_exact(w["X"], w["y"], h)
+    s = orc.lml_slq(w["X"], w["y"], h, m=1500, k=30, seed=7, lanczos_probes=1)
+    # the a^T dA a part is deterministic; the trace part's error shrinks like 1/sqrt(m)
+    err = np.abs(s["grad"] - g) / (np.abs(g) + np.abs(g).max() * 1e-3)
+    assert np.median(err) < 0.05
