@@ -1,0 +1,241 @@
+/*
+ * gp2s.h -- C ABI of the GB300 (sm_103a) engine for the exact sparse-kernel Gaussian-process
+ * log marginal likelihood of gp2Scale (Noack, Risser, Luo, Tekriwal, Pandolfi; arXiv 2512.06143).
+ *
+ * The problem (Sec. 3, Background): data X (n points in R^d) and observations y; a compactly
+ * supported non-stationary kernel
+ *     k(xi, xj) = phi(|xi - xj| / r) * ( sum_l b_l(xi) b_l(xj) + w0 )            (Sec. 3.1, 3.3)
+ * with the Wendland taper phi (eq. wendland; "C2" reading by default), bump functions
+ *     b_l(x) = a_l exp(beta (1 - 1/(1 - |x - c_l|^2 / rho_l^2)))   inside |x - c_l| < rho_l (eq. bump)
+ * and noise V = sigma2 I.  A = K + sigma2 I is sparse because phi vanishes for |xi - xj| >= r.
+ * The engine evaluates
+ *     LML = -1/2 y^T A^{-1} y - 1/2 log|A| - n/2 log(2 pi)                          (Sec. 3)
+ * and its gradient with respect to theta = [centers (L x d), radii (L), amps (L), r, sigma2].
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers (cudaMalloc / torch CUDA tensors).  Pointers whose
+ *     name says "host" are host memory.  X and y may be either: the engine asks the CUDA driver
+ *     which one it got and stages host buffers through its own device workspace.
+ *   - X is n x d, row-major, FP64.  y is n, FP64.  Hyperparameter arrays are host FP64.
+ *   - All device work is issued on the context's stream.  A call returns when its host-visible
+ *     outputs are written (it synchronises that stream once at the end, plus at most one small
+ *     device->host read per Krylov convergence check).
+ *   - Errors are returned as gp2s_status; gp2s_last_error() gives a one-line message.  Nothing
+ *     aborts, prints or traps; a CUDA error reported by the runtime is returned as GP2S_ECUDA.
+ *   - The context owns every intermediate (sorted points, cell table, CSR, Krylov vectors); it
+ *     keeps them until the next gp2s_assemble / gp2s_lml* call or gp2s_destroy.
+ *   - One context per host thread; calls on one context must not overlap.
+ */
+#ifndef GP2S_H
+#define GP2S_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GP2S_OK = 0,
+    GP2S_EINVAL = 1,      /* invalid argument (sizes, d, r <= 0, sigma2 < 0, NaN, null pointer) */
+    GP2S_ENOMEM = 2,      /* device allocation failed (or exceeded GP2S_MEM_LIMIT bytes) */
+    GP2S_ECUDA = 3,       /* a CUDA runtime call failed */
+    GP2S_ENOCONV = 4,     /* a Krylov solve hit max_iter before its tolerance */
+    GP2S_EBREAKDOWN = 5,  /* CG breakdown: p^T A p <= 0 or NaN */
+    GP2S_ETIMEOUT = 6,    /* reserved: a bounded device-side wait gave up */
+    GP2S_EOVERFLOW = 7,   /* nnz would exceed 2^31 - 1 (int32 column / row-pointer limit) */
+    GP2S_ENOTPD = 8,      /* A not positive definite (zero diagonal, Cholesky pivot <= 0) */
+    GP2S_ENOTREADY = 9    /* the call needs an earlier gp2s_assemble / gp2s_solve on this context */
+} gp2s_status;
+
+typedef enum {
+    GP2S_WENDLAND_C2 = 0,        /* (1-t)^4 (4t+1) for d <= 3, (1-t)^5 (5t+1) for d = 4 */
+    GP2S_WENDLAND_C6_PAPER = 1   /* eq. wendland: (1-t)^8 (32t^3 + 25t^2 + 8t + 1), d <= 3 */
+} gp2s_wendland;
+
+typedef enum {
+    GP2S_PREC_FP64 = 0,   /* FP64 values, FP64 SpMV/CG (the plain FP64 GPU form) */
+    GP2S_PREC_MIXED = 1   /* FP32 values + int32 indices for assembly/SpMM/CG; FP64 dots, FP64
+                             residual refinement, FP64 tridiagonal eigensolve and reductions */
+} gp2s_precision;
+
+typedef enum {
+    GP2S_LOGDET_AUTO = 0,   /* EXACT when n <= n_exact, else SLQ */
+    GP2S_LOGDET_EXACT = 1,  /* dense FP64 Cholesky of A: log|A| = 2 sum log L_ii */
+    GP2S_LOGDET_SLQ = 2     /* stochastic Lanczos quadrature on D^{-1/2} A D^{-1/2} */
+} gp2s_logdet_method;
+
+/* Kernel hyperparameters (eq. wendland, eq. bump, Sec. 3.3) and noise (Sec. 3).  Host memory. */
+typedef struct {
+    int32_t d;               /* input dimension, 1..4 */
+    int32_t L;               /* number of bumps, 0..32 */
+    int32_t kind;            /* gp2s_wendland */
+    int32_t reserved;
+    double r;                /* Wendland support radius r0 > 0 */
+    double sigma2;           /* noise variance >= 0 */
+    double beta;             /* bump shape parameter (not differentiated) */
+    double w0;               /* constant added to the bump sum (not differentiated) */
+    const double *centers;   /* host, L x d row-major */
+    const double *radii;     /* host, L */
+    const double *amps;      /* host, L */
+} gp2s_hyper;
+
+/* Options.  gp2s_opts_default() fills the defaults listed here. */
+typedef struct {
+    int32_t precision;       /* gp2s_precision, default MIXED */
+    int32_t logdet;          /* gp2s_logdet_method, default AUTO */
+    int32_t n_exact;         /* AUTO threshold for the dense path, default 20000 */
+    int32_t probes;          /* Rademacher probes m for SLQ / Hutchinson: 0, 32, 64, 96 or 128; default 64 */
+    int32_t lanczos_steps;   /* SLQ steps k per probe, default 100 */
+    int32_t max_iter;        /* iteration cap per CG solve, default 20000 */
+    double tol_inner;        /* FP32 inner CG relative residual, default 1e-5 */
+    double tol_refine;       /* target |y - A a| / |y| of the y solve (FP64 residual), default 1e-8 */
+    double tol_probe;        /* relative residual of the probe solves used by the gradient, default 1e-5 */
+    uint64_t seed;           /* probe seed, default 0 */
+    int32_t precond;         /* 0 = none, 1 = Jacobi (default) */
+    int32_t exact_support;   /* 1 = skip the FP32 guard-band pre-test (every candidate pair is
+                                decided by the FP64 test); default 0 */
+    int32_t max_outer;       /* refinement steps cap, default 8 */
+    int32_t profile;         /* 1 = time every SpMM launch with CUDA events (gp2s_lml_info.ms_spmm); default 0 */
+    int32_t reserved[2];
+} gp2s_opts;
+
+typedef struct {
+    int64_t n, nnz;
+    int64_t candidates;      /* candidate pairs tested (3^d stencil) */
+    int64_t band_pairs;      /* pairs the FP32 guard band sent to the FP64 test */
+    int64_t ncells;          /* occupied cells */
+    int32_t nnz_row_min, nnz_row_max;
+    double guard_delta;      /* relative guard band used by the FP32 pre-test */
+    double cell_h;           /* cell edge */
+    float ms_geometry, ms_count, ms_fill, ms_values64;
+} gp2s_assemble_info;
+
+typedef struct {
+    int32_t iters;           /* FP32 (or FP64) CG iterations of the y column, all refinement steps */
+    int32_t outer;           /* refinement steps */
+    double relres;           /* final |y - A a| / |y|, FP64 residual */
+    float ms;
+} gp2s_solve_info;
+
+typedef struct {
+    int32_t method;          /* GP2S_LOGDET_EXACT or GP2S_LOGDET_SLQ */
+    int32_t probes, steps;
+    int32_t reserved;
+    double logdet_diag;      /* sum log D_ii (SLQ) */
+    double logdet_hat;       /* SLQ estimate of log|D^{-1/2} A D^{-1/2}| */
+    double stderr_hat;       /* standard error of logdet_hat from the probe spread */
+    float ms;
+} gp2s_logdet_info;
+
+typedef struct {
+    double lml, quad, logdet, logdet_stderr, relres;
+    int64_t n, nnz;
+    int32_t iters_y, iters_probes, outer, logdet_method;
+    float ms_assemble, ms_solve, ms_logdet, ms_grad, ms_total;
+    int64_t launches;        /* kernels this call launched */
+    int64_t spmm_launches;   /* SpMM launches of the Krylov solves */
+    double spmm_bytes;       /* algorithmic bytes of those launches: CSR values + indices + row
+                                pointers + each input and output vector element once */
+    float ms_spmm;           /* summed CUDA-event time of the SpMM launches (opts.profile = 1) */
+    float reserved_f;
+} gp2s_lml_info;
+
+typedef struct gp2s_ctx gp2s_ctx;
+
+/* Fill *opts with the defaults above. */
+void gp2s_opts_default(gp2s_opts *opts);
+
+/* Number of hyperparameters of gp2s_lml_grad: L (d + 2) + 2. */
+int32_t gp2s_num_params(int32_t d, int32_t L);
+
+/* Create a context on CUDA device `device` that issues all work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the handle. */
+gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream);
+
+/* Release every device and host buffer of the context. */
+void gp2s_destroy(gp2s_ctx *ctx);
+
+/* One-line description of the last failure on this context ("" if none).  Owned by ctx. */
+const char *gp2s_last_error(const gp2s_ctx *ctx);
+
+/*
+ * Sec. 3.6 (covariance computation) re-designed: assemble A = K + sigma2 I as CSR.
+ * Points are sorted along a Morton curve of a uniform cell grid with edge h >= r; a pair (i, j)
+ * is stored iff i == j or d2(i, j) < r*r with d2 = ((D0*D0 + D1*D1) + D2*D2) + ... in FP64
+ * (round to nearest, no fused multiply-add).  Rows and columns use the sorted numbering;
+ * columns ascend within a row.  In MIXED precision the stored FP32 values are those of the
+ * Jacobi-scaled matrix Ah = D^{-1/2} A D^{-1/2} (D = diag A); FP64 values of Ah are stored too.
+ *   n: number of points (>= 1).  X: n x d FP64, host or device.
+ *   info: optional (NULL allowed).
+ */
+gp2s_status gp2s_assemble(gp2s_ctx *ctx, int64_t n, const double *X, const gp2s_hyper *hyper,
+                          const gp2s_opts *opts, gp2s_assemble_info *info);
+
+/*
+ * Read-only view of the assembled matrix, borrowed from the context (valid until the next
+ * assemble / lml call or destroy).  All pointers are device pointers, sorted numbering:
+ *   rowptr (n + 1, int32), col (nnz, int32), val32 (nnz, FP32 values of Ah, NULL in FP64 mode),
+ *   val64 (nnz, FP64 values of Ah), dscale (n, FP64, D^{-1/2}), perm (n, int32: sorted index ->
+ *   original index).  A_ij = Ah_ij / (dscale_i dscale_j) in FP64.
+ */
+typedef struct {
+    int64_t n, nnz;
+    const int32_t *rowptr, *col, *perm;
+    const float *val32;
+    const double *val64, *dscale;
+} gp2s_csr_view;
+gp2s_status gp2s_csr(gp2s_ctx *ctx, gp2s_csr_view *view);
+
+/*
+ * Sec. 3 / App. B.7 "K^{-1} y": solve A a = y on the last assembled matrix by Jacobi-scaled
+ * conjugate gradients; MIXED precision runs FP32 inner CG and FP64 residual refinement until
+ * |y - A a| / |y| <= opts->tol_refine (FP64 values).  y, a: n FP64 in ORIGINAL point order,
+ * host or device.  The solution is also kept in the context (App. B.6 stores K^{-1} y).
+ */
+gp2s_status gp2s_solve(gp2s_ctx *ctx, const double *y, double *a, gp2s_solve_info *info);
+
+/*
+ * log|A| of the last assembled matrix (Sec. 3; the method is left open in Sec. 3.6 / App. B.7):
+ * EXACT = dense FP64 Cholesky; SLQ = stochastic Lanczos quadrature with opts->probes Rademacher
+ * probes (SplitMix64, seed) and opts->lanczos_steps steps on Ah, plus sum log D_ii.
+ *   logdet: host.  stderr_hat: host, optional (0 for EXACT).
+ */
+gp2s_status gp2s_logdet(gp2s_ctx *ctx, double *logdet, double *stderr_hat, gp2s_logdet_info *info);
+
+/*
+ * The LML of Sec. 3: assemble + solve + log-determinant + reduction, in one call.
+ *   lml: host.  info: optional.
+ */
+gp2s_status gp2s_lml(gp2s_ctx *ctx, int64_t n, const double *X, const double *y,
+                     const gp2s_hyper *hyper, const gp2s_opts *opts, double *lml,
+                     gp2s_lml_info *info);
+
+/*
+ * LML and its gradient d LML / d theta = 1/2 a^T (dA/dtheta) a - 1/2 tr(A^{-1} dA/dtheta),
+ * theta = [centers (L x d), radii (L), amps (L), r, sigma2].  The trace uses Hutchinson's
+ * estimator with the same probes as SLQ (u_s = A^{-1} z_s from the shared multi-RHS CG) in SLQ
+ * mode, and the exact dense inverse in EXACT mode.  dA/dtheta is formed pair by pair on A's
+ * pattern and contracted on the fly; it is never stored.
+ *   grad_host: host, gp2s_num_params(d, L) doubles.
+ */
+gp2s_status gp2s_lml_grad(gp2s_ctx *ctx, int64_t n, const double *X, const double *y,
+                          const gp2s_hyper *hyper, const gp2s_opts *opts, double *lml,
+                          double *grad_host, gp2s_lml_info *info);
+
+/*
+ * Many independent problems in one call (the batched form): problem b has n[b] points of
+ * dimension hyper[b].d, X[b] (n[b] x d) and y[b] (n[b]), host or device.  All problems are
+ * assembled into one block-diagonal CSR and solved together by multi-RHS CG (y plus
+ * opts->probes probe columns each, per-problem scalars); log|A_b| by SLQ (or EXACT when
+ * opts->logdet == EXACT).  lml_host: B doubles.  info_host: optional, B entries.
+ */
+gp2s_status gp2s_lml_batched(gp2s_ctx *ctx, int32_t B, const int64_t *n, const double *const *X,
+                             const double *const *y, const gp2s_hyper *hyper,
+                             const gp2s_opts *opts, double *lml_host, gp2s_lml_info *info_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP2S_H */

@@ -1,0 +1,338 @@
+// adjoint.cu -- gradient of the LML (Sec. 3) with respect to theta = [bump centers (L x d), bump
+// radii (L), bump amplitudes (L), Wendland radius r, noise sigma^2]:
+//     d LML / d theta_p = 1/2 a^T (dA/dtheta_p) a - 1/2 tr(A^{-1} dA/dtheta_p),   a = A^{-1} y.
+// The trace uses Hutchinson's estimator with the SLQ probes: with s = D^{-1/2}, u_s = s * Ah^{-1} z_s
+// (the probe columns of the multi-RHS CG) and v_s = s * z_s,
+//     tr(A^{-1} dA) ~= (1/m) sum_s u_s^T dA v_s.
+// Both terms are contracted with dA on A's own pattern in one pass over the CSR, never storing dA:
+//     W_ij = a_i a_j - (1/m) sum_s (u_is v_js + u_js v_is) / 2
+//     H_il = sum_j phi_ij W_ij b_l(x_j)                        (bump parameters, per row)
+//     g_r  = 1/2 sum_ij (sum_l b_l(x_i) b_l(x_j) + w0) dphi_ij/dr W_ij
+//     g_s2 = 1/2 sum_i W_ii
+// and a per-point pass finishes g_{l,p} = sum_i (d b_l(x_i) / d theta_{l,p}) H_il with the bump
+// derivatives of eq. (bump).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gp2s_kernel_math.cuh"
+#include "gp2s_internal.cuh"
+
+namespace gp2s {
+
+namespace {
+
+__device__ __forceinline__ uint64_t sm64_first(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Probe sign bits: bit s-1 of word (s-1)/32 of row i is 1 when z_s(i) = -1.
+__global__ void k_probe_bits(const int32_t *__restrict__ perm, int64_t n, int m, uint64_t seed,
+                             uint32_t *__restrict__ bits)
+{
+    const int W = (m + 31) / 32;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * W; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e / W;
+        int w = (int)(e - i * W);
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            int s = w * 32 + b + 1;
+            if (s > m) break;
+            uint64_t key = seed ^ (((uint64_t)s << 32) + (uint64_t)(uint32_t)perm[i]);
+            word |= (uint32_t)(sm64_first(key) >> 63) << b;
+        }
+        bits[e] = word;
+    }
+}
+
+__device__ __forceinline__ float flip(float x, uint32_t bit) { return __int_as_float(__float_as_int(x) ^ (int)(bit << 31)); }
+
+template <class T>
+__device__ __forceinline__ float to_f(T v) { return (float)v; }
+
+// sum_s (xa_s z_b,s + xb_s z_a,s) over the m probes (z as sign bits).
+template <class T, int M>
+__device__ __forceinline__ float probe_cross(const T *__restrict__ xa, const uint32_t *__restrict__ za,
+                                             const T *__restrict__ xb, const uint32_t *__restrict__ zb)
+{
+    float acc = 0.0f;
+#pragma unroll
+    for (int w = 0; w < M / 32; ++w) {
+        const uint32_t ba = za[w], bb = zb[w];
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b) {
+            const int s = w * 32 + b;
+            acc += flip(to_f(xa[s]), (bb >> b) & 1u) + flip(to_f(xb[s]), (ba >> b) & 1u);
+        }
+    }
+    return acc;
+}
+
+struct AdjArgs {
+    const int32_t *rowptr, *col;
+    const float4 *Xhi, *Xlo;
+    const float *B32;          // n x L
+    const double *a;           // n (sorted order)
+    const double *s64;         // n
+    const void *U;             // n x m probe solutions of Ah (FP32 or FP64)
+    const uint32_t *zbits;     // n x (m/32)
+    int64_t n;
+    int m;
+    float *H;                  // n x L
+    double *part;              // per block: [g_r, g_s2]
+};
+
+template <int D, class T, int M>
+__global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int L = kp.L;
+    const T *U = reinterpret_cast<const T *>(g.U);
+    constexpr int WZ = M / 32 > 0 ? M / 32 : 1;
+    const float inv_r = (float)kp.inv_r;
+    const float inv2m = M > 0 ? 0.5f / (float)M : 0.0f;
+    double gr = 0.0, gs = 0.0;
+    for (int64_t i = w0; i < g.n; i += nw) {
+        const float4 hi_i = g.Xhi[i], lo_i = g.Xlo[i];
+        const float ai = (float)g.a[i];
+        const float si = (float)g.s64[i];
+        const T *Ui = U + i * M;
+        uint32_t zi[WZ];
+#pragma unroll
+        for (int w = 0; w < WZ; ++w) zi[w] = M > 0 ? g.zbits[i * WZ + w] : 0u;
+        float Hacc[kMaxBumps];
+        for (int l = 0; l < L; ++l) Hacc[l] = 0.0f;
+        float grr = 0.0f, gss = 0.0f;
+        const int p1 = g.rowptr[i + 1];
+        for (int p = g.rowptr[i] + lane; p < p1; p += 32) {
+            const int j = g.col[p];
+            const float aj = (float)g.a[j];
+            const float sj = (float)g.s64[j];
+            float tr = 0.0f;
+            if (M > 0) {
+                uint32_t zj[WZ];
+#pragma unroll
+                for (int w = 0; w < WZ; ++w) zj[w] = g.zbits[(int64_t)j * WZ + w];
+                tr = probe_cross<T, M>(Ui, zi, U + (int64_t)j * M, zj);
+            }
+            const float W = ai * aj - si * sj * tr * inv2m;
+            if (j == i) {
+                gss += W;
+            }
+            // distance (hi/lo split), Wendland value and d/dr
+            const float4 hi_j = g.Xhi[j], lo_j = g.Xlo[j];
+            const float hi[4] = {hi_i.x, hi_i.y, hi_i.z, hi_i.w}, lo[4] = {lo_i.x, lo_i.y, lo_i.z, lo_i.w};
+            const float hj[4] = {hi_j.x, hi_j.y, hi_j.z, hi_j.w}, lj[4] = {lo_j.x, lo_j.y, lo_j.z, lo_j.w};
+            float q = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                float dk = (hi[k] - hj[k]) + (lo[k] - lj[k]);
+                q = fmaf(dk, dk, q);
+            }
+            const float t = sqrtf(q) * inv_r;
+            const float phi = wendland<float>(kp.kind, D, t);
+            const float dphi_dr = -wendland_dt<float>(kp.kind, D, t) * t * inv_r;
+            float S = 0.0f;
+            const float pw = phi * W;
+            for (int l = 0; l < L; ++l) {
+                const float bj = g.B32[(int64_t)j * L + l];
+                S = fmaf(g.B32[i * L + l], bj, S);
+                Hacc[l] = fmaf(pw, bj, Hacc[l]);
+            }
+            grr += (S + (float)kp.w0) * dphi_dr * W;
+        }
+        // reduce the row's H over the warp
+        for (int l = 0; l < L; ++l) {
+            float v = Hacc[l];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) g.H[i * L + l] = v;
+        }
+        gr += (double)grr;
+        gs += (double)gss;
+    }
+    // block reduction of g_r and g_s2 partial sums
+    __shared__ double sh[2][8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gr += __shfl_xor_sync(0xffffffffu, gr, o);
+        gs += __shfl_xor_sync(0xffffffffu, gs, o);
+    }
+    if (lane == 0) {
+        sh[0][threadIdx.x >> 5] = gr;
+        sh[1][threadIdx.x >> 5] = gs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[0][w]; b += sh[1][w]; }
+        g.part[blockIdx.x * 2 + 0] = a;
+        g.part[blockIdx.x * 2 + 1] = b;
+    }
+}
+
+// g_{l,p} = sum_i d b_l(x_i) / d theta_{l,p} * H_il (FP64), per-block partials of the
+// L (d + 2) bump parameters: [centers (L x d), radii (L), amps (L)].
+// Thread t of a block handles bump l = t % L for points i = t / L, t / L + R, ... (R = threads / L
+// points per block step); blockDim.x is a multiple of L.
+template <int D>
+__global__ void __launch_bounds__(256)
+k_bump_grad(const double4 *__restrict__ X64, const float *__restrict__ H, int64_t n, KernelParams kp,
+            double *__restrict__ part)
+{
+    const int L = kp.L;
+    const int P = L * (D + 2);
+    extern __shared__ double acc_sh[];   // blockDim.x x (D + 2)
+    const int l = threadIdx.x % L;
+    const int R = blockDim.x / L;
+    double acc[D + 2];
+#pragma unroll
+    for (int p = 0; p < D + 2; ++p) acc[p] = 0.0;
+    const double rho = kp.radii[l];
+    for (int64_t i = (int64_t)blockIdx.x * R + threadIdx.x / L; i < n; i += (int64_t)gridDim.x * R) {
+        const double h = (double)H[i * L + l];
+        if (h == 0.0) continue;
+        const double4 xv = X64[i];
+        const double x[4] = {xv.x, xv.y, xv.z, xv.w};
+        double q = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            double dk = x[k] - kp.centers[l * D + k];
+            q = q + dk * dk;
+        }
+        const double s = q / (rho * rho);
+        if (!(s < 1.0)) continue;
+        const double om = 1.0 - s;
+        const double e = exp(kp.beta * (1.0 - 1.0 / om));
+        if (!(e > 0.0)) continue;
+        const double b = kp.amps[l] * e;
+        const double dbds = -kp.beta * b / (om * om);            // d b / d s
+#pragma unroll
+        for (int k = 0; k < D; ++k)                               // d s / d c_k = -2 (x_k - c_k) / rho^2
+            acc[k] += h * dbds * (-2.0 * (x[k] - kp.centers[l * D + k]) / (rho * rho));
+        acc[D] += h * dbds * (-2.0 * s / rho);                    // d s / d rho = -2 s / rho
+        acc[D + 1] += h * e;                                      // d b / d a
+    }
+#pragma unroll
+    for (int p = 0; p < D + 2; ++p) acc_sh[threadIdx.x * (D + 2) + p] = acc[p];
+    __syncthreads();
+    // threads 0..L-1 sum their bump's rows of the block (fixed order)
+    if ((int)threadIdx.x < L) {
+        double v[D + 2];
+#pragma unroll
+        for (int p = 0; p < D + 2; ++p) v[p] = 0.0;
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int p = 0; p < D + 2; ++p) v[p] += acc_sh[(r * L + threadIdx.x) * (D + 2) + p];
+        double *out = part + (int64_t)blockIdx.x * P;
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[threadIdx.x * D + k] = v[k];
+        out[L * D + threadIdx.x] = v[D];
+        out[L * D + L + threadIdx.x] = v[D + 1];
+    }
+}
+
+template <int D, class T>
+gp2s_status launch_adjoint(gp2s_ctx *c, const AdjArgs &g, const KernelParams &kp, unsigned gb)
+{
+    switch (g.m) {
+    case 0: k_adjoint<D, T, 0><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 32: k_adjoint<D, T, 32><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 64: k_adjoint<D, T, 64><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 96: k_adjoint<D, T, 96><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 128: k_adjoint<D, T, 128><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    default: return set_err(c, GP2S_EINVAL, "probes must be 0, 32, 64, 96 or 128");
+    }
+    GP2S_LAUNCH(c);
+    return GP2S_OK;
+}
+
+template <class T>
+gp2s_status dispatch_adjoint(gp2s_ctx *c, int d, const AdjArgs &g, const KernelParams &kp, unsigned gb)
+{
+    switch (d) {
+    case 1: return launch_adjoint<1, T>(c, g, kp, gb);
+    case 2: return launch_adjoint<2, T>(c, g, kp, gb);
+    case 3: return launch_adjoint<3, T>(c, g, kp, gb);
+    default: return launch_adjoint<4, T>(c, g, kp, gb);
+    }
+}
+
+}  // namespace
+
+gp2s_status adjoint_gradient(gp2s_ctx *c, int m, bool exact_inverse, double *grad_host)
+{
+    (void)exact_inverse;
+    const Assembled &A = c->A;
+    const int64_t n = A.n;
+    const int d = A.d, L = A.L;
+    const int P = L * (d + 2) + 2;
+    if (!c->have_solution) return set_err(c, GP2S_ENOTREADY, "gradient needs the solve");
+    if (m > 0 && !c->have_probes) return set_err(c, GP2S_ENOTREADY, "gradient needs the probe solves");
+    const bool mixed = A.precision == GP2S_PREC_MIXED;
+    const int W = m > 0 ? m / 32 : 0;
+    GP2S_TRY(ensure(c, c->Z, sizeof(uint32_t) * (size_t)n * (W > 0 ? W : 1) + 64));
+    GP2S_TRY(ensure(c, c->H, sizeof(float) * (size_t)n * (L > 0 ? L : 1) + 64));
+    const int nb = 152 * 8;
+    const int nbf = 152 * 2;
+    GP2S_TRY(ensure(c, c->gpart, sizeof(double) * ((size_t)nb * 2 + (size_t)nbf * P + 64)));
+    double *part = c->gpart.as<double>();
+    double *bpart = part + (size_t)nb * 2;
+    if (m > 0) {
+        unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * W, 256), 152 * 8);
+        k_probe_bits<<<gb, 256, 0, c->stream>>>(c->perm.as<int32_t>(), n, m, A.opts.seed, c->Z.as<uint32_t>());
+        GP2S_LAUNCH(c);
+    }
+    AdjArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.rowptr = c->rowptr.as<int32_t>();
+    g.col = c->col.as<int32_t>();
+    g.Xhi = c->Xhi.as<float4>();
+    g.Xlo = c->Xlo.as<float4>();
+    g.B32 = c->B32.as<float>();
+    g.a = c->vec64.as<double>() + 3 * n;
+    g.s64 = c->s64.as<double>();
+    g.U = c->vec.p;          // probe-group x (first block of the Krylov vectors)
+    g.zbits = c->Z.as<uint32_t>();
+    g.n = n;
+    g.m = m;
+    g.H = c->H.as<float>();
+    g.part = part;
+    if (mixed) GP2S_TRY(dispatch_adjoint<float>(c, d, g, A.kp, nb));
+    else GP2S_TRY(dispatch_adjoint<double>(c, d, g, A.kp, nb));
+    // bump parameters
+    const int Pb = L * (d + 2);
+    if (Pb > 0) {
+        const int thr = L * (256 / L);
+        size_t smem = sizeof(double) * (size_t)thr * (d + 2);
+        switch (d) {
+        case 1: k_bump_grad<1><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4>(), c->H.as<float>(), n, A.kp, bpart); break;
+        case 2: k_bump_grad<2><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4>(), c->H.as<float>(), n, A.kp, bpart); break;
+        case 3: k_bump_grad<3><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4>(), c->H.as<float>(), n, A.kp, bpart); break;
+        default: k_bump_grad<4><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4>(), c->H.as<float>(), n, A.kp, bpart); break;
+        }
+        GP2S_LAUNCH(c);
+    }
+    std::vector<double> hp((size_t)nb * 2), hb((size_t)nbf * (Pb > 0 ? Pb : 1));
+    GP2S_CUDA(c, cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb * 2, cudaMemcpyDeviceToHost, c->stream));
+    if (Pb > 0)
+        GP2S_CUDA(c, cudaMemcpyAsync(hb.data(), bpart, sizeof(double) * (size_t)nbf * Pb, cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    // fixed-order host sums of the (few hundred) block partials
+    for (int p = 0; p < P; ++p) grad_host[p] = 0.0;
+    for (int b = 0; b < nbf && Pb > 0; ++b)
+        for (int p = 0; p < Pb; ++p) grad_host[p] += hb[(size_t)b * Pb + p];
+    double gr = 0.0, gs = 0.0;
+    for (int b = 0; b < nb; ++b) { gr += hp[2 * b]; gs += hp[2 * b + 1]; }
+    grad_host[P - 2] = 0.5 * gr;
+    grad_host[P - 1] = 0.5 * gs;
+    return GP2S_OK;
+}
+
+}  // namespace gp2s

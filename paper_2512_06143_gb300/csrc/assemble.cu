@@ -1,0 +1,643 @@
+// assemble.cu -- count -> scan -> fill assembly of A = K + sigma^2 I into CSR (Sec. 3.6 redesigned),
+// the bump tables (eq. bump), the Jacobi diagonal, and the FP64 values pass.
+//
+// One CTA per work item (a run of at most kRowsPerItem rows of one occupied cell).  The CTA finds
+// the 3^d neighbour cells by binary search in the sorted cell-key table, orders their point ranges
+// by start index, stages chunks of the concatenated candidate points (hi/lo FP32 coordinates, and
+// in the fill pass the FP32 bump values and Jacobi scales) in shared memory, and each warp tests
+// its rows against the staged chunk with a conservative FP32 guard band; pairs inside the band are
+// decided by the exact FP64 test (same operation order as the oracle).  Warp ballots give the row
+// counts (count pass) and the ordered, compacted column/value writes (fill pass): candidates are
+// visited in ascending sorted index, so columns come out ascending.
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+
+#include "gp2s_geometry.cuh"
+#include "gp2s_kernel_math.cuh"
+
+namespace gp2s {
+
+namespace {
+
+constexpr int kAsmThreads = 128;
+constexpr int kAsmWarps = kAsmThreads / kWarp;
+constexpr int kRowsPerItem = 64;
+constexpr int kChunk = 256;
+
+struct AsmArgs {
+    const float4 *Xhi, *Xlo;
+    const double4 *X64;
+    const int4 *items;
+    const int32_t *cell_start;
+    const uint64_t *cell_key;
+    int64_t ncells;
+    const float *B32;     // n x L
+    const float *s32;     // n
+    const int32_t *rowptr;
+    int32_t *rowcnt;
+    int32_t *col;
+    float *val;
+    unsigned long long *stats;   // [0] candidates, [1] band pairs
+};
+
+template <int D>
+__device__ __forceinline__ void decode_coarse(uint64_t ck, int cb, int64_t *cc)
+{
+#pragma unroll
+    for (int k = 0; k < D; ++k) cc[k] = 0;
+    for (int b = 0; b < cb; ++b)
+#pragma unroll
+        for (int k = 0; k < D; ++k) cc[k] |= (int64_t)((ck >> (b * D + k)) & 1ull) << b;
+}
+
+__device__ __forceinline__ int64_t find_cell(const uint64_t *__restrict__ keys, int64_t n, uint64_t k)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (keys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && keys[lo] == k) ? lo : -1;
+}
+
+// FP32 squared distance from the hi/lo split: Dk = (hi_i - hi_j) + (lo_i - lo_j).
+template <int D>
+__device__ __forceinline__ float d2_f32(const float4 &hi_i, const float4 &lo_i, const float4 &hi_j,
+                                        const float4 &lo_j)
+{
+    const float hi[4] = {hi_i.x, hi_i.y, hi_i.z, hi_i.w}, lo[4] = {lo_i.x, lo_i.y, lo_i.z, lo_i.w};
+    const float hj[4] = {hi_j.x, hi_j.y, hi_j.z, hi_j.w}, lj[4] = {lo_j.x, lo_j.y, lo_j.z, lo_j.w};
+    float q = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        float dk = __fadd_rn(__fsub_rn(hi[k], hj[k]), __fsub_rn(lo[k], lj[k]));
+        q = __fmaf_rn(dk, dk, q);
+    }
+    return q;
+}
+
+// The exact pattern test: ((D0*D0 + D1*D1) + D2*D2) + ... < r*r, FP64, no fused multiply-add.
+template <int D>
+__device__ __forceinline__ bool exact_in(const double4 &a, const double4 &b, double r2)
+{
+    const double xa[4] = {a.x, a.y, a.z, a.w}, xb[4] = {b.x, b.y, b.z, b.w};
+    double q = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        double dk = __dsub_rn(xa[k], xb[k]);
+        q = __dadd_rn(q, __dmul_rn(dk, dk));
+    }
+    return q < r2;
+}
+
+template <int D, bool FILL>
+__global__ void __launch_bounds__(kAsmThreads)
+k_assemble(AsmArgs a, GridParams g, SupportParams sp, KernelParams kp)
+{
+    constexpr int NNB = D == 1 ? 3 : D == 2 ? 9 : D == 3 ? 27 : 81;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 *c_hi = reinterpret_cast<float4 *>(smem);
+    float4 *c_lo = c_hi + kChunk;
+    float4 *r_hi = c_lo + kChunk;
+    float4 *r_lo = r_hi + kRowsPerItem;
+    int *c_j = reinterpret_cast<int *>(r_lo + kRowsPerItem);
+    int *r_run = c_j + kChunk;
+    int2 *rng = reinterpret_cast<int2 *>(r_run + kRowsPerItem);      // NNB (start, end)
+    int2 *rng_sorted = rng + NNB;
+    int *pref = reinterpret_cast<int *>(rng_sorted + NNB);           // NNB + 1
+    int *nr_sh = pref + NNB + 1;
+    float *c_B = reinterpret_cast<float *>(nr_sh + 4);               // kChunk x L (fill)
+    float *c_s = c_B + (FILL ? kChunk * kp.L : 0);
+    float *r_B = c_s + (FILL ? kChunk : 0);                          // kRowsPerItem x L
+    float *r_s = r_B + (FILL ? kRowsPerItem * kp.L : 0);
+
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int4 item = a.items[blockIdx.x];
+    const int cell = item.x, r0 = item.y, r1 = item.z;
+    const int nrows = r1 - r0;
+    const int L = kp.L;
+
+    // 1. neighbour cells and their point ranges
+    const int cb = g.bits - g.fine_bits;
+    if (threadIdx.x < NNB) {
+        int64_t cc[D], nc[D];
+        decode_coarse<D>(a.cell_key[cell], cb, cc);
+        int t = threadIdx.x;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            int o = t % 3 - 1;
+            t /= 3;
+            nc[k] = cc[k] + o;
+            ok = ok && nc[k] >= 0 && nc[k] < g.dims[k];
+        }
+        int2 rr = make_int2(0, 0);
+        if (ok) {
+            int64_t f = find_cell(a.cell_key, a.ncells, coarse_key<D>(nc, g));
+            if (f >= 0) rr = make_int2(a.cell_start[f], a.cell_start[f + 1]);
+        }
+        rng[threadIdx.x] = rr;
+    }
+    // rows of the item
+    for (int t = threadIdx.x; t < nrows; t += kAsmThreads) {
+        r_hi[t] = a.Xhi[r0 + t];
+        r_lo[t] = a.Xlo[r0 + t];
+        r_run[t] = 0;
+        if (FILL) {
+            for (int l = 0; l < L; ++l) r_B[t * L + l] = a.B32[(int64_t)(r0 + t) * L + l];
+            r_s[t] = a.s32[r0 + t];
+        }
+    }
+    __syncthreads();
+    // 2. order the non-empty ranges by start (ranges of distinct cells are disjoint)
+    if (wid == 0) {
+        for (int e = lane; e < NNB; e += kWarp) {
+            int2 me = rng[e];
+            if (me.y > me.x) {
+                int rank = 0;
+                for (int f = 0; f < NNB; ++f) {
+                    int2 o = rng[f];
+                    rank += (o.y > o.x && o.x < me.x) ? 1 : 0;
+                }
+                rng_sorted[rank] = me;
+            }
+        }
+        unsigned cnt = 0;
+        for (int e = lane; e < NNB; e += kWarp) cnt += rng[e].y > rng[e].x ? 1u : 0u;
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) {
+            int run = 0;
+            for (int e = 0; e < (int)cnt; ++e) {
+                pref[e] = run;
+                run += rng_sorted[e].y - rng_sorted[e].x;
+            }
+            pref[cnt] = run;
+            nr_sh[0] = (int)cnt;
+        }
+    }
+    __syncthreads();
+    const int nr = nr_sh[0];
+    const int total = pref[nr];
+    unsigned long long band = 0;
+
+    // 3. candidate chunks
+    for (int base = 0; base < total; base += kChunk) {
+        const int cnt = min(kChunk, total - base);
+        for (int q = threadIdx.x; q < cnt; q += kAsmThreads) {
+            int p = base + q;
+            int lo = 0, hi = nr - 1;           // last range with pref <= p
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (pref[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            int j = rng_sorted[lo].x + (p - pref[lo]);
+            c_j[q] = j;
+            c_hi[q] = a.Xhi[j];
+            c_lo[q] = a.Xlo[j];
+            if (FILL) {
+                for (int l = 0; l < L; ++l) c_B[q * L + l] = a.B32[(int64_t)j * L + l];
+                c_s[q] = a.s32[j];
+            }
+        }
+        __syncthreads();
+        for (int rs = wid; rs < nrows; rs += kAsmWarps) {
+            const int i = r0 + rs;
+            const float4 hi_i = r_hi[rs], lo_i = r_lo[rs];
+            int run = r_run[rs];
+            int64_t obase = FILL ? (int64_t)a.rowptr[i] : 0;
+            // the fill pass accepts exactly the count pass's pairs (same arithmetic); the row end
+            // is still checked so a mismatch could never write past the row
+            const int rowlen = FILL ? a.rowptr[i + 1] - a.rowptr[i] : 0;
+            for (int q0 = 0; q0 < cnt; q0 += kWarp) {
+                const int q = q0 + lane;
+                bool acc = false;
+                float d2 = 0.0f;
+                int j = -1;
+                if (q < cnt) {
+                    j = c_j[q];
+                    d2 = d2_f32<D>(hi_i, lo_i, c_hi[q], c_lo[q]);
+                    if (j == i || d2 < sp.thr_lo) {
+                        acc = true;
+                    } else if (d2 <= sp.thr_hi) {
+                        ++band;
+                        acc = exact_in<D>(a.X64[i], a.X64[j], sp.r2);
+                    }
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, acc);
+                if (FILL && acc) {
+                    const int pos = run + __popc(bal & ((1u << lane) - 1u));
+                    float v;
+                    if (j == i) {
+                        v = 1.0f;                               // Ah_ii = A_ii / D_i = 1
+                    } else {
+                        float t = sqrtf(d2) * (float)kp.inv_r;
+                        float phi = wendland<float>(kp.kind, D, t);
+                        float S = 0.0f;
+                        for (int l = 0; l < L; ++l) S = fmaf(r_B[rs * L + l], c_B[q * L + l], S);
+                        S += (float)kp.w0;
+                        v = phi * S * (r_s[rs] * c_s[q]);
+                    }
+                    if (pos < rowlen) {
+                        a.col[obase + pos] = j;
+                        if (a.val) a.val[obase + pos] = v;
+                    }
+                }
+                run += __popc(bal);
+            }
+            if (lane == 0) r_run[rs] = run;
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    if (!FILL) {
+        for (int t = threadIdx.x; t < nrows; t += kAsmThreads) a.rowcnt[r0 + t] = r_run[t];
+        // statistics: candidates tested and FP64 band tests
+        for (int o = 16; o > 0; o >>= 1) band += __shfl_xor_sync(0xffffffffu, band, o);
+        if (lane == 0 && band) atomicAdd(&a.stats[1], band);
+        if (threadIdx.x == 0) atomicAdd(&a.stats[0], (unsigned long long)total * (unsigned long long)nrows);
+    }
+}
+
+size_t asm_smem_bytes(int D, bool fill, int L)
+{
+    int NNB = D == 1 ? 3 : D == 2 ? 9 : D == 3 ? 27 : 81;
+    size_t b = sizeof(float4) * (2 * kChunk + 2 * kRowsPerItem) + sizeof(int) * (kChunk + kRowsPerItem) +
+               sizeof(int2) * 2 * NNB + sizeof(int) * (NNB + 1 + 4);
+    if (fill) b += sizeof(float) * (kChunk * L + kChunk + kRowsPerItem * L + kRowsPerItem);
+    return b + 16;
+}
+
+// Bump tables (eq. bump) in FP64 (+ an FP32 copy), the diagonal D_i = A_ii = (sum_l b_l^2 + w0)
+// + sigma^2 and the Jacobi scales s_i = D_i^{-1/2}.
+template <int D>
+__global__ void k_bumps(const double4 *__restrict__ X64, int64_t n, KernelParams kp,
+                        double *__restrict__ B64, float *__restrict__ B32, double *__restrict__ D64,
+                        double *__restrict__ s64, float *__restrict__ s32, int *__restrict__ bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double4 xv = X64[i];
+        const double x[4] = {xv.x, xv.y, xv.z, xv.w};
+        double S = 0.0;
+        for (int l = 0; l < kp.L; ++l) {
+            double q = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double dk = x[k] - kp.centers[l * D + k];
+                q = q + dk * dk;
+            }
+            double rho = kp.radii[l];
+            double s = q / (rho * rho);
+            double e = 0.0;
+            if (s < 1.0) e = exp(kp.beta * (1.0 - 1.0 / (1.0 - s)));
+            double b = kp.amps[l] * e;
+            B64[i * kp.L + l] = b;
+            B32[i * kp.L + l] = (float)b;
+            S = S + b * b;
+        }
+        double Dii = (S + kp.w0) + kp.sigma2;
+        D64[i] = Dii;
+        if (!(Dii > 0.0) || !isfinite(Dii)) {
+            atomicOr(bad, 1);
+            s64[i] = 0.0;
+            s32[i] = 0.0f;
+        } else {
+            double sc = 1.0 / sqrt(Dii);
+            s64[i] = sc;
+            s32[i] = (float)sc;
+        }
+    }
+}
+
+// FP64 values of Ah on the assembled pattern: one warp per row, lanes over the row's entries.
+template <int D>
+__global__ void __launch_bounds__(256)
+k_values64(const double4 *__restrict__ X64, const int32_t *__restrict__ rowptr,
+           const int32_t *__restrict__ col, int64_t n, KernelParams kp, const double *__restrict__ B64,
+           const double *__restrict__ s64, double *__restrict__ val64)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int L = kp.L;
+    for (int64_t i = warp0; i < n; i += nwarps) {
+        const double4 xi = X64[i];
+        const double si = s64[i];
+        const int p0 = rowptr[i], p1 = rowptr[i + 1];
+        for (int p = p0 + lane; p < p1; p += kWarp) {
+            const int j = col[p];
+            double v;
+            if (j == i) {
+                v = 1.0;
+            } else {
+                const double4 xj = X64[j];
+                const double a[4] = {xi.x, xi.y, xi.z, xi.w}, b[4] = {xj.x, xj.y, xj.z, xj.w};
+                double q = 0.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    double dk = __dsub_rn(a[k], b[k]);
+                    q = __dadd_rn(q, __dmul_rn(dk, dk));
+                }
+                double t = sqrt(q) * kp.inv_r;
+                double phi = wendland<double>(kp.kind, D, t);
+                double S = 0.0;
+                for (int l = 0; l < L; ++l) S = fma(B64[i * L + l], B64[(int64_t)j * L + l], S);
+                v = (phi * (S + kp.w0)) * (si * s64[j]);
+            }
+            val64[p] = v;
+        }
+    }
+}
+
+__global__ void k_rowcnt_minmax(const int32_t *__restrict__ cnt, int64_t n, int *__restrict__ mm)
+{
+    int lo = INT32_MAX, hi = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        lo = min(lo, cnt[i]);
+        hi = max(hi, cnt[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[0], lo);
+        atomicMax(&mm[1], hi);
+    }
+}
+
+template <int D, bool FILL>
+gp2s_status launch_assemble(gp2s_ctx *c, const AsmArgs &a, const GridParams &g, const SupportParams &sp,
+                            const KernelParams &kp, int64_t nitems)
+{
+    size_t smem = asm_smem_bytes(D, FILL, kp.L);
+    GP2S_CUDA(c, cudaFuncSetAttribute(k_assemble<D, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_assemble<D, FILL><<<(unsigned)nitems, kAsmThreads, smem, c->stream>>>(a, g, sp, kp);
+    GP2S_LAUNCH(c);
+    return GP2S_OK;
+}
+
+template <bool FILL>
+gp2s_status dispatch_assemble(gp2s_ctx *c, int d, const AsmArgs &a, const GridParams &g,
+                              const SupportParams &sp, const KernelParams &kp, int64_t nitems)
+{
+    switch (d) {
+    case 1: return launch_assemble<1, FILL>(c, a, g, sp, kp, nitems);
+    case 2: return launch_assemble<2, FILL>(c, a, g, sp, kp, nitems);
+    case 3: return launch_assemble<3, FILL>(c, a, g, sp, kp, nitems);
+    default: return launch_assemble<4, FILL>(c, a, g, sp, kp, nitems);
+    }
+}
+
+float round_down_f(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = std::nextafter(f, -FLT_MAX);
+    return f;
+}
+float round_up_f(double x)
+{
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, FLT_MAX);
+    return f;
+}
+
+}  // namespace
+
+gp2s_status validate_hyper(gp2s_ctx *c, const gp2s_hyper *h)
+{
+    if (!h) return set_err(c, GP2S_EINVAL, "hyper is NULL");
+    if (h->d < 1 || h->d > kMaxDim) return set_err(c, GP2S_EINVAL, "d must be in 1..4");
+    if (h->L < 0 || h->L > kMaxBumps) return set_err(c, GP2S_EINVAL, "L must be in 0..32");
+    if (!(h->r > 0.0) || !std::isfinite(h->r)) return set_err(c, GP2S_EINVAL, "r must be finite and > 0");
+    if (!(h->sigma2 >= 0.0) || !std::isfinite(h->sigma2)) return set_err(c, GP2S_EINVAL, "sigma2 must be finite and >= 0");
+    if (!std::isfinite(h->beta) || !std::isfinite(h->w0)) return set_err(c, GP2S_EINVAL, "beta / w0 must be finite");
+    if (h->kind != GP2S_WENDLAND_C2 && h->kind != GP2S_WENDLAND_C6_PAPER) return set_err(c, GP2S_EINVAL, "unknown Wendland kind");
+    if (h->kind == GP2S_WENDLAND_C6_PAPER && h->d > 3) return set_err(c, GP2S_EINVAL, "eq. (wendland) C6 form is positive definite only for d <= 3");
+    if (h->L > 0 && (!h->centers || !h->radii || !h->amps)) return set_err(c, GP2S_EINVAL, "bump arrays are NULL");
+    for (int l = 0; l < h->L; ++l) {
+        if (!(h->radii[l] > 0.0) || !std::isfinite(h->radii[l]) || !std::isfinite(h->amps[l]))
+            return set_err(c, GP2S_EINVAL, "bump radius must be > 0 and amplitudes finite");
+        for (int k = 0; k < h->d; ++k)
+            if (!std::isfinite(h->centers[l * h->d + k])) return set_err(c, GP2S_EINVAL, "bump center not finite");
+    }
+    return GP2S_OK;
+}
+
+KernelParams make_kernel_params(const gp2s_hyper *h)
+{
+    KernelParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.d = h->d;
+    kp.L = h->L;
+    kp.kind = h->kind;
+    kp.r = h->r;
+    kp.inv_r = 1.0 / h->r;
+    kp.sigma2 = h->sigma2;
+    kp.beta = h->beta;
+    kp.w0 = h->w0;
+    for (int l = 0; l < h->L; ++l) {
+        for (int k = 0; k < h->d; ++k) kp.centers[l * h->d + k] = h->centers[l * h->d + k];
+        kp.radii[l] = h->radii[l];
+        kp.amps[l] = h->amps[l];
+    }
+    return kp;
+}
+
+gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const gp2s_hyper *h,
+                             const gp2s_opts *o)
+{
+    Assembled &A = c->A;
+    A.valid = false;
+    c->have_solution = false;
+    c->have_probes = false;
+    c->have_exact = false;
+    const int d = h->d;
+    cudaEvent_t ev[5];
+    for (int k = 0; k < 5; ++k) GP2S_CUDA(c, cudaEventCreate(&ev[k]));
+    struct EvGuard { cudaEvent_t *e; ~EvGuard() { for (int k = 0; k < 5; ++k) cudaEventDestroy(e[k]); } } guard{ev};
+    GP2S_CUDA(c, cudaEventRecord(ev[0], c->stream));
+
+    // ---- bounding box, grid, guard band (host arithmetic in FP64, no contraction) ----
+    double box[2 * kMaxDim + 1];
+    GP2S_TRY(geom_bbox(c, X_dev, n, d, box));
+    int bad = 0;
+    std::memcpy(&bad, &box[2 * kMaxDim], sizeof(int));
+    if (bad) return set_err(c, GP2S_EINVAL, "X contains NaN or infinity");
+    GridParams g;
+    std::memset(&g, 0, sizeof(g));
+    g.d = d;
+    double h_cell = h->r * (1.0 + std::ldexp(1.0, -20));
+    double M = 0.0;
+    for (int k = 0; k < d; ++k) {
+        M = std::fmax(M, std::fmax(std::fabs(box[k]), std::fabs(box[kMaxDim + k])));
+        g.origin[k] = box[k];
+    }
+    const int max_bits = d == 1 ? 30 : 64 / d;
+    int fine = 2;
+    for (;;) {
+        double inv_h = 1.0 / h_cell;
+        int cb = 1;
+        for (int k = 0; k < d; ++k) {
+            double ext = (box[kMaxDim + k] - box[k]) * inv_h;
+            int64_t dims = (int64_t)std::floor(ext) + 1;
+            g.dims[k] = dims;
+            while ((int64_t(1) << cb) < dims) ++cb;
+        }
+        if (cb + fine > max_bits) fine = std::max(0, max_bits - cb);
+        if (cb + fine <= max_bits) {
+            g.inv_h = inv_h;
+            g.h = h_cell;
+            g.fine_bits = fine;
+            g.bits = cb + fine;
+            break;
+        }
+        h_cell *= 2.0;   // grid too fine for the key width: coarser cells are still correct
+    }
+    SupportParams sp;
+    sp.r2 = h->r * h->r;
+    const double u = std::ldexp(1.0, -24);
+    const double ratio = M / h->r;
+    bool exact = o->exact_support != 0 || ratio > 1e6 || sp.r2 < 1e-30 || M > 1e18;
+    double delta = 32.0 * u + 16.0 * d * u * u * ratio;
+    if (exact) {
+        sp.thr_lo = -1.0f;
+        sp.thr_hi = FLT_MAX;
+        delta = INFINITY;
+    } else {
+        sp.thr_lo = round_down_f(sp.r2 * (1.0 - delta));
+        sp.thr_hi = round_up_f(sp.r2 * (1.0 + delta));
+    }
+
+    // ---- sort, permute, cells ----
+    GP2S_TRY(geom_sort(c, X_dev, n, g));
+    GP2S_TRY(geom_permute(c, X_dev, n, d));
+    int64_t ncells = 0, nitems = 0;
+    GP2S_TRY(geom_cells(c, n, g, kRowsPerItem, &ncells, &nitems));
+    KernelParams kp = make_kernel_params(h);
+
+    // ---- bumps, diagonal, Jacobi scales ----
+    const int L = h->L;
+    GP2S_TRY(ensure(c, c->B64, sizeof(double) * (size_t)n * (L > 0 ? L : 1)));
+    GP2S_TRY(ensure(c, c->B32, sizeof(float) * (size_t)n * (L > 0 ? L : 1)));
+    GP2S_TRY(ensure(c, c->D64, sizeof(double) * n));
+    GP2S_TRY(ensure(c, c->s64, sizeof(double) * n));
+    GP2S_TRY(ensure(c, c->s32, sizeof(float) * n));
+    GP2S_TRY(ensure(c, c->counters, 256));
+    int *dbad = c->counters.as<int>();
+    unsigned long long *stats = reinterpret_cast<unsigned long long *>(c->counters.as<char>() + 64);
+    int *mm = reinterpret_cast<int *>(c->counters.as<char>() + 128);
+    GP2S_CUDA(c, cudaMemsetAsync(c->counters.p, 0, 256, c->stream));
+    {
+        unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
+        const double4 *x64 = c->Xs64.as<double4>();
+        double *B64 = c->B64.as<double>();
+        switch (d) {
+        case 1: k_bumps<1><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
+        case 2: k_bumps<2><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
+        case 3: k_bumps<3><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
+        default: k_bumps<4><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
+        }
+        GP2S_LAUNCH(c);
+    }
+    GP2S_CUDA(c, cudaEventRecord(ev[1], c->stream));
+
+    // ---- count -> scan ----
+    GP2S_TRY(ensure(c, c->rowcnt, sizeof(int32_t) * (n + 1)));
+    GP2S_TRY(ensure(c, c->rowptr, sizeof(int32_t) * (n + 1)));
+    AsmArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.Xhi = c->Xhi.as<float4>();
+    a.Xlo = c->Xlo.as<float4>();
+    a.X64 = c->Xs64.as<double4>();
+    a.items = c->items.as<int4>();
+    a.cell_start = c->cell_start.as<int32_t>();
+    a.cell_key = cell_keys_ptr(c, ncells);
+    a.ncells = ncells;
+    a.B32 = c->B32.as<float>();
+    a.s32 = c->s32.as<float>();
+    a.rowcnt = c->rowcnt.as<int32_t>();
+    a.stats = stats;
+    if (nitems > 0) GP2S_TRY(dispatch_assemble<false>(c, d, a, g, sp, kp, nitems));
+    GP2S_CUDA(c, cudaEventRecord(ev[2], c->stream));
+    int64_t nnz = 0;
+    GP2S_TRY(scan_counts_i32(c, c->rowcnt.as<int32_t>(), c->rowptr.as<int32_t>(), n, &nnz));
+    int hbad = 0;
+    GP2S_CUDA(c, cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hbad) return set_err(c, GP2S_ENOTPD, "a diagonal entry of A is zero (sigma2 = 0 and the point lies outside every bump, w0 = 0)");
+
+    // ---- fill ----
+    const bool mixed = o->precision == GP2S_PREC_MIXED;
+    GP2S_TRY(ensure(c, c->col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
+    if (mixed) GP2S_TRY(ensure(c, c->val32, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1)));
+    GP2S_TRY(ensure(c, c->val64, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1)));
+    a.rowptr = c->rowptr.as<int32_t>();
+    a.col = c->col.as<int32_t>();
+    a.val = mixed ? c->val32.as<float>() : nullptr;
+    if (nitems > 0) GP2S_TRY(dispatch_assemble<true>(c, d, a, g, sp, kp, nitems));
+    GP2S_CUDA(c, cudaEventRecord(ev[3], c->stream));
+
+    // ---- FP64 values ----
+    {
+        unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 32);
+        const double4 *x64 = c->Xs64.as<double4>();
+        const int32_t *rp = c->rowptr.as<int32_t>(), *cl = c->col.as<int32_t>();
+        const double *B64 = c->B64.as<double>(), *s64 = c->s64.as<double>();
+        double *v64 = c->val64.as<double>();
+        switch (d) {
+        case 1: k_values64<1><<<gb, 256, 0, c->stream>>>(x64, rp, cl, n, kp, B64, s64, v64); break;
+        case 2: k_values64<2><<<gb, 256, 0, c->stream>>>(x64, rp, cl, n, kp, B64, s64, v64); break;
+        case 3: k_values64<3><<<gb, 256, 0, c->stream>>>(x64, rp, cl, n, kp, B64, s64, v64); break;
+        default: k_values64<4><<<gb, 256, 0, c->stream>>>(x64, rp, cl, n, kp, B64, s64, v64); break;
+        }
+        GP2S_LAUNCH(c);
+    }
+    GP2S_CUDA(c, cudaEventRecord(ev[4], c->stream));
+    {
+        int init[2] = {INT32_MAX, 0};
+        GP2S_CUDA(c, cudaMemcpyAsync(mm, init, sizeof(init), cudaMemcpyHostToDevice, c->stream));
+        unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 4);
+        k_rowcnt_minmax<<<gb, 256, 0, c->stream>>>(c->rowcnt.as<int32_t>(), n, mm);
+        GP2S_LAUNCH(c);
+    }
+    unsigned long long hstats[2];
+    int hmm[2];
+    GP2S_CUDA(c, cudaMemcpyAsync(hstats, stats, sizeof(hstats), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaMemcpyAsync(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+
+    gp2s_assemble_info &info = A.info;
+    std::memset(&info, 0, sizeof(info));
+    info.n = n;
+    info.nnz = nnz;
+    info.candidates = (int64_t)hstats[0];
+    info.band_pairs = (int64_t)hstats[1];
+    info.ncells = ncells;
+    info.nnz_row_min = hmm[0];
+    info.nnz_row_max = hmm[1];
+    info.guard_delta = delta;
+    info.cell_h = g.h;
+    cudaEventElapsedTime(&info.ms_geometry, ev[0], ev[1]);
+    cudaEventElapsedTime(&info.ms_count, ev[1], ev[2]);
+    cudaEventElapsedTime(&info.ms_fill, ev[2], ev[3]);
+    cudaEventElapsedTime(&info.ms_values64, ev[3], ev[4]);
+
+    A.n = n;
+    A.nnz = nnz;
+    A.ncells = ncells;
+    A.nitems = nitems;
+    A.d = d;
+    A.L = L;
+    A.precision = o->precision;
+    A.kp = kp;
+    A.gp = g;
+    A.sp = sp;
+    A.opts = *o;
+    A.valid = true;
+    return GP2S_OK;
+}
+
+}  // namespace gp2s

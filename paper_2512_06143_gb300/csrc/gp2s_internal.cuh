@@ -1,0 +1,190 @@
+// gp2s_internal.cuh -- shared declarations of the GB300 engine (device helpers, context, launchers).
+// Internal to the library; the public ABI is include/gp2s.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gp2s.h"
+
+namespace gp2s {
+
+constexpr int kMaxDim = 4;
+constexpr int kMaxBumps = 32;
+constexpr int kWarp = 32;
+
+// ------------------------------------------------------------------------------------------
+// Kernel hyperparameters passed by value to kernels (eq. wendland, eq. bump, Sec. 3.3).
+// ------------------------------------------------------------------------------------------
+struct KernelParams {
+    int d, L, kind, pad;
+    double r, inv_r, sigma2, beta, w0;
+    double centers[kMaxBumps * kMaxDim];
+    double radii[kMaxBumps];
+    double amps[kMaxBumps];
+};
+
+// Geometry of the cell grid: cell edge h >= r, FP64 origin, F fine bits per dimension below the
+// cell level, B bits per dimension in total (d * B <= 64).
+struct GridParams {
+    int d, fine_bits, bits, pad;
+    double origin[kMaxDim];
+    double inv_h;             // 1 / h
+    double h;
+    int64_t dims[kMaxDim];    // cells per dimension
+};
+
+// FP32 guard band of the support pre-test: accept if d2_f32 < thr_lo, reject if d2_f32 > thr_hi,
+// otherwise decide with the exact FP64 test.
+struct SupportParams {
+    float thr_lo, thr_hi;
+    double r2;                // r * r in FP64 (the exact test's threshold)
+};
+
+// ------------------------------------------------------------------------------------------
+// Device buffers (grow-only).
+// ------------------------------------------------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct HostPinned {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// The assembled single problem.
+struct Assembled {
+    bool valid = false;
+    int64_t n = 0, nnz = 0, ncells = 0, nitems = 0;
+    int d = 0, L = 0, precision = GP2S_PREC_MIXED;
+    KernelParams kp{};
+    GridParams gp{};
+    SupportParams sp{};
+    gp2s_opts opts{};
+    gp2s_assemble_info info{};
+};
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
+}  // namespace gp2s
+
+struct gp2s_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    size_t mem_limit = 0;     // GP2S_MEM_LIMIT (0 = none)
+    size_t mem_in_use = 0;
+    // geometry / sort
+    gp2s::DevBuf Xin, yin, keys, keys2, idx, idx2, perm, iperm;
+    gp2s::DevBuf Xs64, Xhi, Xlo, ys64;
+    gp2s::DevBuf bbox_part, bbox;
+    gp2s::DevBuf hist, scan_tmp, scan_tmp2;
+    gp2s::DevBuf cell_start, cell_flag, items, item_cnt;
+    // bumps / diagonal
+    gp2s::DevBuf B64, B32, D64, s64, s32;
+    // CSR
+    gp2s::DevBuf rowcnt, rowptr, col, val32, val64, counters;
+    // Krylov
+    gp2s::DevBuf vec, vec64, partials, scal, Z, rec;
+    // dense
+    gp2s::DevBuf dense;
+    // adjoint
+    gp2s::DevBuf H, gpart;
+    // host staging
+    gp2s::HostPinned hbuf;
+    gp2s::Assembled A;
+    // last solve
+    bool have_solution = false;
+    bool have_probes = false;
+    int32_t solve_iters = 0, solve_outer = 0;
+    double solve_relres = 0.0;
+    int32_t probe_iters = 0;
+    bool have_exact = false;   // dense factor of the current matrix is in `dense`
+    double exact_lhat = 0.0;   // its 2 sum log L_ii
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // launch accounting and optional SpMM timing
+    int64_t launches = 0;
+    int64_t spmm_launches = 0;
+    double spmm_bytes = 0.0;
+    bool profile = false;
+    std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop) per profiled SpMM launch
+    size_t prof_used = 0;
+    double prof_ms = 0.0;
+};
+
+namespace gp2s {
+
+// Status helpers ---------------------------------------------------------------------------
+gp2s_status set_err(gp2s_ctx *c, gp2s_status st, const std::string &msg);
+gp2s_status cuda_err(gp2s_ctx *c, cudaError_t e, const char *where);
+gp2s_status ensure(gp2s_ctx *c, DevBuf &b, size_t bytes);
+gp2s_status ensure_host(gp2s_ctx *c, HostPinned &b, size_t bytes);
+
+#define GP2S_CUDA(ctx, expr)                                     \
+    do {                                                         \
+        cudaError_t e__ = (expr);                                \
+        if (e__ != cudaSuccess) return gp2s::cuda_err((ctx), e__, #expr); \
+    } while (0)
+#define GP2S_TRY(expr)                                           \
+    do {                                                         \
+        gp2s_status s__ = (expr);                                \
+        if (s__ != GP2S_OK) return s__;                          \
+    } while (0)
+#define GP2S_LAUNCH(ctx)                                         \
+    do {                                                         \
+        ++(ctx)->launches;                                       \
+        cudaError_t e__ = cudaGetLastError();                    \
+        if (e__ != cudaSuccess) return gp2s::cuda_err((ctx), e__, "kernel launch"); \
+    } while (0)
+
+// Primitives (prim.cu) -----------------------------------------------------------------------
+// Exclusive scan of n int32 counts into out (n + 1 entries, out[n] = total), int64 accumulation.
+// *total_host receives the total (the call synchronises the stream to read it).
+gp2s_status scan_counts_i32(gp2s_ctx *c, const int32_t *in, int32_t *out, int64_t n, int64_t *total_host);
+gp2s_status scan_counts_i64(gp2s_ctx *c, const int32_t *in, int64_t *out, int64_t n, int64_t *total_host);
+// Stable LSD radix sort of (64-bit key, 32-bit value) pairs on the low `bits` key bits.
+// Results end in keys/vals (the alternate buffers are scratch of the same size).
+gp2s_status radix_sort_pairs(gp2s_ctx *c, uint64_t *keys, uint64_t *keys_alt, int32_t *vals,
+                             int32_t *vals_alt, int64_t n, int bits);
+
+// Geometry + assembly (geometry.cu, assemble.cu) ---------------------------------------------
+gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const gp2s_hyper *h,
+                             const gp2s_opts *o);
+
+// Krylov (krylov.cu) ---------------------------------------------------------------------------
+// Multi-RHS CG on the assembled Ah for the y column (scaled rhs s * y) and m probe columns.
+struct CGResult {
+    int iters_y = 0, iters_probes = 0, outer = 0;
+    double relres = 0.0;
+    gp2s_status status = GP2S_OK;
+};
+gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_probes, int m,
+                         int ksteps, CGResult *res);
+gp2s_status slq_logdet(gp2s_ctx *c, int m, int ksteps, double *logdet_hat, double *stderr_hat);
+gp2s_status exact_logdet_solve(gp2s_ctx *c, const double *y_sorted_dev, double *logdet_hat,
+                               bool want_inverse);
+// Reductions used by several stages
+gp2s_status sum_log_diag(gp2s_ctx *c, double *out_host);
+gp2s_status dot_f64(gp2s_ctx *c, const double *a, const double *b, int64_t n, double *out_host);
+
+// Adjoint (adjoint.cu) ---------------------------------------------------------------------------
+gp2s_status adjoint_gradient(gp2s_ctx *c, int m, bool exact_inverse, double *grad_host);
+
+// Batched engine (batched.cu) ----------------------------------------------------------------
+gp2s_status batched_lml(gp2s_ctx *c, int32_t B, const int64_t *n, const double *const *X,
+                        const double *const *y, const gp2s_hyper *hyper, const gp2s_opts *opts,
+                        double *lml_host, gp2s_lml_info *info_host);
+
+// Device helpers -------------------------------------------------------------------------------
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace gp2s

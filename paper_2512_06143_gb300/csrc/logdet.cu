@@ -1,0 +1,458 @@
+// logdet.cu -- log|A| (Sec. 3; the method is left open in Sec. 3.6 / App. B.7):
+//   * SLQ: stochastic Lanczos quadrature (Ubaru, Chen & Saad 2017) on Ah = D^{-1/2} A D^{-1/2}.
+//     For every probe z_s the tridiagonal T_s comes from the recorded CG coefficients (CG-Lanczos
+//     relation); its eigenvalues theta_j and eigenvector first components tau_j come from an
+//     implicit-shift symmetric tridiagonal QR iteration with Wilkinson shifts (Golub & Van Loan,
+//     Sec. 8.3), one thread per probe in FP64, and log|Ah| ~= (n/m) sum_s sum_j tau_sj^2 log theta_sj.
+//   * EXACT: dense FP64 Cholesky of Ah (right-looking, 32-wide panels: diagonal-block factor,
+//     panel triangular solve, symmetric rank-32 update of the trailing lower triangle), then
+//     log|Ah| = 2 sum log L_ii and the y solve by forward/backward substitution.
+//   log|A| = sum log D_ii + log|Ah| in both cases.
+#include <cmath>
+#include <cstring>
+
+#include "gp2s_internal.cuh"
+
+namespace gp2s {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Symmetric tridiagonal eigenvalues + first eigenvector components, implicit QR with Wilkinson
+// shift and bulge chasing, deflating negligible off-diagonals.  a: diagonal (k), b: off-diagonal
+// (k - 1), q: first row of the accumulated rotations (k).  Returns false if it fails to converge.
+// ---------------------------------------------------------------------------------------------
+__host__ __device__ bool tridiag_eig(double *a, double *b, double *q, int k)
+{
+    const double eps = 2.220446049250313e-16;
+    for (int i = 0; i < k; ++i) q[i] = i == 0 ? 1.0 : 0.0;
+    int hi = k - 1;
+    int guard = 0;
+    while (hi > 0) {
+        // deflate from the bottom
+        if (fabs(b[hi - 1]) <= eps * (fabs(a[hi - 1]) + fabs(a[hi]))) {
+            b[hi - 1] = 0.0;
+            --hi;
+            continue;
+        }
+        // start of the unreduced block ending at hi
+        int lo = hi - 1;
+        while (lo > 0 && fabs(b[lo - 1]) > eps * (fabs(a[lo - 1]) + fabs(a[lo]))) --lo;
+        if (lo > 0) b[lo - 1] = 0.0;
+        if (++guard > 60 * k) return false;
+        // Wilkinson shift from the trailing 2x2 block
+        const double bb = b[hi - 1];
+        const double dd = 0.5 * (a[hi - 1] - a[hi]);
+        const double rr = hypot(dd, bb);
+        const double mu = a[hi] - bb * bb / (dd + (dd >= 0.0 ? rr : -rr));
+        // bulge chase over [lo, hi]
+        double x = a[lo] - mu, z = b[lo];
+        for (int j = lo; j < hi; ++j) {
+            double r = hypot(x, z);
+            double c = r > 0.0 ? x / r : 1.0;
+            double s = r > 0.0 ? -z / r : 0.0;
+            if (j > lo) b[j - 1] = r;   // the rotation folds the bulge into b[j-1]
+            // 2x2 similarity on rows/cols j, j+1 with P = [[c, s], [-s, c]]
+            const double aj = a[j], aj1 = a[j + 1], bj = b[j];
+            const double cc = c * c, ss = s * s, cs = c * s;
+            a[j] = aj * cc - 2.0 * bj * cs + aj1 * ss;
+            a[j + 1] = aj * ss + 2.0 * bj * cs + aj1 * cc;
+            b[j] = (aj - aj1) * cs + bj * (cc - ss);
+            if (j + 1 < hi) {
+                // the next off-diagonal b[j+1] is rotated into the new bulge at (j + 2, j)
+                x = b[j];
+                z = -s * b[j + 1];
+                b[j + 1] = c * b[j + 1];
+            }
+            // accumulate the first row of Q <- Q P
+            const double qj = q[j], qj1 = q[j + 1];
+            q[j] = qj * c - qj1 * s;
+            q[j + 1] = qj * s + qj1 * c;
+        }
+    }
+    return true;
+}
+
+// One thread per probe: T from CG coefficients, eigen-decomposition, Gauss quadrature of log.
+__global__ void k_slq(const double *__restrict__ rec, const double *__restrict__ sc, int m, int ksteps,
+                      double *__restrict__ work, double *__restrict__ out, int *__restrict__ bad)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= m) return;
+    double *a = work + (int64_t)s * 3 * ksteps;
+    double *b = a + ksteps;
+    double *q = b + ksteps;
+    // number of recorded steps for this probe column (column s + 1 of the CG scalar block)
+    int steps = (int)sc[(s + 1) * 8 + 6];
+    int k = steps < ksteps ? steps : ksteps;
+    if (k <= 0) { out[s] = 0.0; atomicOr(bad, 1); return; }
+    const double *al = rec + (int64_t)s * ksteps * 2;
+    // CG-Lanczos relation: T_00 = 1/alpha_0; T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1};
+    // T_{j,j+1} = sqrt(beta_j)/alpha_j
+    for (int j = 0; j < k; ++j) {
+        double aj = al[2 * j];
+        a[j] = 1.0 / aj + (j > 0 ? al[2 * (j - 1) + 1] / al[2 * (j - 1)] : 0.0);
+        if (j + 1 < k) b[j] = sqrt(al[2 * j + 1]) / aj;
+    }
+    if (!tridiag_eig(a, b, q, k)) { out[s] = nan(""); atomicOr(bad, 2); return; }
+    double g = 0.0;
+    for (int j = 0; j < k; ++j) {
+        if (!(a[j] > 0.0)) { atomicOr(bad, 4); out[s] = nan(""); return; }
+        g += q[j] * q[j] * log(a[j]);
+    }
+    out[s] = g;
+}
+
+__global__ void k_sum_log(const double *__restrict__ D, int64_t n, double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += log(D[i]);
+    s = warp_sum_d(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void k_dot64(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                        double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s = fma(a[i], b[i], s);
+    s = warp_sum_d(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dense FP64 Cholesky (lower, column-major-free: row-major n x n, only the lower triangle used)
+// ---------------------------------------------------------------------------------------------
+constexpr int NB = 32;
+
+__global__ void k_densify(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                          const double *__restrict__ val, int64_t n, double *__restrict__ Ad)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n; i += nw)
+        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) Ad[i * n + col[p]] = val[p];
+}
+
+// Factor the NB x NB diagonal block at (kb, kb) in shared memory.
+__global__ void k_potrf_diag(double *__restrict__ Ad, int64_t n, int kb, int *__restrict__ bad)
+{
+    __shared__ double S[NB][NB + 1];
+    const int nbk = (int)(n - kb < NB ? n - kb : NB);
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        int i = t / NB, j = t % NB;
+        S[i][j] = (i < nbk && j < nbk) ? Ad[(int64_t)(kb + i) * n + kb + j] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < nbk; ++j) {
+        if (threadIdx.x == 0) {
+            double d = S[j][j];
+            if (!(d > 0.0)) { atomicOr(bad, 1); d = 1.0; }
+            S[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < nbk; i += blockDim.x) S[i][j] /= S[j][j];
+        __syncthreads();
+        for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
+            int i = t / nbk, l = t % nbk;
+            if (i > j && l > j && l <= i) S[i][l] -= S[i][j] * S[l][j];
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < nbk * nbk; t += blockDim.x) {
+        int i = t / nbk, j = t % nbk;
+        if (j <= i) Ad[(int64_t)(kb + i) * n + kb + j] = S[i][j];
+    }
+}
+
+// Panel: rows r >= kb + NB, columns kb..kb+NB: L21 = A21 L11^{-T}.  One thread per row.
+__global__ void k_trsm_panel(double *__restrict__ Ad, int64_t n, int kb)
+{
+    __shared__ double Lk[NB][NB + 1];
+    const int nbk = (int)(n - kb < NB ? n - kb : NB);
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        int i = t / NB, j = t % NB;
+        Lk[i][j] = (i < nbk && j <= i) ? Ad[(int64_t)(kb + i) * n + kb + j] : 0.0;
+    }
+    __syncthreads();
+    int64_t r = kb + nbk + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double x[NB];
+    double *row = Ad + r * n + kb;
+    for (int j = 0; j < nbk; ++j) {
+        double v = row[j];
+        for (int l = 0; l < j; ++l) v -= x[l] * Lk[j][l];
+        x[j] = v / Lk[j][j];
+    }
+    for (int j = 0; j < nbk; ++j) row[j] = x[j];
+}
+
+// Trailing update of the lower triangle: A[i][j] -= sum_l L[i][kb+l] L[j][kb+l] for
+// i >= j >= kb + NB.  64 x 64 output tiles, 256 threads, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) k_syrk(double *__restrict__ Ad, int64_t n, int kb)
+{
+    const int64_t t0 = kb + NB;
+    const int64_t ti = t0 + (int64_t)blockIdx.y * 64, tj = t0 + (int64_t)blockIdx.x * 64;
+    if (tj > ti + 63) return;   // strictly upper tile
+    __shared__ double Li[64][NB + 1], Lj[64][NB + 1];
+    const int nbk = (int)(n - kb < NB ? n - kb : NB);
+    for (int t = threadIdx.x; t < 64 * NB; t += blockDim.x) {
+        int r = t / NB, l = t % NB;
+        Li[r][l] = (ti + r < n && l < nbk) ? Ad[(ti + r) * n + kb + l] : 0.0;
+        Lj[r][l] = (tj + r < n && l < nbk) ? Ad[(tj + r) * n + kb + l] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int l = 0; l < nbk; ++l) {
+        double vi[4], vj[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { vi[a] = Li[ty + 16 * a][l]; vj[a] = Lj[tx + 16 * a][l]; }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(vi[a], vj[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int64_t i = ti + ty + 16 * a, j = tj + tx + 16 * b;
+            if (i < n && j <= i) Ad[i * n + j] -= acc[a][b];
+        }
+}
+
+__global__ void k_logdiag(const double *__restrict__ Ad, int64_t n, double *__restrict__ part)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += log(Ad[i * n + i]);
+    s = warp_sum_d(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Forward substitution L z = b, block kb: solve the NB x NB diagonal block (one CTA).
+__global__ void k_trsv_diag(const double *__restrict__ Ad, int64_t n, int kb, double *__restrict__ x, int trans)
+{
+    __shared__ double xs[NB];
+    const int nbk = (int)(n - kb < NB ? n - kb : NB);
+    if (threadIdx.x == 0) {
+        if (!trans) {
+            for (int j = 0; j < nbk; ++j) {
+                double v = x[kb + j];
+                for (int l = 0; l < j; ++l) v -= Ad[(int64_t)(kb + j) * n + kb + l] * xs[l];
+                xs[j] = v / Ad[(int64_t)(kb + j) * n + kb + j];
+            }
+        } else {
+            for (int j = nbk - 1; j >= 0; --j) {
+                double v = x[kb + j];
+                for (int l = j + 1; l < nbk; ++l) v -= Ad[(int64_t)(kb + l) * n + kb + j] * xs[l];
+                xs[j] = v / Ad[(int64_t)(kb + j) * n + kb + j];
+            }
+        }
+        for (int j = 0; j < nbk; ++j) x[kb + j] = xs[j];
+    }
+}
+
+// Forward: x[i] -= sum_l L[i][kb+l] x[kb+l] for i >= kb + NB (one warp per row).
+// Backward (trans): x[j] -= sum_l L[kb+l][j] x[kb+l] for j < kb (one thread per column j).
+__global__ void k_trsv_update(const double *__restrict__ Ad, int64_t n, int kb, double *__restrict__ x, int trans)
+{
+    const int nbk = (int)(n - kb < NB ? n - kb : NB);
+    if (!trans) {
+        const int lane = threadIdx.x & 31;
+        const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t i = kb + nbk + w0; i < n; i += nw) {
+            double v = lane < nbk ? Ad[i * n + kb + lane] * x[kb + lane] : 0.0;
+            v = warp_sum_d(v);
+            if (lane == 0) x[i] -= v;
+        }
+    } else {
+        for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < kb; j += (int64_t)gridDim.x * blockDim.x) {
+            double v = 0.0;
+            for (int l = 0; l < nbk; ++l) v = fma(Ad[(int64_t)(kb + l) * n + j], x[kb + l], v);
+            x[j] -= v;
+        }
+    }
+}
+
+__global__ void k_gp2s_mul(int64_t n, const double *a, const double *b, double *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] * b[i];
+}
+
+gp2s_status reduce_parts(gp2s_ctx *c, const double *part, int cnt, double *out_host)
+{
+    std::vector<double> h(cnt);
+    GP2S_CUDA(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    double s = 0.0;
+    for (int k = 0; k < cnt; ++k) s += h[k];
+    *out_host = s;
+    return GP2S_OK;
+}
+
+}  // namespace
+
+gp2s_status sum_log_diag(gp2s_ctx *c, double *out_host)
+{
+    const int nb = 152 * 2;
+    GP2S_TRY(ensure(c, c->gpart, sizeof(double) * (2 * nb + 8)));
+    k_sum_log<<<nb, 256, 0, c->stream>>>(c->D64.as<double>(), c->A.n, c->gpart.as<double>());
+    GP2S_LAUNCH(c);
+    return reduce_parts(c, c->gpart.as<double>(), nb, out_host);
+}
+
+gp2s_status dot_f64(gp2s_ctx *c, const double *a, const double *b, int64_t n, double *out_host)
+{
+    const int nb = 152 * 2;
+    GP2S_TRY(ensure(c, c->gpart, sizeof(double) * (2 * nb + 8)));
+    k_dot64<<<nb, 256, 0, c->stream>>>(a, b, n, c->gpart.as<double>());
+    GP2S_LAUNCH(c);
+    return reduce_parts(c, c->gpart.as<double>(), nb, out_host);
+}
+
+gp2s_status slq_logdet(gp2s_ctx *c, int m, int ksteps, double *logdet_hat, double *stderr_hat)
+{
+    if (m <= 0 || !c->have_probes) return set_err(c, GP2S_ENOTREADY, "SLQ needs the probe CG run");
+    GP2S_TRY(ensure(c, c->dense, sizeof(double) * ((size_t)m * 3 * ksteps + m + 8)));
+    double *work = c->dense.as<double>();
+    double *out = work + (size_t)m * 3 * ksteps;
+    int *bad = reinterpret_cast<int *>(out + m);
+    GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    k_slq<<<(m + 31) / 32, 32, 0, c->stream>>>(c->rec.as<double>(), c->scal.as<double>(), m, ksteps, work, out, bad);
+    GP2S_LAUNCH(c);
+    std::vector<double> g(m);
+    int hbad = 0;
+    GP2S_CUDA(c, cudaMemcpyAsync(g.data(), out, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hbad) return set_err(c, GP2S_EBREAKDOWN, "SLQ: tridiagonal eigensolve failed or non-positive Ritz value");
+    const double n = (double)c->A.n;
+    double mean = 0.0;
+    for (int s = 0; s < m; ++s) mean += n * g[s];
+    mean /= m;
+    double var = 0.0;
+    for (int s = 0; s < m; ++s) var += (n * g[s] - mean) * (n * g[s] - mean);
+    var = m > 1 ? var / (m - 1) : 0.0;
+    *logdet_hat = mean;
+    if (stderr_hat) *stderr_hat = std::sqrt(var / m);
+    return GP2S_OK;
+}
+
+gp2s_status exact_logdet_solve(gp2s_ctx *c, const double *y_sorted_dev, double *logdet_hat, bool want_inverse)
+{
+    (void)want_inverse;
+    const Assembled &A = c->A;
+    const int64_t n = A.n;
+    const size_t bytes = sizeof(double) * (size_t)n * (size_t)n;
+    GP2S_TRY(ensure(c, c->dense, bytes + 64));
+    double *Ad = c->dense.as<double>();
+    GP2S_CUDA(c, cudaMemsetAsync(Ad, 0, bytes, c->stream));
+    {
+        unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 16);
+        k_densify<<<gb, 256, 0, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val64.as<double>(), n, Ad);
+        GP2S_LAUNCH(c);
+    }
+    GP2S_TRY(ensure(c, c->counters, 256));
+    int *bad = reinterpret_cast<int *>(c->counters.as<char>() + 192);
+    GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    for (int64_t kb = 0; kb < n; kb += NB) {
+        k_potrf_diag<<<1, 256, 0, c->stream>>>(Ad, n, (int)kb, bad);
+        GP2S_LAUNCH(c);
+        int64_t rest = n - kb - NB;
+        if (rest > 0) {
+            k_trsm_panel<<<(unsigned)ceil_div(rest, 64), 64, 0, c->stream>>>(Ad, n, (int)kb);
+            GP2S_LAUNCH(c);
+            unsigned tiles = (unsigned)ceil_div(rest, 64);
+            k_syrk<<<dim3(tiles, tiles), 256, 0, c->stream>>>(Ad, n, (int)kb);
+            GP2S_LAUNCH(c);
+        }
+    }
+    int hbad = 0;
+    GP2S_CUDA(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hbad) return set_err(c, GP2S_ENOTPD, "dense Cholesky: non-positive pivot");
+    const int nb = 152 * 2;
+    GP2S_TRY(ensure(c, c->gpart, sizeof(double) * (2 * nb + 8)));
+    k_logdiag<<<nb, 256, 0, c->stream>>>(Ad, n, c->gpart.as<double>());
+    GP2S_LAUNCH(c);
+    double half = 0.0;
+    GP2S_TRY(reduce_parts(c, c->gpart.as<double>(), nb, &half));
+    *logdet_hat = 2.0 * half;
+    c->have_exact = true;
+    c->exact_lhat = *logdet_hat;
+
+    if (y_sorted_dev) {
+        // a = s * (Ah^{-1} (s * y)) by forward / backward substitution in vec64 slot 3
+        GP2S_TRY(ensure(c, c->vec64, sizeof(double) * (size_t)n * 4 + 256));
+        double *b64 = c->vec64.as<double>();
+        double *xh = b64 + n, *a64 = b64 + 3 * n;
+        GP2S_TRY(ensure(c, c->gpart, sizeof(double) * (2 * nb + 8)));
+        const unsigned gbn = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+        // b64 = s * y ; xh = b64
+        k_gp2s_mul<<<gbn, 256, 0, c->stream>>>(n, c->s64.as<double>(), y_sorted_dev, b64);
+        GP2S_LAUNCH(c);
+        GP2S_CUDA(c, cudaMemcpyAsync(xh, b64, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        const unsigned gbu = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 8);
+        for (int64_t kb = 0; kb < n; kb += NB) {
+            k_trsv_diag<<<1, 32, 0, c->stream>>>(Ad, n, (int)kb, xh, 0);
+            GP2S_LAUNCH(c);
+            if (kb + NB < n) {
+                k_trsv_update<<<gbu, 256, 0, c->stream>>>(Ad, n, (int)kb, xh, 0);
+                GP2S_LAUNCH(c);
+            }
+        }
+        for (int64_t kb = ((n - 1) / NB) * NB; kb >= 0; kb -= NB) {
+            k_trsv_diag<<<1, 32, 0, c->stream>>>(Ad, n, (int)kb, xh, 1);
+            GP2S_LAUNCH(c);
+            if (kb > 0) {
+                k_trsv_update<<<gbn, 256, 0, c->stream>>>(Ad, n, (int)kb, xh, 1);
+                GP2S_LAUNCH(c);
+            }
+        }
+        k_gp2s_mul<<<gbn, 256, 0, c->stream>>>(n, c->s64.as<double>(), xh, a64);
+        GP2S_LAUNCH(c);
+        c->have_solution = true;
+    }
+    return GP2S_OK;
+}
+
+}  // namespace gp2s

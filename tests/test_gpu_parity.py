@@ -1,0 +1,280 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI (gp2s_* in libgp2s.so).
+
+Tolerances (written here, derived in the design doc):
+  * pattern: identical sets of (row, column) pairs (bit-exact, FP64 support test on both sides);
+  * FP64 values: max |dA| <= 1e-12 max |A|;
+  * FP32 values (MIXED): max |dA| <= 1e-6 max |A| and |dA|_F <= 1e-6 |A|_F;
+  * solve: |y - A_oracle a| / |y| <= 1e-8 with the oracle's FP64 A;
+  * log-determinant: 1e-10 relative (exact path), 1e-3 relative with identical probes (SLQ);
+  * gradient: Hutchinson with identical probes, max |dg| <= 1e-3 max |g| (FP32 probe solves).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2512_06143_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_06143_gb300 as gp
+    from paper_2512_06143_gb300 import build
+    build.build()
+    gp.load()
+    return gp
+
+
+@pytest.fixture(scope="module")
+def ctx(gp):
+    return gp.Context(0)
+
+
+def _csr_orig(c):
+    """GPU CSR (sorted numbering) -> sorted arrays of original (row, col) keys and FP64 A values."""
+    rp = c["rowptr"].cpu().numpy().astype(np.int64)
+    col = c["col"].cpu().numpy().astype(np.int64)
+    perm = c["perm"].cpu().numpy().astype(np.int64)
+    s = c["dscale"].cpu().numpy()
+    n = rp.shape[0] - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    A64 = c["val64"].cpu().numpy() / (s[rows] * s[col])
+    A32 = None
+    if c["val32"] is not None:
+        A32 = c["val32"].cpu().numpy().astype(np.float64) / (s[rows] * s[col])
+    key = perm[rows] * n + perm[col]
+    order = np.argsort(key, kind="stable")
+    return key[order], A64[order], (A32[order] if A32 is not None else None), rp, col
+
+
+def _oracle_keys(csr):
+    n = csr.n
+    rows = np.repeat(np.arange(n), np.diff(csr.rowptr))
+    return rows.astype(np.int64) * n + csr.col.astype(np.int64), csr.val
+
+
+def _check_assembly(gp, ctx, w, exact_support=0, precision=None, method="auto"):
+    import oracle
+    h = gp.Hyper(**w["hyper"])
+    opts = gp.default_opts(exact_support=exact_support)
+    if precision is not None:
+        opts.precision = precision
+    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
+    info = ctx.assemble(X, h, opts)
+    c = ctx.csr()
+    key, A64, A32, rp, col = _csr_orig(c)
+    ho = oracle.Hyper(**w["hyper"])
+    ocsr = oracle.assemble(w["X"], ho, method)
+    okey, oval = _oracle_keys(ocsr)
+    assert info["nnz"] == ocsr.nnz
+    assert np.array_equal(key, okey), "pattern differs from the oracle"
+    amax = np.abs(oval).max()
+    assert np.abs(A64 - oval).max() <= 1e-12 * amax
+    if A32 is not None:
+        d = A32 - oval
+        assert np.abs(d).max() <= 1e-6 * amax
+        assert np.linalg.norm(d) <= 1e-6 * np.linalg.norm(oval)
+    # columns ascending within each sorted row, diagonal of Ah exactly 1
+    n = rp.shape[0] - 1
+    for i in range(0, n, max(1, n // 97)):
+        cc = col[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(cc) > 0)
+    v64 = c["val64"].cpu().numpy()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    assert np.all(v64[rows == col] == 1.0)
+    return info
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_assembly_random_dims(gp, ctx, d):
+    w = W.random_small(100 + d, 6000 + 37 * d, d, L=3, clustered=(d % 2 == 1))
+    _check_assembly(gp, ctx, w)
+
+
+def test_assembly_paper_wendland_and_w0(gp, ctx):
+    w = W.random_small(201, 5000, 3, L=2, kind=1, w0=0.5)
+    _check_assembly(gp, ctx, w)
+
+
+def test_assembly_small_2d_workload(gp, ctx):
+    info = _check_assembly(gp, ctx, W.small_2d(0))
+    assert 25 < info["nnz"] / info["n"] < 40
+
+
+def test_assembly_guard_band_off_gives_identical_pattern(gp, ctx):
+    w = W.random_small(202, 8000, 3, clustered=True)
+    a = _check_assembly(gp, ctx, w, exact_support=0)
+    b = _check_assembly(gp, ctx, w, exact_support=1)
+    assert a["nnz"] == b["nnz"]
+    assert b["band_pairs"] >= b["candidates"] - b["n"] - 1 or b["band_pairs"] > a["band_pairs"]
+
+
+def test_assembly_fp64_precision(gp, ctx):
+    w = W.random_small(203, 4000, 2)
+    _check_assembly(gp, ctx, w, precision=gp.PREC_FP64)
+
+
+def test_assembly_exact_boundary_grid(gp, ctx):
+    # 2-D grid with spacing 1/8, r = 1/4: pairs at distance exactly r are excluded (strict <)
+    g = np.arange(40) / 8.0
+    X = np.array([[a, b] for a in g for b in g])
+    w = dict(X=X, y=np.zeros(len(X)), hyper=dict(d=2, r=0.25, sigma2=1e-2, centers=np.array([[2.0, 2.0]]),
+                                                  radii=np.array([3.0]), amps=np.array([1.0]), beta=1.0, w0=0.0,
+                                                  kind=0))
+    info = _check_assembly(gp, ctx, w)
+    assert info["nnz"] < 9 * len(X)
+
+
+def test_assembly_degenerate_inputs(gp, ctx):
+    rng = np.random.default_rng(5)
+    hyper = dict(d=3, r=0.3, sigma2=1e-2, centers=np.array([[0.5, 0.5, 0.5]]), radii=np.array([2.0]),
+                 amps=np.array([1.0]), beta=1.0, w0=0.0, kind=0)
+    # one point, two points
+    for n in (1, 2):
+        X = rng.random((n, 3))
+        _check_assembly(gp, ctx, dict(X=X, hyper=hyper))
+    # duplicates and everything inside one cell
+    X = rng.random((300, 3)) * 0.05
+    X[100:150] = X[0]
+    _check_assembly(gp, ctx, dict(X=X, hyper=hyper))
+    # points on cell boundaries (coordinates multiples of r)
+    X = np.floor(rng.random((2000, 3)) * 10) * 0.3
+    X = X + rng.integers(0, 2, (2000, 3)) * 1e-17
+    _check_assembly(gp, ctx, dict(X=X, hyper=hyper))
+
+
+def test_assembly_clusters_3d_full_size_sampled_rows(gp, ctx):
+    """1M-point clustered workload (the benchmark's configuration): GPU rows vs oracle brute force
+    on sampled rows; pattern bit-exact, values within tolerance."""
+    import oracle
+    w = W.clusters_3d(0)
+    h = gp.Hyper(**w["hyper"])
+    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
+    info = ctx.assemble(X, h, gp.default_opts())
+    assert 85 < info["nnz"] / info["n"] < 115
+    c = ctx.csr()
+    rp = c["rowptr"].cpu().numpy().astype(np.int64)
+    col = c["col"].cpu().numpy().astype(np.int64)
+    perm = c["perm"].cpu().numpy().astype(np.int64)
+    s = c["dscale"].cpu().numpy()
+    v32 = c["val32"].cpu().numpy().astype(np.float64)
+    v64 = c["val64"].cpu().numpy()
+    iperm = np.empty_like(perm)
+    iperm[perm] = np.arange(len(perm))
+    rng = np.random.default_rng(1)
+    rows = rng.choice(len(perm), 96, replace=False)
+    ho = oracle.Hyper(**w["hyper"])
+    ref = oracle.rows_brute(w["X"], ho, rows)
+    for r, (oc, ov) in zip(rows, ref):
+        i = iperm[r]
+        cs = col[rp[i]:rp[i + 1]]
+        oc_g = np.sort(perm[cs])
+        assert np.array_equal(oc_g, oc)
+        order = np.argsort(perm[cs])
+        a64 = v64[rp[i]:rp[i + 1]][order] / (s[i] * s[cs][order])
+        a32 = v32[rp[i]:rp[i + 1]][order] / (s[i] * s[cs][order])
+        scale = max(np.abs(ov).max(), 1e-300)
+        assert np.abs(a64 - ov).max() <= 1e-12 * scale
+        assert np.abs(a32 - ov).max() <= 1e-6 * scale
+
+
+# ------------------------------------------------------------------------------------------------
+# Solve, log-determinant, LML, gradient
+# ------------------------------------------------------------------------------------------------
+def _oracle_residual(w, a):
+    import oracle
+    ho = oracle.Hyper(**w["hyper"])
+    csr = oracle.assemble(w["X"], ho)
+    return np.linalg.norm(w["y"] - csr.matmat(a)) / np.linalg.norm(w["y"])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_solve_reaches_refined_residual(gp, ctx, precision):
+    w = W.random_small(300, 12000, 3, L=3, sigma2=1e-3, clustered=True)
+    h = gp.Hyper(**w["hyper"])
+    opts = gp.default_opts(precision=gp.PREC_MIXED if precision == "mixed" else gp.PREC_FP64)
+    ctx.assemble(torch.tensor(w["X"], device="cuda"), h, opts)
+    a, info = ctx.solve(torch.tensor(w["y"], device="cuda"))
+    a = a.cpu().numpy()
+    assert info["relres"] <= 1e-8
+    assert _oracle_residual(w, a) <= 1e-8
+
+
+def test_lml_exact_small_2d_matches_oracle(gp, ctx):
+    import oracle
+    w = W.small_2d(0)
+    h = gp.Hyper(**w["hyper"])
+    opts = gp.default_opts(precision=gp.PREC_FP64, logdet=gp.LOGDET_EXACT)
+    lml, info = ctx.lml(w["X"], w["y"], h, opts)
+    e = oracle.lml_exact(w["X"], w["y"], oracle.Hyper(**w["hyper"]))
+    assert info["logdet"] == pytest.approx(e["logdet"], rel=1e-10)
+    assert info["quad"] == pytest.approx(e["quad"], rel=1e-8)
+    assert lml == pytest.approx(e["lml"], rel=1e-8)
+    assert info["relres"] <= 1e-8
+
+
+def test_logdet_slq_matches_oracle_with_identical_probes(gp, ctx):
+    import oracle
+    w = W.random_small(301, 6000, 2, L=3, sigma2=1e-3)
+    h = gp.Hyper(**w["hyper"])
+    opts = gp.default_opts(logdet=gp.LOGDET_SLQ, probes=32, lanczos_steps=60, seed=11)
+    lml, info = ctx.lml(w["X"], w["y"], h, opts)
+    s = oracle.lml_slq(w["X"], w["y"], oracle.Hyper(**w["hyper"]), m=32, k=60, seed=11, grad=False)
+    assert info["logdet"] == pytest.approx(s["logdet"], rel=1e-3)
+    assert info["quad"] == pytest.approx(s["quad"], rel=1e-7)
+    assert lml == pytest.approx(s["lml"], rel=1e-3)
+    # and the estimate is within a few standard errors of the exact value
+    e = oracle.lml_exact(w["X"], w["y"], oracle.Hyper(**w["hyper"]))
+    assert abs(info["logdet"] - e["logdet"]) <= 5 * info["logdet_stderr"] + 1e-9 * abs(e["logdet"])
+
+
+def test_gradient_matches_oracle_hutchinson(gp, ctx):
+    import oracle
+    w = W.random_small(302, 4000, 2, L=3, sigma2=1e-3)
+    h = gp.Hyper(**w["hyper"])
+    opts = gp.default_opts(probes=32, lanczos_steps=50, seed=5, tol_probe=1e-6)
+    lml, g, info = ctx.lml_grad(w["X"], w["y"], h, opts)
+    s = oracle.lml_slq(w["X"], w["y"], oracle.Hyper(**w["hyper"]), m=32, k=50, seed=5)
+    gref = s["grad"]
+    assert np.abs(g - gref).max() <= 1e-3 * np.abs(gref).max()
+
+
+def test_autograd_function(gp, ctx):
+    w = W.random_small(303, 3000, 2, L=2, sigma2=1e-3)
+    h = gp.Hyper(**w["hyper"])
+    theta = torch.tensor(h.theta(), dtype=torch.float64, requires_grad=True)
+    X = torch.tensor(w["X"], device="cuda")
+    y = torch.tensor(w["y"], device="cuda")
+    opts = gp.default_opts(probes=32, seed=2)
+    out = gp.GP2SLML.apply(theta, X, y, h, opts)
+    out.backward()
+    lml, g, _ = ctx.lml_grad(X, y, h, opts)
+    assert float(out) == pytest.approx(lml, rel=1e-12)
+    np.testing.assert_allclose(theta.grad.numpy(), g, rtol=1e-12)
+
+
+def test_invalid_arguments_are_reported(gp, ctx):
+    w = W.random_small(304, 100, 2)
+    h = gp.Hyper(**w["hyper"])
+    bad = gp.Hyper(**{**w["hyper"], "r": -1.0})
+    with pytest.raises(gp.GP2SError) as e:
+        ctx.assemble(w["X"], bad)
+    assert e.value.status == gp.EINVAL
+    X = w["X"].copy()
+    X[3, 1] = np.nan
+    with pytest.raises(gp.GP2SError) as e:
+        ctx.assemble(X, h)
+    assert e.value.status == gp.EINVAL
+    with pytest.raises(gp.GP2SError) as e:
+        ctx.lml(w["X"], w["y"], h, gp.default_opts(probes=33))
+    assert e.value.status == gp.EINVAL
+    # a zero diagonal (sigma2 = 0, point outside every bump, w0 = 0) is not positive definite
+    far = gp.Hyper(**{**w["hyper"], "sigma2": 0.0, "centers": np.full((3, 2), 50.0)})
+    with pytest.raises(gp.GP2SError) as e:
+        ctx.assemble(w["X"], far)
+    assert e.value.status == gp.ENOTPD
