@@ -353,7 +353,7 @@ class _CudaArray:
     """A borrowed 1-D device buffer exposed through __cuda_array_interface__ (so torch can view it)."""
 
     def __init__(self, ptr: int, count: int, typestr: str):
-        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 2, "strides": None}
 
 
