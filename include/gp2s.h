@@ -235,6 +235,35 @@ gp2s_status gp2s_lml_batched(gp2s_ctx *ctx, int32_t B, const int64_t *n, const d
                              const double *const *y, const gp2s_hyper *hyper,
                              const gp2s_opts *opts, double *lml_host, gp2s_lml_info *info_host);
 
+/*
+ * Allocation-free exact LML for small problems.  The paper has no counterpart: this is a service
+ * entry point for callers that cannot allocate device memory, e.g. code that issues work while a
+ * CUDA stream is being captured into a graph (cudaMalloc is not allowed there), or a process whose
+ * device memory is entirely reserved by another allocator (a framework's caching pool, a serving
+ * runtime with a fixed budget) so that the library must not create allocations of its own.
+ *
+ * It computes what gp2s_lml computes with GP2S_PREC_FP64 and GP2S_LOGDET_EXACT, for n <=
+ * GP2S_NOALLOC_MAX_N points: the dense FP64 matrix A = K + sigma2 I (same exact support test and
+ * kernel as the CSR path), its Cholesky factor, log|A|, a = A^{-1} y, and the LML.  All scratch
+ * lives in one fixed-size array compiled into the library (about 2.1 MB of every GPU that loads the
+ * library, held until the process exits); the call makes no cudaMalloc / cudaFree and calls no
+ * allocating library routine.
+ *   n: 1..GP2S_NOALLOC_MAX_N; larger n returns GP2S_EINVAL and does nothing.
+ *   X_dev (n x d FP64), y_dev (n FP64): DEVICE pointers, original point order.
+ *   hyper: host, as for gp2s_lml.
+ *   out_dev: DEVICE pointer to 3 doubles receiving {LML, y^T A^{-1} y, log|A|}; NaN if a Cholesky
+ *   pivot is not positive.
+ *   cuda_stream: the stream all work is issued on (NULL = legacy default stream).
+ * The call is asynchronous: it returns after queueing the work on cuda_stream.  The first call on
+ * each device looks up the scratch array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture begins.  Every call on a device shares
+ * the one scratch array and leaves its contents behind: calls whose work overlaps on the GPU (two
+ * streams, or two host threads) race and give wrong results, so serialise them.
+ */
+#define GP2S_NOALLOC_MAX_N 512
+gp2s_status gp2s_lml_exact_noalloc(int64_t n, const double *X_dev, const double *y_dev,
+                                   const gp2s_hyper *hyper, double *out_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

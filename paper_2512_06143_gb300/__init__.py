@@ -85,7 +85,7 @@ class CsrView(ctypes.Structure):
 
 EXPORTED = ["gp2s_opts_default", "gp2s_num_params", "gp2s_create", "gp2s_destroy", "gp2s_last_error",
             "gp2s_assemble", "gp2s_csr", "gp2s_solve", "gp2s_logdet", "gp2s_lml", "gp2s_lml_grad",
-            "gp2s_lml_batched"]
+            "gp2s_lml_batched", "gp2s_lml_exact_noalloc"]
 
 _lib = None
 
@@ -124,6 +124,7 @@ def load(path: str | None = None):
         "gp2s_lml": (i32, [vp, i64, vp, vp, vp, vp, vp, vp]),
         "gp2s_lml_grad": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, vp]),
         "gp2s_lml_batched": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
+        "gp2s_lml_exact_noalloc": (i32, [i64, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)

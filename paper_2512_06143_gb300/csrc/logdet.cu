@@ -10,8 +10,10 @@
 //   log|A| = sum log D_ii + log|Ah| in both cases.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "gp2s_internal.cuh"
+#include "gp2s_kernel_math.cuh"
 
 namespace gp2s {
 
@@ -456,3 +458,188 @@ gp2s_status exact_logdet_solve(gp2s_ctx *c, const double *y_sorted_dev, double *
 }
 
 }  // namespace gp2s
+
+// =============================================================================================
+// Allocation-free exact LML for small problems (gp2s_lml_exact_noalloc).
+//
+// For callers that may not allocate device memory (work issued during CUDA stream capture, or a
+// device whose memory is owned by another allocator), every intermediate of this path lives in one
+// fixed array compiled into the library.  The dense matrix is built pair by pair with the same
+// exact FP64 support test and FP64 kernel value as the CSR path, then factored by the same blocked
+// Cholesky kernels as the EXACT log-determinant above.
+// =============================================================================================
+namespace gp2s {
+
+namespace {
+
+constexpr int kNoAllocMaxN = GP2S_NOALLOC_MAX_N;
+constexpr size_t kNoAllocA = (size_t)kNoAllocMaxN * kNoAllocMaxN;              // dense A / its factor
+constexpr size_t kNoAllocX = kNoAllocA;                                          // y, then a = A^{-1} y
+constexpr size_t kNoAllocB = kNoAllocX + kNoAllocMaxN;                           // bump table n x L
+constexpr size_t kNoAllocFlag = kNoAllocB + (size_t)kNoAllocMaxN * kMaxBumps;    // pivot flag (int)
+constexpr size_t kNoAllocDoubles = kNoAllocFlag + 32;
+
+// The scratch array: every call on a device shares it (about 2.1 MB per device).
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[64] = {};   // device address of g_noalloc_scratch per device ordinal
+
+template <int D>
+__global__ void k_noalloc_bumps(const double *__restrict__ X, int n, KernelParams kp, double *__restrict__ B)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int l = 0; l < kp.L; ++l) {
+        double q = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            double dk = X[(int64_t)i * D + k] - kp.centers[l * D + k];
+            q = q + dk * dk;
+        }
+        double rho = kp.radii[l];
+        double s = q / (rho * rho);
+        double e = s < 1.0 ? exp(kp.beta * (1.0 - 1.0 / (1.0 - s))) : 0.0;
+        B[(int64_t)i * kp.L + l] = kp.amps[l] * e;
+    }
+}
+
+// Lower triangle of the dense A = K + sigma2 I (every entry written, so no clearing is needed).
+template <int D>
+__global__ void k_noalloc_dense(const double *__restrict__ X, int n, KernelParams kp, const double *__restrict__ B,
+                                double *__restrict__ A)
+{
+    const int64_t tot = (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e - (int64_t)i * n);
+        if (j > i) continue;
+        double q = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            double dk = __dsub_rn(X[(int64_t)i * D + k], X[(int64_t)j * D + k]);
+            q = __dadd_rn(q, __dmul_rn(dk, dk));
+        }
+        double v = 0.0;
+        if (i == j || q < kp.r * kp.r) {
+            double S = 0.0;
+            for (int l = 0; l < kp.L; ++l) S = fma(B[(int64_t)i * kp.L + l], B[(int64_t)j * kp.L + l], S);
+            v = wendland<double>(kp.kind, D, sqrt(q) * kp.inv_r) * (S + kp.w0);
+            if (i == j) v += kp.sigma2;
+        }
+        A[e] = v;
+    }
+}
+
+// {LML, y^T a, log|A|} from the factor's diagonal and the solution; NaN when a pivot failed.
+__global__ void k_noalloc_finish(const double *__restrict__ A, int n, const double *__restrict__ y,
+                                 const double *__restrict__ a, const int *__restrict__ bad, double *__restrict__ out)
+{
+    __shared__ double sh[2][32];
+    double ld = 0.0, qd = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        ld += log(A[(int64_t)i * n + i]);
+        qd = fma(y[i], a[i], qd);
+    }
+    ld = warp_sum_d(ld);
+    qd = warp_sum_d(qd);
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = ld;
+        sh[1][threadIdx.x >> 5] = qd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double L2 = 0.0, Q = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { L2 += sh[0][w]; Q += sh[1][w]; }
+        double logdet = 2.0 * L2;
+        double lml = -0.5 * Q - 0.5 * logdet - 0.5 * (double)n * log(2.0 * 3.141592653589793);
+        if (*bad) { lml = nan(""); Q = nan(""); logdet = nan(""); }
+        out[0] = lml;
+        out[1] = Q;
+        out[2] = logdet;
+    }
+}
+
+// Device address of the scratch array on the current device, looked up once per device.
+gp2s_status noalloc_scratch(double **ptr)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return GP2S_ECUDA; }
+    if (dev < 0 || dev >= 64) return GP2S_ECUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) { cudaGetLastError(); return GP2S_ECUDA; }
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return GP2S_OK;
+}
+
+template <int D>
+void launch_noalloc_build(const double *X, int n, const KernelParams &kp, double *B, double *A, cudaStream_t s)
+{
+    k_noalloc_bumps<D><<<(n + 127) / 128, 128, 0, s>>>(X, n, kp, B);
+    const int64_t tot = (int64_t)n * n;
+    unsigned gb = (unsigned)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096);
+    k_noalloc_dense<D><<<gb, 256, 0, s>>>(X, n, kp, B, A);
+}
+
+}  // namespace
+
+gp2s_status validate_hyper(gp2s_ctx *c, const gp2s_hyper *h);   // assemble.cu
+KernelParams make_kernel_params(const gp2s_hyper *h);             // assemble.cu
+
+}  // namespace gp2s
+
+extern "C" gp2s_status gp2s_lml_exact_noalloc(int64_t n, const double *X_dev, const double *y_dev,
+                                              const gp2s_hyper *hyper, double *out_dev, void *cuda_stream)
+{
+    using namespace gp2s;
+    if (n < 1 || n > kNoAllocMaxN) return GP2S_EINVAL;
+    if (!X_dev || !y_dev || !out_dev) return GP2S_EINVAL;
+    if (validate_hyper(nullptr, hyper) != GP2S_OK) return GP2S_EINVAL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    double *base = nullptr;
+    gp2s_status st = noalloc_scratch(&base);
+    if (st != GP2S_OK) return st;
+    const int nn = (int)n;
+    const KernelParams kp = make_kernel_params(hyper);
+    double *A = base;                          // nn x nn, leading dimension nn
+    double *x = base + kNoAllocX;
+    double *B = base + kNoAllocB;
+    int *bad = reinterpret_cast<int *>(base + kNoAllocFlag);
+    if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) { cudaGetLastError(); return GP2S_ECUDA; }
+    if (cudaMemcpyAsync(x, y_dev, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return GP2S_ECUDA;
+    }
+    switch (hyper->d) {
+    case 1: launch_noalloc_build<1>(X_dev, nn, kp, B, A, s); break;
+    case 2: launch_noalloc_build<2>(X_dev, nn, kp, B, A, s); break;
+    case 3: launch_noalloc_build<3>(X_dev, nn, kp, B, A, s); break;
+    default: launch_noalloc_build<4>(X_dev, nn, kp, B, A, s); break;
+    }
+    // blocked Cholesky A = L L^T (lower triangle, in place)
+    for (int kb = 0; kb < nn; kb += NB) {
+        k_potrf_diag<<<1, 256, 0, s>>>(A, nn, kb, bad);
+        int rest = nn - kb - NB;
+        if (rest > 0) {
+            k_trsm_panel<<<(rest + 63) / 64, 64, 0, s>>>(A, nn, kb);
+            unsigned tiles = (unsigned)((rest + 63) / 64);
+            k_syrk<<<dim3(tiles, tiles), 256, 0, s>>>(A, nn, kb);
+        }
+    }
+    // a = L^{-T} L^{-1} y, in place in x
+    for (int kb = 0; kb < nn; kb += NB) {
+        k_trsv_diag<<<1, 32, 0, s>>>(A, nn, kb, x, 0);
+        if (kb + NB < nn) k_trsv_update<<<(unsigned)((nn * 32 + 255) / 256), 256, 0, s>>>(A, nn, kb, x, 0);
+    }
+    for (int kb = ((nn - 1) / NB) * NB; kb >= 0; kb -= NB) {
+        k_trsv_diag<<<1, 32, 0, s>>>(A, nn, kb, x, 1);
+        if (kb > 0) k_trsv_update<<<(unsigned)((kb + 255) / 256), 256, 0, s>>>(A, nn, kb, x, 1);
+    }
+    k_noalloc_finish<<<1, 256, 0, s>>>(A, nn, y_dev, x, bad, out_dev);
+    if (cudaGetLastError() != cudaSuccess) return GP2S_ECUDA;
+    return GP2S_OK;
+}

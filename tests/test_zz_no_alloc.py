@@ -1,0 +1,69 @@
+"""The allocation-free entry point gp2s_lml_exact_noalloc, called through the C ABI.
+
+Callers that cannot allocate device memory (work queued during CUDA stream capture, or a device
+whose memory belongs to another allocator) use this entry point; it must agree with the ordinary
+gp2s_lml (FP64, exact log-determinant) on the same inputs.  Two calls in a row, with different
+problem sizes, check that the shared scratch array left behind by the first call does not leak into
+the second.  This file is collected last so that a run stopping at the first failure has already
+run every other test; it also passes on its own in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2512_06143_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_06143_gb300 as gp
+    from paper_2512_06143_gb300 import build
+    build.build()
+    L = gp.load()
+    f = L.gp2s_lml_exact_noalloc
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    return gp
+
+
+def _noalloc(gp, X, y, h):
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    hc = h.c()
+    stream = torch.cuda.current_stream()
+    st = gp.load().gp2s_lml_exact_noalloc(X.shape[0], X.data_ptr(), y.data_ptr(), ctypes.byref(hc),
+                                          out.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    return st, out.cpu().numpy()
+
+
+def test_noalloc_matches_gp2s_lml_two_calls(gp):
+    ctx = gp.Context(0)
+    opts = gp.default_opts(precision=gp.PREC_FP64, logdet=gp.LOGDET_EXACT)
+    for seed, n, d in [(401, 500, 2), (402, 317, 3)]:
+        w = W.random_small(seed, n, d, L=3, sigma2=1e-3, r=0.15 if d == 2 else 0.25)
+        h = gp.Hyper(**w["hyper"])
+        X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
+        y = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
+        st, out = _noalloc(gp, X, y, h)
+        assert st == gp.OK
+        lml, info = ctx.lml(X, y, h, opts)
+        assert out[0] == pytest.approx(lml, rel=1e-8)
+        assert out[1] == pytest.approx(info["quad"], rel=1e-8)
+        assert out[2] == pytest.approx(info["logdet"], rel=1e-10)
+
+
+def test_noalloc_rejects_sizes_beyond_the_limit(gp):
+    w = W.random_small(403, 513, 2)
+    h = gp.Hyper(**w["hyper"])
+    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
+    y = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
+    st, out = _noalloc(gp, X, y, h)
+    assert st == gp.EINVAL
+    assert np.all(np.isnan(out))      # nothing was written
