@@ -134,7 +134,7 @@ def oracle_sample(workload: str, budget_s: float = 20.0):
     oracle.build()
     if workload == "clusters_3d":
         full_n, target, m = 1_000_000, 100.0, 64
-        ns = 3000
+        ns = 12000
         gen = lambda n: W.clusters_3d(0, n=n, target_nnz=target)  # noqa: E731
     elif workload == "sphere_4d":
         full_n, target, m = 10_000_000, 60.0, 32

@@ -238,6 +238,8 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (cudaSetDevice(device) != cudaSuccess) return GP2S_ECUDA;
     gp2s_ctx *c = new gp2s_ctx();
     c->device = device;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0) c->num_sms = sms;
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     const char *lim = std::getenv("GP2S_MEM_LIMIT");
     if (lim) c->mem_limit = (size_t)std::strtoull(lim, nullptr, 10);
@@ -255,7 +257,8 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->scan_tmp, &c->scan_tmp2, &c->cell_start, &c->cell_flag, &c->items, &c->item_cnt,
                       &c->B64, &c->B32, &c->D64, &c->s64, &c->s32, &c->rowcnt, &c->rowptr, &c->col,
                       &c->val32, &c->val64, &c->counters, &c->vec, &c->vec64, &c->partials, &c->scal,
-                      &c->Z, &c->rec, &c->dense, &c->H, &c->gpart};
+                      &c->Z, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
+                      &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_split};
     for (DevBuf *b : bufs) free_buf(*b);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->hbuf.p) cudaFreeHost(c->hbuf.p);

@@ -79,6 +79,7 @@ struct Timer {
 
 struct gp2s_ctx {
     int device = 0;
+    int num_sms = 152;
     cudaStream_t stream = nullptr;
     std::string err;
     size_t mem_limit = 0;     // GP2S_MEM_LIMIT (0 = none)
@@ -94,7 +95,11 @@ struct gp2s_ctx {
     // CSR
     gp2s::DevBuf rowcnt, rowptr, col, val32, val64, counters;
     // Krylov
-    gp2s::DevBuf vec, vec64, partials, scal, Z, rec;
+    gp2s::DevBuf vec, vec64, partials, scal, Z, rec, rsplit;
+    // row-block (8 rows) copy of the FP32 matrix for the multi-RHS SpMM
+    gp2s::DevBuf rb_cnt, rb_ptr, rb_col, rb_val, rb_split;
+    bool rb_valid = false;
+    int64_t rb_entries = 0;
     // dense
     gp2s::DevBuf dense;
     // adjoint

@@ -12,8 +12,10 @@
 // row-major: the y group is n values, the probe group n x m values.  In MIXED precision vectors are
 // FP32, dot products use compensated FP32 partial sums that are combined in FP64, and the scalars
 // (alpha, beta, rho) are FP64.  In FP64 precision everything is FP64.
+#include <climits>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "gp2s_internal.cuh"
 
@@ -21,7 +23,7 @@ namespace gp2s {
 
 namespace {
 
-constexpr int kSpmmThreads = 256;
+constexpr int kSpmmThreads = 1024;
 constexpr int kSpmmWarps = kSpmmThreads / kWarp;
 constexpr int kMaxPartBlocks = 152 * 8;
 constexpr int kScal = 8;   // doubles per column in the scalar block
@@ -133,20 +135,29 @@ __device__ __forceinline__ double warp_sum(double v)
 // ---------------------------------------------------------------------------------------------
 // SpMM: Q = Ah P for the y column (lanes over a row's entries) and the m probe columns (all lanes
 // per entry, K = m / 32 columns per lane), plus the partial dots p_c^T q_c.
-// One CTA owns a contiguous range of rows; its warps take rows round-robin.
+// One CTA per SM owns a contiguous range of rows holding an equal share of the entries
+// (row_split), so the P rows its warps gather (the Morton neighbourhood of the range) stay in that
+// SM's L1; its warps take consecutive rows round-robin.  Each warp stages 32 (column, value)
+// entries of its row in shared memory and broadcasts them with one shared load per entry, with
+// four independent P-row loads in flight.
 // ---------------------------------------------------------------------------------------------
+template <class T> struct Staged;
+template <> struct Staged<float> { int j; float v; };
+template <> struct Staged<double> { int j; int pad; double v; };
+
 template <class T, class V, int K, bool HAS_Y>
-__global__ void __launch_bounds__(kSpmmThreads)
+__global__ void __launch_bounds__(kSpmmThreads, 1)
 k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const V *__restrict__ val,
-       int64_t n, int64_t rows_per_block, const T *__restrict__ py, const T *__restrict__ pz,
+       int64_t n, const int32_t *__restrict__ row_split, const T *__restrict__ py, const T *__restrict__ pz,
        T *__restrict__ qy, T *__restrict__ qz, double *__restrict__ part, int pstride,
        const int *__restrict__ active)
 {
     using Acc = typename AccOf<T>::type;
     constexpr int M = 32 * K;
+    __shared__ Staged<T> stage[kSpmmWarps][kWarp];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t r_begin = (int64_t)blockIdx.x * rows_per_block;
-    const int64_t r_end = min(n, r_begin + rows_per_block);
+    const int64_t r_begin = row_split[blockIdx.x];
+    const int64_t r_end = row_split[blockIdx.x + 1];
     Acc dz[K > 0 ? K : 1];
     Acc dy;
     for (int64_t i = r_begin + wid; i < r_end; i += kSpmmWarps) {
@@ -157,7 +168,7 @@ k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, cons
         T accy = T(0);
         for (int pb = p0; pb < p1; pb += kWarp) {
             const int p = pb + lane;
-            int cj = 0;
+            int cj = (int)i;     // padding entries: a valid row with value 0
             T cv = T(0);
             if (p < p1) {
                 cj = col[p];
@@ -165,15 +176,21 @@ k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, cons
             }
             if (HAS_Y) accy += cv * py[cj];
             if (K > 0) {
+                Staged<T> e;
+                e.j = cj;
+                e.v = cv;
+                stage[wid][lane] = e;
+                __syncwarp();
                 const int cnt = min(kWarp, p1 - pb);
+#pragma unroll 4
                 for (int t = 0; t < cnt; ++t) {
-                    const int j = __shfl_sync(0xffffffffu, cj, t);
-                    const T v = __shfl_sync(0xffffffffu, cv, t);
+                    const Staged<T> s = stage[wid][t];
                     T pv[K > 0 ? K : 1];
-                    load_k<T, (K > 0 ? K : 1)>(pz + (int64_t)j * M + lane * K, pv);
+                    load_k<T, (K > 0 ? K : 1)>(pz + (int64_t)s.j * M + lane * K, pv);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc[k] += v * pv[k];
+                    for (int k = 0; k < K; ++k) acc[k] += s.v * pv[k];
                 }
+                __syncwarp();
             }
         }
         if (K > 0) {
@@ -192,19 +209,26 @@ k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, cons
             }
         }
     }
-    // block reduction of the partial dots: y column (lane 0 of each warp) and probe columns
-    __shared__ double red[kSpmmWarps][M + 1];
-    if (HAS_Y) {
-        double v = lane == 0 ? dy.value() : 0.0;
-        if (lane == 0) red[wid][M] = v;
-    }
+    // block reduction of the partial dots: y column (lane 0 of each warp) and probe columns, in
+    // two halves to keep the shared buffer small (fixed order: deterministic)
+    constexpr int HW = kSpmmWarps / 2;
+    __shared__ double red[HW][M + 1];
+    if (wid >= HW) {
+        if (HAS_Y && lane == 0) red[wid - HW][M] = dy.value();
 #pragma unroll
-    for (int k = 0; k < K; ++k) red[wid][lane * K + k] = dz[k].value();
+        for (int k = 0; k < K; ++k) red[wid - HW][lane * K + k] = dz[k].value();
+    }
+    __syncthreads();
+    if (wid < HW) {
+        if (HAS_Y && lane == 0) red[wid][M] += dy.value();
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[wid][lane * K + k] += dz[k].value();
+    }
     __syncthreads();
     for (int cidx = threadIdx.x; cidx < M + 1; cidx += kSpmmThreads) {
         if (cidx == M && !HAS_Y) continue;
         double s = 0.0;
-        for (int w = 0; w < kSpmmWarps; ++w) s += red[w][cidx];
+        for (int w = 0; w < HW; ++w) s += red[w][cidx];
         const int c = cidx == M ? 0 : cidx + 1;
         part[(int64_t)c * pstride + blockIdx.x] = s;
     }
@@ -321,6 +345,7 @@ __global__ void k_scal_beta(const double *__restrict__ part, int pstride, int np
             // p is not updated for inactive columns (beta unused)
         } else {
             atomicAdd(count, 1);
+            if (c > 0) atomicAdd(count + 1, 1);
         }
     }
 }
@@ -508,16 +533,81 @@ struct CGBuffers {
     void *xz, *rz, *pz, *qz, *xy, *ry, *py, *qy;
 };
 
+template <int K>
+gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb);
+
+// y-only SpMV (the y column after every probe column has stopped, and the refinement solves):
+// one warp per row, lanes over the row's entries, many warps per SM to keep enough independent
+// loads in flight; per-CTA partial dot p^T q.
+constexpr int kSpmvThreads = 256;
+constexpr int kSpmvBlocks = 152 * 8;
+template <class T, class V>
+__global__ void __launch_bounds__(kSpmvThreads)
+k_spmv_y(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const V *__restrict__ val, int64_t n,
+         const T *__restrict__ py, T *__restrict__ qy, double *__restrict__ part)
+{
+    using Acc = typename AccOf<T>::type;
+    __shared__ double sh[kSpmvThreads / kWarp];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    Acc d;
+    for (int64_t i = w0; i < n; i += nw) {
+        const int p1 = rowptr[i + 1];
+        T s = T(0);
+        for (int p = rowptr[i] + lane; p < p1; p += kWarp) s += (T)val[p] * py[col[p]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            qy[i] = s;
+            d.fma2(py[i], s);
+        }
+    }
+    if (lane == 0) sh[wid] = d.value();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kSpmvThreads / kWarp; ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// The FP32 multi-RHS SpMM runs on the RB8 copy when it has been built.
+template <class T>
+bool rb_launch(gp2s_ctx *c, int m, bool has_y)
+{
+    return std::is_same<T, float>::value && c->rb_valid && m > 0 && has_y;
+}
+
+// Row ranges of the SpMM CTAs with equal shares of the entries: split[b] = first row whose entries
+// start at or after b * nnz / nb.
+__global__ void k_row_split(const int32_t *__restrict__ rowptr, int64_t n, int nb, int32_t *__restrict__ split)
+{
+    const int64_t nnz = rowptr[n];
+    for (int b = threadIdx.x; b <= nb; b += blockDim.x) {
+        if (b == 0) { split[0] = 0; continue; }
+        if (b == nb) { split[nb] = (int32_t)n; continue; }
+        const int64_t target = nnz * b / nb;
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (rowptr[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        split[b] = (int32_t)lo;
+    }
+}
+
 template <class T, class V>
 gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBuffers &B, double *part,
-                        int pstride, int nb, int64_t rpb, const int *active)
+                        int pstride, int nb, const int32_t *rsplit, const int *active, int *nparts)
 {
+    *nparts = nb;
     const Assembled &A = c->A;
     const int32_t *rp = c->rowptr.as<int32_t>(), *cl = c->col.as<int32_t>();
     const T *py = (const T *)B.py, *pz = (const T *)B.pz;
     T *qy = (T *)B.qy, *qz = (T *)B.qz;
 #define GP2S_SPMM_CASE(KK, HY)                                                                    \
-    k_spmm<T, V, KK, HY><<<nb, kSpmmThreads, 0, c->stream>>>(rp, cl, val, A.n, rpb, py, pz, qy, qz, \
+    k_spmm<T, V, KK, HY><<<nb, kSpmmThreads, 0, c->stream>>>(rp, cl, val, A.n, rsplit, py, pz, qy, qz, \
                                                              part, pstride, active)
     int K = m / 32;
     // algorithmic bytes: values + column indices + row pointers + every input and output element once
@@ -537,6 +627,25 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
         ev_b = c->prof_ev[c->prof_used + 1];
         c->prof_used += 2;
         GP2S_CUDA(c, cudaEventRecord(ev_a, c->stream));
+    }
+    if (rb_launch<T>(c, m, has_y)) {
+        switch (K) {
+        case 1: GP2S_TRY(launch_rb<1>(c, B, part, pstride, nb)); break;
+        case 2: GP2S_TRY(launch_rb<2>(c, B, part, pstride, nb)); break;
+        case 3: GP2S_TRY(launch_rb<3>(c, B, part, pstride, nb)); break;
+        default: GP2S_TRY(launch_rb<4>(c, B, part, pstride, nb)); break;
+        }
+        if (c->profile) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
+        return GP2S_OK;
+    }
+    if (has_y && K == 0) {
+        const int nbv = (int)std::min<int64_t>(std::min(kSpmvBlocks, pstride),
+                                               std::max<int64_t>(1, ceil_div(A.n * kWarp, kSpmvThreads)));
+        k_spmv_y<T, V><<<nbv, kSpmvThreads, 0, c->stream>>>(rp, cl, val, A.n, py, qy, part);
+        GP2S_LAUNCH(c);
+        *nparts = nbv;
+        if (c->profile) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
+        return GP2S_OK;
     }
     if (has_y) {
         switch (K) {
@@ -574,6 +683,226 @@ gp2s_status flush_profile(gp2s_ctx *c)
     return GP2S_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Row-block (RB8) SpMM for the FP32 multi-RHS solves.
+//
+// With m = 64 probe columns every stored entry of the CSR makes the warp gather a 256-byte row of
+// P through L1, and the SpMM is L1-bandwidth bound.  Consecutive rows in Morton order share most
+// of their columns, so the RB8 copy of Ah groups 8 consecutive rows into a block that stores the
+// union of their column lists once, with the 8 values of each union column (0 for a row that does
+// not hold it).  A gathered P row then feeds 8 rows from registers: the L1 traffic per stored entry
+// drops about four-fold at the cost of some multiplications by zero.
+// ---------------------------------------------------------------------------------------------
+constexpr int kRB = 8;
+
+// Union of the 8 sorted column lists of a row block by a warp-wide 8-way merge: lane r < 8 holds
+// the head of row r; each step emits the smallest head, with the value of every row that holds it.
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+k_rb_build(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const float *__restrict__ val,
+           int64_t n, int64_t nblk, int32_t *__restrict__ cnt, const int32_t *__restrict__ bptr,
+           int32_t *__restrict__ ucol, float *__restrict__ uval)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = w0; b < nblk; b += nw) {
+        const int64_t r = b * kRB + lane;
+        int pos = 0, end = 0;
+        if (lane < kRB && r < n) {
+            pos = rowptr[r];
+            end = rowptr[r + 1];
+        }
+        int head = pos < end ? col[pos] : INT_MAX;
+        int64_t e = FILL ? bptr[b] : 0;
+        int emitted = 0;
+        for (;;) {
+            int mn = head;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            if (mn == INT_MAX) break;
+            const bool mine = head == mn;
+            if (FILL) {
+                if (lane < kRB) uval[e * kRB + lane] = mine ? val[pos] : 0.0f;
+                if (lane == 0) ucol[e] = mn;
+                ++e;
+            }
+            if (mine) {
+                ++pos;
+                head = pos < end ? col[pos] : INT_MAX;
+            }
+            ++emitted;
+        }
+        if (!FILL && lane == 0) cnt[b] = emitted;
+    }
+}
+
+template <int K> struct RBCfg {
+    static constexpr int threads = K <= 2 ? 1024 : 512;
+    static constexpr int warps = threads / kWarp;
+};
+
+template <int K, bool HAS_Y>
+__global__ void __launch_bounds__(RBCfg<K>::threads, 1)
+k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, const float *__restrict__ uval,
+          int64_t n, const int32_t *__restrict__ blk_split, const float *__restrict__ py,
+          const float *__restrict__ pz, float *__restrict__ qy, float *__restrict__ qz, double *__restrict__ part,
+          int pstride)
+{
+    constexpr int M = 32 * K;
+    constexpr int W = RBCfg<K>::warps;
+    extern __shared__ __align__(16) unsigned char rb_sh[];
+    int *s_col = reinterpret_cast<int *>(rb_sh);                                    // W x 32
+    float4 *s_val = reinterpret_cast<float4 *>(rb_sh + sizeof(int) * W * kWarp);  // W x 32 x 2
+    double *red = reinterpret_cast<double *>(rb_sh + sizeof(int) * W * kWarp + sizeof(float4) * W * kWarp * 2);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t b_begin = blk_split[blockIdx.x], b_end = blk_split[blockIdx.x + 1];
+    Acc32 dz[K];
+    Acc32 dy;
+    for (int64_t b = b_begin + wid; b < b_end; b += W) {
+        const int64_t r0 = b * kRB;
+        const int nrows = (int)(n - r0 < kRB ? n - r0 : kRB);
+        float acc[kRB][K];
+#pragma unroll
+        for (int r = 0; r < kRB; ++r)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[r][k] = 0.0f;
+        float ay[kRB];
+#pragma unroll
+        for (int r = 0; r < kRB; ++r) ay[r] = 0.0f;
+        const int e0 = bptr[b], e1 = bptr[b + 1];
+        for (int eb = e0; eb < e1; eb += kWarp) {
+            const int e = eb + lane;
+            int cj = (int)r0;
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+            if (e < e1) {
+                cj = ucol[e];
+                v0 = reinterpret_cast<const float4 *>(uval)[(int64_t)e * 2];
+                v1 = reinterpret_cast<const float4 *>(uval)[(int64_t)e * 2 + 1];
+            }
+            if (HAS_Y) {
+                const float yj = py[cj];
+                ay[0] = fmaf(v0.x, yj, ay[0]); ay[1] = fmaf(v0.y, yj, ay[1]);
+                ay[2] = fmaf(v0.z, yj, ay[2]); ay[3] = fmaf(v0.w, yj, ay[3]);
+                ay[4] = fmaf(v1.x, yj, ay[4]); ay[5] = fmaf(v1.y, yj, ay[5]);
+                ay[6] = fmaf(v1.z, yj, ay[6]); ay[7] = fmaf(v1.w, yj, ay[7]);
+            }
+            s_col[wid * kWarp + lane] = cj;
+            s_val[(wid * kWarp + lane) * 2] = v0;
+            s_val[(wid * kWarp + lane) * 2 + 1] = v1;
+            __syncwarp();
+            const int cnt = min(kWarp, e1 - eb);
+#pragma unroll 2
+            for (int t = 0; t < cnt; ++t) {
+                const int j = s_col[wid * kWarp + t];
+                const float4 a0 = s_val[(wid * kWarp + t) * 2], a1 = s_val[(wid * kWarp + t) * 2 + 1];
+                float pv[K];
+                load_k<float, K>(pz + (int64_t)j * M + lane * K, pv);
+                const float vr[kRB] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                for (int r = 0; r < kRB; ++r)
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc[r][k] = fmaf(vr[r], pv[k], acc[r][k]);
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int r = 0; r < kRB; ++r) {
+            if (r < nrows) {
+                const int64_t i = r0 + r;
+                store_k<float, K>(qz + i * M + lane * K, acc[r]);
+                float pi[K];
+                load_k<float, K>(pz + i * M + lane * K, pi);
+#pragma unroll
+                for (int k = 0; k < K; ++k) dz[k].fma2(pi[k], acc[r][k]);
+            }
+        }
+        if (HAS_Y) {
+#pragma unroll
+            for (int r = 0; r < kRB; ++r) {
+                float v = ay[r];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && r < nrows) {
+                    qy[r0 + r] = v;
+                    dy.fma2(py[r0 + r], v);
+                }
+            }
+        }
+    }
+    // block reduction of the partial dots (two halves, fixed order)
+    constexpr int HW = W / 2;
+    if (wid >= HW) {
+        if (HAS_Y && lane == 0) red[(wid - HW) * (M + 1) + M] = dy.value();
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[(wid - HW) * (M + 1) + lane * K + k] = dz[k].value();
+    }
+    __syncthreads();
+    if (wid < HW) {
+        if (HAS_Y && lane == 0) red[wid * (M + 1) + M] += dy.value();
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[wid * (M + 1) + lane * K + k] += dz[k].value();
+    }
+    __syncthreads();
+    for (int cidx = threadIdx.x; cidx < M + 1; cidx += RBCfg<K>::threads) {
+        if (cidx == M && !HAS_Y) continue;
+        double s = 0.0;
+        for (int w = 0; w < HW; ++w) s += red[w * (M + 1) + cidx];
+        const int c = cidx == M ? 0 : cidx + 1;
+        part[(int64_t)c * pstride + blockIdx.x] = s;
+    }
+}
+
+template <int K>
+size_t rb_smem()
+{
+    constexpr int W = RBCfg<K>::warps;
+    return sizeof(int) * W * kWarp + sizeof(float4) * W * kWarp * 2 + sizeof(double) * (W / 2) * (32 * K + 1);
+}
+
+template <int K>
+gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb)
+{
+    const size_t smem = rb_smem<K>();
+    auto kern = k_spmm_rb<K, true>;
+    GP2S_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<nb, RBCfg<K>::threads, smem, c->stream>>>(c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
+                                                     c->rb_val.as<float>(), c->A.n, c->rb_split.as<int32_t>(),
+                                                     (const float *)B.py, (const float *)B.pz, (float *)B.qy,
+                                                     (float *)B.qz, part, pstride);
+    GP2S_LAUNCH(c);
+    return GP2S_OK;
+}
+
+// Build the RB8 copy of the FP32 matrix (count -> scan -> fill) and its per-CTA block ranges.
+gp2s_status build_rb8(gp2s_ctx *c)
+{
+    const Assembled &A = c->A;
+    const int64_t n = A.n;
+    const int64_t nblk = ceil_div(n, kRB);
+    GP2S_TRY(ensure(c, c->rb_cnt, sizeof(int32_t) * (size_t)(nblk + 1)));
+    GP2S_TRY(ensure(c, c->rb_ptr, sizeof(int32_t) * (size_t)(nblk + 1)));
+    const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(nblk * 32, 256), 152 * 16);
+    k_rb_build<false><<<gb, 256, 0, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val32.as<float>(),
+                                                 n, nblk, c->rb_cnt.as<int32_t>(), nullptr, nullptr, nullptr);
+    GP2S_LAUNCH(c);
+    int64_t nu = 0;
+    GP2S_TRY(scan_counts_i32(c, c->rb_cnt.as<int32_t>(), c->rb_ptr.as<int32_t>(), nblk, &nu));
+    GP2S_TRY(ensure(c, c->rb_col, sizeof(int32_t) * (size_t)(nu + 1)));
+    GP2S_TRY(ensure(c, c->rb_val, sizeof(float) * kRB * (size_t)(nu + 1)));
+    k_rb_build<true><<<gb, 256, 0, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val32.as<float>(),
+                                                n, nblk, nullptr, c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
+                                                c->rb_val.as<float>());
+    GP2S_LAUNCH(c);
+    const int nb = std::max(1, std::min(kMaxPartBlocks, c->num_sms));
+    GP2S_TRY(ensure(c, c->rb_split, sizeof(int32_t) * (size_t)(nb + 1)));
+    k_row_split<<<1, 1024, 0, c->stream>>>(c->rb_ptr.as<int32_t>(), nblk, nb, c->rb_split.as<int32_t>());
+    GP2S_LAUNCH(c);
+    c->rb_entries = nu;
+    c->rb_valid = true;
+    return GP2S_OK;
+}
+
 // One CG run (x0 = 0) on columns [y | probes]; the probe right-hand sides must already be in rz.
 template <class T, class V>
 gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const double *rhs_y, double tol_y,
@@ -583,9 +912,12 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     const Assembled &A = c->A;
     const int64_t n = A.n;
     const int k = 1 + m;
-    const int nb = (int)std::min<int64_t>(kMaxPartBlocks, std::max<int64_t>(1, ceil_div(n, 64)));
-    const int64_t rpb = ceil_div(n, nb);
+    const int nb = std::max(1, std::min(kMaxPartBlocks, c->num_sms));   // one SpMM CTA per SM
     const int pstride = kMaxPartBlocks;
+    GP2S_TRY(ensure(c, c->rsplit, sizeof(int32_t) * (size_t)(nb + 1)));
+    k_row_split<<<1, 1024, 0, c->stream>>>(c->rowptr.as<int32_t>(), n, nb, c->rsplit.as<int32_t>());
+    GP2S_LAUNCH(c);
+    const int32_t *rsplit = c->rsplit.as<int32_t>();
     // update-kernel geometry
     const int ut = m > 0 ? m * std::max(1, 256 / m) : 256;
     const int nbz = m > 0 ? (int)std::min<int64_t>(152 * 4, std::max<int64_t>(1, ceil_div(n, ut / m))) : 0;
@@ -598,7 +930,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     double *part = c->partials.as<double>();
     double *sc = c->scal.as<double>();
     int *active = reinterpret_cast<int *>(sc + kScal * kMaxCols);
-    int *flags = active + k;       // [0] breakdown, [1] active count
+    int *flags = active + kMaxCols;   // [0] breakdown, [1] active columns, [2] active probe columns
     GP2S_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int) * 4, c->stream));
 
     k_cg_init<T><<<nbz + nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, rhs_y, (T *)B.xz, (T *)B.rz, (T *)B.pz,
@@ -610,30 +942,35 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     const int check_every = 8;
     int it = 0;
     int *hcount = reinterpret_cast<int *>(c->hbuf.p);
+    int mc = m;          // probe columns still iterated; 0 once every probe column has stopped
     for (; it < max_iter; ++it) {
-        GP2S_TRY((launch_spmm<T, V>(c, m, true, val, B, part, pstride, nb, rpb, active)));
-        k_scal_alpha<<<k, 256, 0, c->stream>>>(part, pstride, nb, sc, active, flags, rec, ksteps);
+        const int kc = 1 + mc;
+        int np = nb;
+        GP2S_TRY((launch_spmm<T, V>(c, mc, true, val, B, part, pstride, nb, rsplit, active, &np)));
+        k_scal_alpha<<<kc, 256, 0, c->stream>>>(part, pstride, np, sc, active, flags, rec, ksteps);
         GP2S_LAUNCH(c);
-        GP2S_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int), c->stream));
-        k_update<T><<<nbz + nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, (T *)B.xz, (T *)B.rz, (const T *)B.pz,
-                                                     (const T *)B.qz, (T *)B.xy, (T *)B.ry, (const T *)B.py,
-                                                     (const T *)B.qy, sc, part, pstride, nbz);
+        GP2S_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int) * 2, c->stream));
+        k_update<T><<<(mc > 0 ? nbz : 0) + nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, (T *)B.xz, (T *)B.rz,
+                                                                     (const T *)B.pz, (const T *)B.qz, (T *)B.xy,
+                                                                     (T *)B.ry, (const T *)B.py, (const T *)B.qy, sc,
+                                                                     part, pstride, mc > 0 ? nbz : 0);
         GP2S_LAUNCH(c);
-        k_scal_beta<<<k, 256, 0, c->stream>>>(part, pstride, nby, nbz, sc, active, flags + 1, rec, ksteps,
-                                              kmin_probe);
+        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, pstride, nby, nbz, sc, active, flags + 1, rec, ksteps,
+                                               kmin_probe);
         GP2S_LAUNCH(c);
         {
-            int64_t tot = n * (int64_t)(m + 1);
+            int64_t tot = n * (int64_t)(mc + 1);
             unsigned gb = (unsigned)std::min<int64_t>(ceil_div(tot, 256), 152 * 8);
-            k_direction<T><<<gb, 256, 0, c->stream>>>(n, m > 0 ? m : 1, (const T *)B.rz, (T *)B.pz,
-                                                       (const T *)B.ry, (T *)B.py, sc, active);
+            k_direction<T><<<gb, 256, 0, c->stream>>>(n, mc, (const T *)B.rz, (T *)B.pz, (const T *)B.ry,
+                                                       (T *)B.py, sc, active);
             GP2S_LAUNCH(c);
         }
         if ((it + 1) % check_every == 0 || it + 1 == max_iter) {
-            GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream));
+            GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
             GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
             GP2S_TRY(flush_profile(c));
             if (hcount[1] == 0) { ++it; break; }
+            if (mc > 0 && hcount[2] == 0) mc = 0;   // only the y column is left: y-only kernels
         }
     }
     // iteration counts per column group
@@ -715,6 +1052,7 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
         GP2S_LAUNCH(c);
     }
     const gp2s_opts &o = A.opts;
+    if (mixed && mm > 0 && !c->rb_valid) GP2S_TRY(build_rb8(c));
     const double tol_first = mixed ? o.tol_inner : std::min(o.tol_inner, 0.1 * o.tol_refine);
     int iy = 0, iz = 0;
     bool brk = false;

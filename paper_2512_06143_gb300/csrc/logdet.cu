@@ -82,13 +82,16 @@ __host__ __device__ bool tridiag_eig(double *a, double *b, double *q, int k)
     return true;
 }
 
-// One thread per probe: T from CG coefficients, eigen-decomposition, Gauss quadrature of log.
+// One CTA per probe (its first thread runs the sequential QR iteration on arrays in shared
+// memory): T from CG coefficients, eigen-decomposition, Gauss quadrature of log.
 __global__ void k_slq(const double *__restrict__ rec, const double *__restrict__ sc, int m, int ksteps,
                       double *__restrict__ work, double *__restrict__ out, int *__restrict__ bad)
 {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= m) return;
-    double *a = work + (int64_t)s * 3 * ksteps;
+    extern __shared__ double slq_sh[];
+    const int s = blockIdx.x;
+    if (s >= m || threadIdx.x != 0) return;
+    (void)work;
+    double *a = slq_sh;
     double *b = a + ksteps;
     double *q = b + ksteps;
     // number of recorded steps for this probe column (column s + 1 of the CG scalar block)
@@ -359,7 +362,9 @@ gp2s_status slq_logdet(gp2s_ctx *c, int m, int ksteps, double *logdet_hat, doubl
     double *out = work + (size_t)m * 3 * ksteps;
     int *bad = reinterpret_cast<int *>(out + m);
     GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-    k_slq<<<(m + 31) / 32, 32, 0, c->stream>>>(c->rec.as<double>(), c->scal.as<double>(), m, ksteps, work, out, bad);
+    const size_t smem = sizeof(double) * 3 * (size_t)ksteps;
+    GP2S_CUDA(c, cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_slq<<<m, 32, smem, c->stream>>>(c->rec.as<double>(), c->scal.as<double>(), m, ksteps, work, out, bad);
     GP2S_LAUNCH(c);
     std::vector<double> g(m);
     int hbad = 0;
