@@ -93,7 +93,9 @@ typedef struct {
     double tol_refine;       /* target |y - A a| / |y| of the y solve (FP64 residual), default 1e-8 */
     double tol_probe;        /* relative residual of the probe solves used by the gradient, default 1e-5 */
     uint64_t seed;           /* probe seed, default 0 */
-    int32_t precond;         /* 0 = none, 1 = Jacobi (default) */
+    int32_t precond;         /* 1 = Jacobi scaling Ah = D^{-1/2} A D^{-1/2} (0 is read as 1);
+                                2 = block-Jacobi on Morton-consecutive 64-row blocks of Ah on top of
+                                it (MIXED precision; FP64 precision runs 1).  Default 2. */
     int32_t exact_support;   /* 1 = skip the FP32 guard-band pre-test (every candidate pair is
                                 decided by the FP64 test); default 0 */
     int32_t max_outer;       /* refinement steps cap, default 8 */

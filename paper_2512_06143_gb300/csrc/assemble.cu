@@ -455,6 +455,7 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     c->have_probes = false;
     c->have_exact = false;
     c->rb_valid = false;
+    c->bj_valid = false;
     const int d = h->d;
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) GP2S_CUDA(c, cudaEventCreate(&ev[k]));

@@ -146,6 +146,7 @@ static gp2s_status validate_opts(gp2s_ctx *c, const gp2s_opts *o)
     if (o->max_iter < 1) return set_err(c, GP2S_EINVAL, "max_iter must be >= 1");
     if (!(o->tol_inner > 0.0) || !(o->tol_refine > 0.0) || !(o->tol_probe > 0.0)) return set_err(c, GP2S_EINVAL, "tolerances must be > 0");
     if (o->max_outer < 0) return set_err(c, GP2S_EINVAL, "max_outer must be >= 0");
+    if (o->precond < 0 || o->precond > 2) return set_err(c, GP2S_EINVAL, "precond must be 0, 1 or 2");
     return GP2S_OK;
 }
 
@@ -219,7 +220,7 @@ void gp2s_opts_default(gp2s_opts *o)
     o->tol_refine = 1e-8;
     o->tol_probe = 1e-5;
     o->seed = 0;
-    o->precond = 1;
+    o->precond = 2;
     o->exact_support = 0;
     o->max_outer = 8;
 }
@@ -258,7 +259,8 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->B64, &c->B32, &c->D64, &c->s64, &c->s32, &c->rowcnt, &c->rowptr, &c->col,
                       &c->val32, &c->val64, &c->counters, &c->vec, &c->vec64, &c->partials, &c->scal,
                       &c->Z, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
-                      &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_split};
+                      &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_split,
+                      &c->bj_Minv, &c->bj_ld};
     for (DevBuf *b : bufs) free_buf(*b);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->hbuf.p) cudaFreeHost(c->hbuf.p);
@@ -400,7 +402,9 @@ static gp2s_status lml_impl(gp2s_ctx *c, int64_t n, const double *X, const doubl
     if ((grad || method == GP2S_LOGDET_SLQ) && m <= 0) return set_err(c, GP2S_EINVAL, "SLQ / gradient need probes > 0");
     GP2S_TRY(stage_y(c, y));
     CGResult res;
+    c->probes_for_grad = grad != nullptr;
     gp2s_status st = do_solve(c, method, m, &res);
+    c->probes_for_grad = false;
     if (st != GP2S_OK) return st;
     cudaEventRecord(e2.e, c->stream);
     double ldiag = 0.0, lhat = 0.0, se = 0.0;

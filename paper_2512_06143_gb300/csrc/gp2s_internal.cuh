@@ -100,6 +100,11 @@ struct gp2s_ctx {
     gp2s::DevBuf rb_cnt, rb_ptr, rb_col, rb_val, rb_split;
     bool rb_valid = false;
     int64_t rb_entries = 0;
+    // block-Jacobi preconditioner: FP32 M^{-1} per 64-row block and the block log-determinants
+    gp2s::DevBuf bj_Minv, bj_ld;
+    bool bj_valid = false;
+    double bj_logdet = 0.0;
+    bool probes_for_grad = false;   // the probe solves feed the Hutchinson gradient
     // dense
     gp2s::DevBuf dense;
     // adjoint

@@ -116,6 +116,9 @@ __device__ __forceinline__ void store_k(T *__restrict__ p, const T (&v)[K])
         *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
     } else if constexpr (sizeof(T) == 8 && K == 2) {
         *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+    } else if constexpr (sizeof(T) == 8 && K == 4) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
     } else {
 #pragma unroll
         for (int k = 0; k < K; ++k) p[k] = v[k];
@@ -272,17 +275,24 @@ __device__ __forceinline__ double block_sum(const double *__restrict__ p, int cn
 }
 
 // Initial scalars: rho = b^T b (partials in part), b2 = rho, tol2 = tol^2 b2, alpha = beta = 0.
-__global__ void k_scal_init(const double *__restrict__ part, int pstride, int nparts_y, int nparts_z,
-                            double *__restrict__ sc, int *__restrict__ active, double tol_y, double tol_z)
+// For a preconditioned column (pc_y for column 0, pc_z for the probe columns) part holds r^T z
+// and part_rr holds r^T r; for a plain CG column part holds r^T r.
+__global__ void k_scal_init(const double *__restrict__ part, const double *__restrict__ part_rr, int pstride,
+                            int nparts_y, int nparts_z, double *__restrict__ sc, int *__restrict__ active,
+                            double tol_y, double tol_z, int pc_y, int pc_z)
 {
     const int c = blockIdx.x;
-    double s = block_sum(part + (int64_t)c * pstride, c == 0 ? nparts_y : nparts_z);
+    const int np = c == 0 ? nparts_y : nparts_z;
+    const bool pc = c == 0 ? pc_y : pc_z;
+    double s = block_sum(part + (int64_t)c * pstride, np);
+    __syncthreads();
+    double s2 = pc ? block_sum(part_rr + (int64_t)c * pstride, np) : s;
     if (threadIdx.x == 0) {
         double *q = sc + c * kScal;
         q[S_RHO] = s;
-        q[S_B2] = s;
+        q[S_B2] = s2;
         double tol = c == 0 ? tol_y : tol_z;
-        q[S_TOL] = tol * tol * s;
+        q[S_TOL] = tol * tol * s2;
         q[S_ALPHA] = 0.0;
         q[S_BETA] = 0.0;
         q[S_STEPS] = 0.0;
@@ -319,26 +329,31 @@ __global__ void k_scal_alpha(const double *__restrict__ part, int pstride, int n
 
 // beta_c = rr_c / rho_c, rho_c = rr_c, convergence test |r|^2 <= tol^2 |b|^2 once at least
 // kmin steps are recorded (the probe columns keep iterating to give SLQ its k Lanczos steps).
-__global__ void k_scal_beta(const double *__restrict__ part, int pstride, int nparts_y, int nparts_z,
-                            double *__restrict__ sc, int *__restrict__ active, int *__restrict__ count,
-                            double *__restrict__ rec, int ksteps, int kmin_probe)
+__global__ void k_scal_beta(const double *__restrict__ part, const double *__restrict__ part_rr, int pstride,
+                            int nparts_y, int nparts_z, double *__restrict__ sc, int *__restrict__ active,
+                            int *__restrict__ count, double *__restrict__ rec, int ksteps, int kmin_probe, int pc_y,
+                            int pc_z)
 {
     const int c = blockIdx.x;
-    double s = block_sum(part + (int64_t)c * pstride, c == 0 ? nparts_y : nparts_z);
+    const int np = c == 0 ? nparts_y : nparts_z;
+    const bool pc = c == 0 ? pc_y : pc_z;
+    double s = block_sum(part + (int64_t)c * pstride, np);
+    __syncthreads();
+    double s2 = pc ? block_sum(part_rr + (int64_t)c * pstride, np) : s;
     if (threadIdx.x == 0) {
         double *q = sc + c * kScal;
         if (!active[c]) {
             q[S_BETA] = 0.0;
             return;
         }
-        q[S_RR] = s;
+        q[S_RR] = s2;
         double b = s / q[S_RHO];
         int st = (int)q[S_STEPS];
         if (c > 0 && rec && st < ksteps) rec[((int64_t)(c - 1) * ksteps + st) * 2 + 1] = b;
         q[S_BETA] = b;
         q[S_RHO] = s;
         q[S_STEPS] = (double)(st + 1);
-        bool conv = s <= q[S_TOL];
+        bool conv = s2 <= q[S_TOL];
         int kmin = c == 0 ? 0 : kmin_probe;
         if ((conv && st + 1 >= kmin) || !(s == s)) {
             active[c] = 0;
@@ -348,6 +363,15 @@ __global__ void k_scal_beta(const double *__restrict__ part, int pstride, int np
             if (c > 0) atomicAdd(count + 1, 1);
         }
     }
+}
+
+// Restart of the probe columns as PCG: rho = r^T z for the still active columns.
+__global__ void k_scal_restart(const double *__restrict__ part, int pstride, int nparts, double *__restrict__ sc,
+                               const int *__restrict__ active)
+{
+    const int c = blockIdx.x + 1;
+    double s = block_sum(part + (int64_t)c * pstride, nparts);
+    if (threadIdx.x == 0 && active[c]) sc[c * kScal + S_RHO] = s;
 }
 
 // x += alpha p ; r -= alpha q ; partial r^T r.  Probe group: thread t owns column t % m.
@@ -411,21 +435,43 @@ __global__ void k_update(int64_t n, int m, T *__restrict__ xz, T *__restrict__ r
     }
 }
 
-// p = r + beta p for active columns.
+// p = r + beta p for active columns.  CTAs [0, gz) cover the probe group: thread t owns the four
+// columns 4 (t % (m/4)) .. +3 for the whole launch (beta and the active flags stay in registers)
+// and strides over rows; the remaining CTAs cover the y column.
 template <class T>
 __global__ void k_direction(int64_t n, int m, const T *__restrict__ rz, T *__restrict__ pz, const T *__restrict__ ry,
-                            T *__restrict__ py, const double *__restrict__ sc, const int *__restrict__ active)
+                            T *__restrict__ py, const double *__restrict__ sc, const int *__restrict__ active, int gz)
 {
-    const int64_t tz = n * m;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tz + n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        if (e < tz) {
-            int c = (int)(e % m) + 1;
-            if (active[c]) pz[e] = rz[e] + (T)sc[c * kScal + S_BETA] * pz[e];
-        } else {
-            int64_t i = e - tz;
-            if (active[0]) py[i] = ry[i] + (T)sc[S_BETA] * py[i];
+    if ((int)blockIdx.x < gz) {
+        const int cgs = m / 4;
+        const int rows_per_step = blockDim.x / cgs;
+        if ((int)threadIdx.x >= cgs * rows_per_step) return;
+        const int cg = threadIdx.x % cgs;
+        const int c0 = cg * 4;
+        T b[4];
+        bool act[4], all = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            act[q] = active[c0 + q + 1] != 0;
+            b[q] = (T)sc[(c0 + q + 1) * kScal + S_BETA];
+            all = all && act[q];
         }
+        for (int64_t i = (int64_t)blockIdx.x * rows_per_step + threadIdx.x / cgs; i < n;
+             i += (int64_t)gz * rows_per_step) {
+            const int64_t e = i * m + c0;
+            T r4[4], p4[4];
+            load_k<T, 4>(rz + e, r4);
+            load_k<T, 4>(pz + e, p4);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) p4[q] = (all || act[q]) ? r4[q] + b[q] * p4[q] : p4[q];
+            store_k<T, 4>(pz + e, p4);
+        }
+    } else {
+        if (!active[0]) return;
+        const T b = (T)sc[S_BETA];
+        const int gy = gridDim.x - gz;
+        for (int64_t i = (int64_t)(blockIdx.x - gz) * blockDim.x + threadIdx.x; i < n; i += (int64_t)gy * blockDim.x)
+            py[i] = ry[i] + b * py[i];
     }
 }
 
@@ -531,6 +577,7 @@ __global__ void k_sum_parts(const double *__restrict__ part, int cnt, int groups
 // ---------------------------------------------------------------------------------------------
 struct CGBuffers {
     void *xz, *rz, *pz, *qz, *xy, *ry, *py, *qy;
+    void *zz, *zy;   // preconditioned residuals (block-Jacobi PCG)
 };
 
 template <int K>
@@ -756,10 +803,16 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
     float4 *s_val = reinterpret_cast<float4 *>(rb_sh + sizeof(int) * W * kWarp);  // W x 32 x 2
     double *red = reinterpret_cast<double *>(rb_sh + sizeof(int) * W * kWarp + sizeof(float4) * W * kWarp * 2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t b_begin = blk_split[blockIdx.x], b_end = blk_split[blockIdx.x + 1];
+    // Chunks of W consecutive row blocks go round-robin to the CTAs (one per SM), a warp per
+    // block: all SMs sweep the Morton order side by side, so the P rows gathered at any moment
+    // lie in a narrow window that stays resident in L2.
+    (void)blk_split;
+    const int64_t nblk = (n + kRB - 1) / kRB;
     Acc32 dz[K];
     Acc32 dy;
-    for (int64_t b = b_begin + wid; b < b_end; b += W) {
+    for (int64_t chunk = blockIdx.x; chunk * W < nblk; chunk += gridDim.x) {
+        const int64_t b = chunk * W + wid;
+        if (b >= nblk) continue;
         const int64_t r0 = b * kRB;
         const int nrows = (int)(n - r0 < kRB ? n - r0 : kRB);
         float acc[kRB][K];
@@ -874,6 +927,321 @@ gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride
     return GP2S_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Block-Jacobi preconditioner on Morton-consecutive blocks of kBJ rows.
+//
+// The paper leaves the solver's preconditioning open.  M = blockdiag(Ah_bb) = L L^T over blocks
+// of kBJ consecutive rows of the Morton order: spatially close points whose mutual covariances are
+// the largest entries of their rows, so these small dense blocks cut the iteration count
+// several-fold against plain Jacobi scaling.  The probe columns run their first k steps as plain
+// CG on Ah (those coefficients are Ah's Lanczos tridiagonal for SLQ; SLQ on the preconditioned
+// operator L^{-1} Ah L^{-T} would have a far larger probe variance) and are then restarted as PCG
+// with M to finish the solves the gradient needs; the y column runs PCG throughout.
+// ---------------------------------------------------------------------------------------------
+constexpr int kBJ = 64;
+constexpr int kPCThreads = 256;
+
+// One CTA per block: dense FP64 block from the CSR, Cholesky, L^{-1}; writes M^{-1} = L^{-T} L^{-1}
+// (FP32, symmetric) and the block's log|M_b|.
+// Rows beyond n (last block) are padded with the identity.
+__global__ void __launch_bounds__(kPCThreads)
+k_bj_build(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const double *__restrict__ val64,
+           int64_t n, float *__restrict__ Minv32, double *__restrict__ logdet_blk,
+           int *__restrict__ bad)
+{
+    extern __shared__ double bj_sh[];
+    double (*S)[kBJ + 1] = reinterpret_cast<double (*)[kBJ + 1]>(bj_sh);                    // L
+    double (*V)[kBJ + 1] = reinterpret_cast<double (*)[kBJ + 1]>(bj_sh + kBJ * (kBJ + 1));  // L^{-1}
+    const int64_t b = blockIdx.x;
+    const int64_t i0 = b * kBJ;
+    const int nb = (int)(n - i0 < kBJ ? n - i0 : kBJ);
+    for (int t = threadIdx.x; t < kBJ * kBJ; t += blockDim.x) {
+        int i = t / kBJ, j = t % kBJ;
+        S[i][j] = (i == j && i >= nb) ? 1.0 : 0.0;
+        V[i][j] = 0.0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = wid; i < nb; i += kPCThreads / kWarp) {
+        for (int p = rowptr[i0 + i] + lane; p < rowptr[i0 + i + 1]; p += kWarp) {
+            int64_t j = col[p] - i0;
+            if (j >= 0 && j < nb) S[i][j] = val64[p];
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < kBJ; ++j) {
+        if (threadIdx.x == 0) {
+            double d = S[j][j];
+            if (!(d > 0.0)) { atomicOr(bad, 1); d = 1.0; }
+            S[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < kBJ; i += blockDim.x) S[i][j] /= S[j][j];
+        __syncthreads();
+        for (int t = threadIdx.x; t < kBJ * kBJ; t += blockDim.x) {
+            int i = t / kBJ, k = t % kBJ;
+            if (i > j && k > j && k <= i) S[i][k] -= S[i][j] * S[k][j];
+        }
+        __syncthreads();
+    }
+    // L^{-1}: column c solves L v = e_c by forward substitution (one thread per column)
+    if (threadIdx.x < kBJ) {
+        const int cc = threadIdx.x;
+        V[cc][cc] = 1.0 / S[cc][cc];
+        for (int i = cc + 1; i < kBJ; ++i) {
+            double s = 0.0;
+            for (int k = cc; k < i; ++k) s += S[i][k] * V[k][cc];
+            V[i][cc] = -s / S[i][i];
+        }
+    }
+    __syncthreads();
+    float *Mb = Minv32 + b * kBJ * kBJ;
+    for (int t = threadIdx.x; t < kBJ * kBJ; t += blockDim.x) {
+        int i = t / kBJ, j = t % kBJ;
+        // (L^{-T} L^{-1})_ij = sum_k V[k][i] V[k][j], k >= max(i, j)
+        double s = 0.0;
+        for (int k = i > j ? i : j; k < kBJ; ++k) s += V[k][i] * V[k][j];
+        Mb[t] = (float)s;
+    }
+    if (threadIdx.x == 0) {
+        double ld = 0.0;
+        for (int i = 0; i < nb; ++i) ld += log(S[i][i]);
+        logdet_blk[b] = 2.0 * ld;
+    }
+}
+
+// Out (kBJ x m, row stride m) = Mat (kBJ x kBJ, given transposed in shared memory: MT[k][i] =
+// Mat[i][k]) x In (kBJ x m in shared memory).  Each thread owns 4 x 4 output tiles.
+template <class Fn>
+__device__ __forceinline__ void bj_tile_mm(const float *__restrict__ MT, const float *__restrict__ In, int m, Fn &&emit)
+{
+    const int cgroups = m / 4;
+    const int tiles = (kBJ / 4) * cgroups;
+    for (int tt = threadIdx.x; tt < tiles; tt += blockDim.x) {
+        const int rg = tt / cgroups, cg = tt - rg * cgroups;
+        const int i0 = rg * 4, c0 = cg * 4;
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
+#pragma unroll 8
+        for (int k = 0; k < kBJ; ++k) {
+            const float4 mv = *reinterpret_cast<const float4 *>(MT + k * kBJ + i0);
+            const float4 iv = *reinterpret_cast<const float4 *>(In + k * m + c0);
+            const float ma[4] = {mv.x, mv.y, mv.z, mv.w}, ia[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(ma[a], ia[q], acc[a][q]);
+        }
+        emit(i0, c0, acc);
+    }
+}
+
+// Fused PCG step on kBJ-row blocks.  INIT: x = 0, r = rhs, z = M^{-1} r, p = z.  UPDATE:
+// x += alpha p, r -= alpha q, z = M^{-1} r.  RESTART (a CG column switching to PCG): x and r kept,
+// z = M^{-1} r, p = z.  All emit per-CTA partial dots r^T z and r^T r per column.
+// CTAs [0, gz) work on the probe group (n x m), CTAs [gz, gridDim) on the y column.
+enum { PC_INIT = 0, PC_UPDATE = 1, PC_RESTART = 2 };
+template <int MODE>
+__global__ void __launch_bounds__(kPCThreads, 3)
+k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv32, float *__restrict__ xz,
+          float *__restrict__ rz, float *__restrict__ pz, const float *__restrict__ qz, float *__restrict__ zz,
+          float *__restrict__ xy, float *__restrict__ ry, float *__restrict__ py, const float *__restrict__ qy,
+          float *__restrict__ zy, const double *__restrict__ rhs_y, const double *__restrict__ sc,
+          double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride)
+{
+    constexpr bool INIT = MODE == PC_INIT;
+    constexpr bool SETP = MODE != PC_UPDATE;   // p = z (INIT, RESTART)
+    extern __shared__ __align__(16) float pc_sh[];
+    if ((int)blockIdx.x < gz) {
+        float *MT = pc_sh;                       // M^{-1} (symmetric, so no transpose)
+        float *R = pc_sh + kBJ * kBJ;            // kBJ x m residual block
+        float *Pd = R + kBJ * m;                 // 16 x m partial dot rows (r^T z), then (r^T r)
+        double acc_rz = 0.0, acc_rr = 0.0;       // thread c < m: this CTA's column sums
+        // elementwise phase: thread t owns the 4 columns 4 (t % cgs) .. +3 of rows t / cgs + k rps
+        const int cgs = m / 4;
+        const int rps = kPCThreads / cgs;
+        const int ecg = threadIdx.x % cgs, er0 = threadIdx.x / cgs;
+        const bool eth = er0 < rps;
+        float a4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            a4[q] = MODE == PC_UPDATE ? (float)sc[(ecg * 4 + q + 1) * kScal + S_ALPHA] : 0.0f;
+        for (int64_t b = blockIdx.x; b < nblk; b += gz) {
+            const int64_t i0 = b * kBJ;
+            const int nb = (int)(n - i0 < kBJ ? n - i0 : kBJ);
+            const float4 *Mg = reinterpret_cast<const float4 *>(Minv32 + b * kBJ * kBJ);
+            for (int t = threadIdx.x; t < kBJ * kBJ / 4; t += blockDim.x) reinterpret_cast<float4 *>(MT)[t] = Mg[t];
+            if (eth) {
+                for (int i = er0; i < kBJ; i += rps) {
+                    float r4[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (i < nb) {
+                        const int64_t e = (i0 + i) * m + ecg * 4;
+                        load_k<float, 4>(rz + e, r4);
+                        if (MODE == PC_INIT) {
+                            const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+                            store_k<float, 4>(xz + e, zero4);   // the right-hand side was written into r
+                        } else if (MODE == PC_UPDATE) {
+                            float x4[4], p4[4], q4[4];
+                            load_k<float, 4>(xz + e, x4);
+                            load_k<float, 4>(pz + e, p4);
+                            load_k<float, 4>(qz + e, q4);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                x4[q] = x4[q] + a4[q] * p4[q];
+                                r4[q] = r4[q] - a4[q] * q4[q];
+                            }
+                            store_k<float, 4>(xz + e, x4);
+                            store_k<float, 4>(rz + e, r4);
+                        }
+                    }
+                    *reinterpret_cast<float4 *>(R + i * m + ecg * 4) = make_float4(r4[0], r4[1], r4[2], r4[3]);
+                }
+            }
+            __syncthreads();
+            // z = M^{-1} r, written with the partial dots of this block
+            bj_tile_mm(MT, R, m, [&](int it, int c0, float (&acc)[4][4]) {
+                float drz[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    if (it + a >= nb) continue;
+                    const int64_t e = (i0 + it + a) * m + c0;
+                    *reinterpret_cast<float4 *>(zz + e) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+                    if (SETP)
+                        *reinterpret_cast<float4 *>(pz + e) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) drz[q] = fmaf(R[(it + a) * m + c0 + q], acc[a][q], drz[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) Pd[(it / 4) * m + c0 + q] = drz[q];
+            });
+            __syncthreads();
+            if ((int)threadIdx.x < m) {
+                float srz = 0.0f, srr = 0.0f;
+                for (int g = 0; g < 16; ++g) srz += Pd[g * m + threadIdx.x];
+                for (int i = 0; i < nb; ++i) {
+                    const float rv = R[i * m + threadIdx.x];
+                    srr = fmaf(rv, rv, srr);
+                }
+                acc_rz += (double)srz;
+                acc_rr += (double)srr;
+            }
+            __syncthreads();
+        }
+        if ((int)threadIdx.x < m) {
+            part_rz[(int64_t)(threadIdx.x + 1) * pstride + blockIdx.x] = acc_rz;
+            part_rr[(int64_t)(threadIdx.x + 1) * pstride + blockIdx.x] = acc_rr;
+        }
+    } else {
+        // y column: the CTA's four 64-thread groups each take one block; thread i of a group owns
+        // row i and forms z_i = sum_k Minv[k][i] r_k (coalesced rows of the symmetric M^{-1})
+        constexpr int G = kPCThreads / kBJ;
+        float *R = pc_sh;                         // G x kBJ
+        __shared__ double red[2][kPCThreads / kWarp];
+        const int gy = gridDim.x - gz;
+        const int cb = blockIdx.x - gz;
+        const int sub = threadIdx.x / kBJ;
+        double arz = 0.0, arr = 0.0;
+        const double alpha = MODE == PC_UPDATE ? sc[S_ALPHA] : 0.0;
+        const float a = (float)alpha;
+        for (int64_t bg = cb; bg * G < nblk; bg += gy) {
+            const int64_t b = bg * G + sub;
+            const bool live = b < nblk;
+            const int64_t i0 = b * kBJ;
+            const int nb = live ? (int)(n - i0 < kBJ ? n - i0 : kBJ) : 0;
+            {
+                const int i = threadIdx.x % kBJ;
+                float r = 0.0f;
+                if (i < nb) {
+                    const int64_t e = i0 + i;
+                    if (MODE == PC_INIT) {
+                        r = (float)rhs_y[e];
+                        ry[e] = r;
+                        xy[e] = 0.0f;
+                    } else if (MODE == PC_RESTART) {
+                        r = ry[e];
+                    } else {
+                        r = ry[e];
+                        if (alpha != 0.0) {
+                            xy[e] = xy[e] + a * py[e];
+                            r = r - a * qy[e];
+                            ry[e] = r;
+                        }
+                    }
+                }
+                R[sub * kBJ + i] = r;
+            }
+            __syncthreads();
+            if (live) {
+                const int i = threadIdx.x % kBJ;
+                float z = 0.0f;
+                const float *Mb = Minv32 + b * kBJ * kBJ;
+                const float *Rb = R + sub * kBJ;
+#pragma unroll 8
+                for (int k = 0; k < kBJ; ++k) z = fmaf(Mb[k * kBJ + i], Rb[k], z);
+                if (i < nb) {
+                    zy[i0 + i] = z;
+                    if (SETP) py[i0 + i] = z;
+                    arz = fma((double)Rb[i], (double)z, arz);
+                    arr = fma((double)Rb[i], (double)Rb[i], arr);
+                }
+            }
+            __syncthreads();
+        }
+        double v1 = arz, v2 = arr;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+            v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[0][threadIdx.x >> 5] = v1;
+            red[1][threadIdx.x >> 5] = v2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int w = 0; w < kPCThreads / kWarp; ++w) { s1 += red[0][w]; s2 += red[1][w]; }
+            part_rz[cb] = s1;
+            part_rr[cb] = s2;
+        }
+    }
+}
+
+size_t pc_smem(int m) { return sizeof(float) * ((size_t)kBJ * kBJ + (size_t)kBJ * (m > 0 ? m : 1) + 16 * (size_t)(m > 0 ? m : 1)) + 64; }
+
+// Build the block-Jacobi factors of the current matrix (FP64 blocks -> FP32 L and M^{-1}).
+gp2s_status build_block_jacobi(gp2s_ctx *c)
+{
+    const int64_t n = c->A.n;
+    const int64_t nblk = ceil_div(n, kBJ);
+    GP2S_TRY(ensure(c, c->bj_Minv, sizeof(float) * (size_t)nblk * kBJ * kBJ));
+    GP2S_TRY(ensure(c, c->bj_ld, sizeof(double) * (size_t)nblk + 64));
+    GP2S_TRY(ensure(c, c->counters, 256));
+    int *bad = reinterpret_cast<int *>(c->counters.as<char>() + 208);
+    GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    const size_t smem = sizeof(double) * 2 * kBJ * (kBJ + 1);
+    GP2S_CUDA(c, cudaFuncSetAttribute(k_bj_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_bj_build<<<(unsigned)nblk, kPCThreads, smem, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(),
+                                                                c->val64.as<double>(), n, c->bj_Minv.as<float>(),
+                                                                c->bj_ld.as<double>(), bad);
+    GP2S_LAUNCH(c);
+    // log|M| = sum of the block log-determinants (fixed-order host sum)
+    std::vector<double> ld((size_t)nblk);
+    int hbad = 0;
+    GP2S_CUDA(c, cudaMemcpyAsync(ld.data(), c->bj_ld.p, sizeof(double) * nblk, cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hbad) return set_err(c, GP2S_ENOTPD, "block-Jacobi: a diagonal block is not positive definite");
+    double s = 0.0;
+    for (double v : ld) s += v;
+    c->bj_logdet = s;
+    c->bj_valid = true;
+    return GP2S_OK;
+}
+
 // Build the RB8 copy of the FP32 matrix (count -> scan -> fill) and its per-CTA block ranges.
 gp2s_status build_rb8(gp2s_ctx *c)
 {
@@ -933,10 +1301,44 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     int *flags = active + kMaxCols;   // [0] breakdown, [1] active columns, [2] active probe columns
     GP2S_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(int) * 4, c->stream));
 
-    k_cg_init<T><<<nbz + nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, rhs_y, (T *)B.xz, (T *)B.rz, (T *)B.pz,
-                                                  (T *)B.xy, (T *)B.ry, (T *)B.py, part, pstride, nbz);
+    // Block-Jacobi PCG (FP32 vectors, when the preconditioner is built) or plain CG on Ah.  The y
+    // column is preconditioned from the start; the probe columns only when no SLQ records are
+    // wanted, otherwise they run kmin_probe plain CG steps (Ah's Lanczos coefficients) and are
+    // then restarted as PCG.
+    const bool pc_avail = std::is_same<T, float>::value && c->bj_valid;
+    bool pcy = pc_avail;
+    bool pcz = pc_avail && kmin_probe == 0;
+    const int64_t nblk = ceil_div(n, kBJ);
+    // probe group: one 64-row block per CTA step, ~6 CTAs per SM; y column: 4 blocks per CTA step
+    const int pgz = m > 0 ? (int)std::min<int64_t>((int64_t)c->num_sms * 6, nblk) : 0;
+    const int pgy = (int)std::min<int64_t>(kMaxPartBlocks, ceil_div(nblk, kPCThreads / kBJ));
+    GP2S_TRY(ensure(c, c->partials, sizeof(double) * (size_t)pstride * kMaxCols * 2));
+    part = c->partials.as<double>();
+    double *part_rr = part + (size_t)pstride * kMaxCols;
+    const float *Minv = pc_avail ? c->bj_Minv.as<float>() : nullptr;
+    if (pc_avail) {
+        const size_t smem = pc_smem(m);
+        GP2S_CUDA(c, cudaFuncSetAttribute(k_pc_step<PC_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GP2S_CUDA(c, cudaFuncSetAttribute(k_pc_step<PC_UPDATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GP2S_CUDA(c, cudaFuncSetAttribute(k_pc_step<PC_RESTART>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+#define GP2S_PC(MODE, GZ, GY, MM)                                                                                \
+    k_pc_step<MODE><<<(GZ) + (GY), kPCThreads, pc_smem(MM), c->stream>>>(                                       \
+        n, MM, nblk, GZ, Minv, (float *)B.xz, (float *)B.rz, (float *)B.pz, (const float *)B.qz, (float *)B.zz, \
+        (float *)B.xy, (float *)B.ry, (float *)B.py, (const float *)B.qy, (float *)B.zy, rhs_y, sc, part, part_rr, pstride)
+    // initial state: probe group then y column
+    if (m > 0) {
+        if (pcz) GP2S_PC(PC_INIT, pgz, 0, m);
+        else k_cg_init<T><<<nbz, ut, 0, c->stream>>>(n, m, rhs_y, (T *)B.xz, (T *)B.rz, (T *)B.pz, (T *)B.xy,
+                                                      (T *)B.ry, (T *)B.py, part, pstride, nbz);
+        GP2S_LAUNCH(c);
+    }
+    if (pcy) GP2S_PC(PC_INIT, 0, pgy, 0);
+    else k_cg_init<T><<<nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, rhs_y, (T *)B.xz, (T *)B.rz, (T *)B.pz,
+                                                  (T *)B.xy, (T *)B.ry, (T *)B.py, part, pstride, 0);
     GP2S_LAUNCH(c);
-    k_scal_init<<<k, 256, 0, c->stream>>>(part, pstride, nby, nbz, sc, active, tol_y, tol_z);
+    k_scal_init<<<k, 256, 0, c->stream>>>(part, part_rr, pstride, pcy ? pgy : nby, pcz ? pgz : nbz, sc, active, tol_y,
+                                          tol_z, pcy, pcz);
     GP2S_LAUNCH(c);
 
     const int check_every = 8;
@@ -944,27 +1346,48 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     int *hcount = reinterpret_cast<int *>(c->hbuf.p);
     int mc = m;          // probe columns still iterated; 0 once every probe column has stopped
     for (; it < max_iter; ++it) {
+        if (pc_avail && !pcz && mc > 0 && it == kmin_probe) {
+            // the SLQ steps are recorded: restart the probe columns as PCG from their iterates
+            GP2S_PC(PC_RESTART, pgz, 0, mc);
+            GP2S_LAUNCH(c);
+            k_scal_restart<<<mc, 256, 0, c->stream>>>(part, pstride, pgz, sc, active);
+            GP2S_LAUNCH(c);
+            pcz = true;
+        }
         const int kc = 1 + mc;
         int np = nb;
         GP2S_TRY((launch_spmm<T, V>(c, mc, true, val, B, part, pstride, nb, rsplit, active, &np)));
         k_scal_alpha<<<kc, 256, 0, c->stream>>>(part, pstride, np, sc, active, flags, rec, ksteps);
         GP2S_LAUNCH(c);
         GP2S_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int) * 2, c->stream));
-        k_update<T><<<(mc > 0 ? nbz : 0) + nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, (T *)B.xz, (T *)B.rz,
-                                                                     (const T *)B.pz, (const T *)B.qz, (T *)B.xy,
-                                                                     (T *)B.ry, (const T *)B.py, (const T *)B.qy, sc,
-                                                                     part, pstride, mc > 0 ? nbz : 0);
-        GP2S_LAUNCH(c);
-        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, pstride, nby, nbz, sc, active, flags + 1, rec, ksteps,
-                                               kmin_probe);
-        GP2S_LAUNCH(c);
-        {
-            int64_t tot = n * (int64_t)(mc + 1);
-            unsigned gb = (unsigned)std::min<int64_t>(ceil_div(tot, 256), 152 * 8);
-            k_direction<T><<<gb, 256, 0, c->stream>>>(n, mc, (const T *)B.rz, (T *)B.pz, (const T *)B.ry,
-                                                       (T *)B.py, sc, active);
+        if (mc > 0) {
+            if (pcz) GP2S_PC(PC_UPDATE, pgz, 0, mc);
+            else k_update<T><<<nbz, ut, 0, c->stream>>>(n, m, (T *)B.xz, (T *)B.rz, (const T *)B.pz, (const T *)B.qz,
+                                                         (T *)B.xy, (T *)B.ry, (const T *)B.py, (const T *)B.qy, sc,
+                                                         part, pstride, nbz);
             GP2S_LAUNCH(c);
         }
+        if (pcy) GP2S_PC(PC_UPDATE, 0, pgy, 0);
+        else k_update<T><<<nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, (T *)B.xz, (T *)B.rz, (const T *)B.pz,
+                                                     (const T *)B.qz, (T *)B.xy, (T *)B.ry, (const T *)B.py,
+                                                     (const T *)B.qy, sc, part, pstride, 0);
+        GP2S_LAUNCH(c);
+        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, part_rr, pstride, pcy ? pgy : nby, pcz ? pgz : nbz, sc, active,
+                                               flags + 1, rec, ksteps, kmin_probe, pcy, pcz);
+        GP2S_LAUNCH(c);
+        {
+            // direction: p = z + beta p (z = M^{-1} r for a preconditioned group, z = r otherwise)
+            const int cgs = mc / 4;
+            const int dthreads = mc > 0 ? cgs * std::max(1, 256 / cgs) : 256;
+            const int dgz = mc > 0 ? (int)std::min<int64_t>(152 * 8, ceil_div(n, dthreads / cgs)) : 0;
+            const int dgy = (int)std::min<int64_t>(152 * 2, ceil_div(n, dthreads));
+            const T *zzp = pcz ? (const T *)B.zz : (const T *)B.rz;
+            const T *zyp = pcy ? (const T *)B.zy : (const T *)B.ry;
+            k_direction<T><<<dgz + dgy, dthreads, 0, c->stream>>>(n, mc, zzp, (T *)B.pz, zyp, (T *)B.py, sc, active,
+                                                                 dgz);
+            GP2S_LAUNCH(c);
+        }
+#undef GP2S_PC
         if ((it + 1) % check_every == 0 || it + 1 == max_iter) {
             GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
             GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1024,13 +1447,17 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
     const size_t es = mixed ? sizeof(float) : sizeof(double);
     const int mm = m > 0 ? m : 0;
     // vectors: y group 4 n, probe group 4 n m
-    GP2S_TRY(ensure(c, c->vec, es * (size_t)n * (4 + 4 * (size_t)mm) + 256));
+    GP2S_TRY(ensure(c, c->vec, es * (size_t)n * (5 + 5 * (size_t)mm) + 256));
     CGBuffers B;
     char *base = c->vec.as<char>();
     size_t nz = es * (size_t)n * mm;
     B.xz = base; B.rz = base + nz; B.pz = base + 2 * nz; B.qz = base + 3 * nz;
     char *yb = base + 4 * nz;
     B.xy = yb; B.ry = yb + es * n; B.py = yb + 2 * es * n; B.qy = yb + 3 * es * n;
+    B.zz = yb + 4 * es * n;
+    B.zy = (char *)B.zz + nz;
+    // block-Jacobi preconditioner (FP32 path, opts.precond == 2)
+    if (mixed && A.opts.precond == 2 && !c->bj_valid) GP2S_TRY(build_block_jacobi(c));
     // FP64 refinement vectors: b64, xhat64, res64, a64 (solution in sorted order)
     GP2S_TRY(ensure(c, c->vec64, sizeof(double) * (size_t)n * 4 + 256));
     double *b64 = c->vec64.as<double>();
@@ -1054,13 +1481,16 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
     const gp2s_opts &o = A.opts;
     if (mixed && mm > 0 && !c->rb_valid) GP2S_TRY(build_rb8(c));
     const double tol_first = mixed ? o.tol_inner : std::min(o.tol_inner, 0.1 * o.tol_refine);
+    // probe columns: the k SLQ steps always; solved to tol_probe only when the gradient needs
+    // u_s = A^{-1} D^{1/2} z_s (a relative tolerance of 1 stops them right after the k steps)
+    const double tol_z = c->probes_for_grad ? o.tol_probe : 1.0;
     int iy = 0, iz = 0;
     bool brk = false;
     if (mixed)
-        GP2S_TRY((cg_run<float, float>(c, mm, c->val32.as<float>(), B, b64, tol_first, o.tol_probe, mm > 0 ? ksteps : 0,
+        GP2S_TRY((cg_run<float, float>(c, mm, c->val32.as<float>(), B, b64, tol_first, tol_z, mm > 0 ? ksteps : 0,
                                        ksteps, rec, o.max_iter, &iy, &iz, &brk)));
     else
-        GP2S_TRY((cg_run<double, double>(c, mm, c->val64.as<double>(), B, b64, tol_first, o.tol_probe,
+        GP2S_TRY((cg_run<double, double>(c, mm, c->val64.as<double>(), B, b64, tol_first, tol_z,
                                          mm > 0 ? ksteps : 0, ksteps, rec, o.max_iter, &iy, &iz, &brk)));
     res->iters_probes = iz;
     int total_y = iy;
@@ -1082,8 +1512,10 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
         if (!(relres > o.tol_refine) || outer >= o.max_outer) break;
         ++outer;
         int iy2 = 0, iz2 = 0;
+        // the correction only has to shrink the residual by tol_refine / relres (with a 10x margin)
+        const double tol_corr = std::min(0.5, std::max(o.tol_inner, 0.1 * o.tol_refine / relres));
         if (mixed)
-            GP2S_TRY((cg_run<float, float>(c, 0, c->val32.as<float>(), B, r64, o.tol_inner, o.tol_probe, 0, 0, nullptr,
+            GP2S_TRY((cg_run<float, float>(c, 0, c->val32.as<float>(), B, r64, tol_corr, o.tol_probe, 0, 0, nullptr,
                                            o.max_iter, &iy2, &iz2, &brk)));
         else
             GP2S_TRY((cg_run<double, double>(c, 0, c->val64.as<double>(), B, r64, std::min(o.tol_inner, 0.1 * o.tol_refine),
