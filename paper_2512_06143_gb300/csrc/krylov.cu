@@ -785,7 +785,7 @@ k_rb_build(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, 
 }
 
 template <int K> struct RBCfg {
-    static constexpr int threads = K <= 2 ? 1024 : 512;
+    static constexpr int threads = 512;   // 16 warps, ~128 registers each: deep unrolled gathers
     static constexpr int warps = threads / kWarp;
 };
 
@@ -845,7 +845,7 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             s_val[(wid * kWarp + lane) * 2 + 1] = v1;
             __syncwarp();
             const int cnt = min(kWarp, e1 - eb);
-#pragma unroll 2
+#pragma unroll 8
             for (int t = 0; t < cnt; ++t) {
                 const int j = s_col[wid * kWarp + t];
                 const float4 a0 = s_val[(wid * kWarp + t) * 2], a1 = s_val[(wid * kWarp + t) * 2 + 1];
