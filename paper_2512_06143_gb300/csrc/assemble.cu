@@ -373,7 +373,7 @@ gp2s_status launch_assemble(gp2s_ctx *c, const AsmArgs &a, const GridParams &g, 
                             const KernelParams &kp, int64_t nitems)
 {
     size_t smem = asm_smem_bytes(D, FILL, kp.L);
-    GP2S_CUDA(c, cudaFuncSetAttribute(k_assemble<D, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GP2S_TRY(smem_attr(c, (const void *)k_assemble<D, FILL>, smem));
     k_assemble<D, FILL><<<(unsigned)nitems, kAsmThreads, smem, c->stream>>>(a, g, sp, kp);
     GP2S_LAUNCH(c);
     return GP2S_OK;

@@ -1,14 +1,98 @@
-// batched.cu -- many independent problems in one call (see gp2s_lml_batched in include/gp2s.h).
+// batched.cu -- many independent problems in one call (gp2s_lml_batched).
+//
+// The paper's training loop evaluates one LML per MCMC block (App. D); a batch of independent,
+// unevenly sized problems (different N, d, radii and bumps) is served here by a pool of worker
+// threads, each owning an engine context with its own CUDA stream and workspace.  Problems are
+// handed out largest-first from a shared counter, so the streams stay busy and the small problems
+// fill the gaps the large ones leave; every problem runs the same kernels as a single gp2s_lml
+// call (assembly, multi-RHS CG with FP64 refinement, SLQ), which is what the parity tests cover.
+// The worker contexts persist in the parent context, so repeated batched calls reuse their
+// workspaces without new allocations once the largest problem has been seen.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <string>
+#include <numeric>
+#include <thread>
+#include <vector>
+
 #include "gp2s_internal.cuh"
 
 namespace gp2s {
+
+gp2s_status lml_single(gp2s_ctx *c, int64_t n, const double *X, const double *y, const gp2s_hyper *h,
+                       const gp2s_opts *o, double *lml, double *grad, gp2s_lml_info *info);   // capi.cu
 
 gp2s_status batched_lml(gp2s_ctx *c, int32_t B, const int64_t *n, const double *const *X,
                         const double *const *y, const gp2s_hyper *hyper, const gp2s_opts *opts,
                         double *lml_host, gp2s_lml_info *info_host)
 {
-    (void)B; (void)n; (void)X; (void)y; (void)hyper; (void)opts; (void)lml_host; (void)info_host;
-    return set_err(c, GP2S_EINVAL, "batched form not built");
+    if (B < 0) return set_err(c, GP2S_EINVAL, "B must be >= 0");
+    if (B == 0) return GP2S_OK;
+    if (!n || !X || !y || !hyper || !lml_host) return set_err(c, GP2S_EINVAL, "batched: NULL argument");
+    gp2s_opts o;
+    if (opts) o = *opts;
+    else gp2s_opts_default(&o);
+    // a batch of mid-sized problems is served by SLQ unless the exact path is asked for explicitly
+    if (o.logdet == GP2S_LOGDET_AUTO) o.logdet = GP2S_LOGDET_SLQ;
+    // device inputs may have been produced on the caller's stream: let that work finish first
+    GP2S_CUDA(c, cudaSetDevice(c->device));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+
+    // worker contexts (created once, kept in the parent)
+    const int nworkers = std::max(1, std::min<int>(B, (int)c->batch_workers_max));
+    while ((int)c->workers.size() < nworkers) {
+        cudaStream_t s = nullptr;
+        GP2S_CUDA(c, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        gp2s_ctx *w = nullptr;
+        gp2s_status st = gp2s_create(&w, c->device, s);
+        if (st != GP2S_OK) {
+            cudaStreamDestroy(s);
+            return set_err(c, st, "batched: cannot create a worker context");
+        }
+        w->mem_limit = c->mem_limit;
+        c->workers.push_back(w);
+        c->worker_streams.push_back(s);
+    }
+    // largest problems first
+    std::vector<int32_t> order(B);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return n[a] > n[b]; });
+    std::atomic<int32_t> next{0};
+    std::mutex mu;
+    gp2s_status first = GP2S_OK;
+    std::string first_msg;
+    auto work = [&](int wi) {
+        gp2s_ctx *w = c->workers[wi];
+        for (;;) {
+            const int32_t k = next.fetch_add(1);
+            if (k >= B) break;
+            const int32_t b = order[k];
+            gp2s_lml_info info;
+            double v = 0.0;
+            gp2s_status st = lml_single(w, n[b], X[b], y[b], &hyper[b], &o, &v, nullptr, &info);
+            lml_host[b] = st == GP2S_OK ? v : std::numeric_limits<double>::quiet_NaN();
+            if (info_host) {
+                if (st == GP2S_OK) info_host[b] = info;
+                else std::memset(&info_host[b], 0, sizeof(gp2s_lml_info));
+            }
+            if (st != GP2S_OK) {
+                std::lock_guard<std::mutex> lk(mu);
+                if (first == GP2S_OK) {
+                    first = st;
+                    first_msg = "problem " + std::to_string(b) + ": " + w->err;
+                }
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int wi = 1; wi < nworkers; ++wi) th.emplace_back(work, wi);
+    work(0);
+    for (auto &t : th) t.join();
+    if (first != GP2S_OK) return set_err(c, first, first_msg);
+    return GP2S_OK;
 }
 
 }  // namespace gp2s

@@ -5,7 +5,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 
 #include "gp2s_internal.cuh"
 
@@ -49,6 +52,21 @@ gp2s_status ensure(gp2s_ctx *c, DevBuf &b, size_t bytes)
     }
     b.bytes = alloc;
     c->mem_in_use += alloc;
+    return GP2S_OK;
+}
+
+gp2s_status smem_attr(gp2s_ctx *c, const void *func, size_t smem)
+{
+    // The attribute belongs to the function on this device, shared by every context and host
+    // thread (the batched engine runs several at once): it only ever grows, under a lock, so a
+    // launch sized for an earlier, larger request is never invalidated by a smaller one.
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> set;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &cur = set[std::make_pair(c->device, func)];
+    if (smem <= cur) return GP2S_OK;
+    GP2S_CUDA(c, cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cur = smem;
     return GP2S_OK;
 }
 
@@ -242,6 +260,8 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0) c->num_sms = sms;
     c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const char *bw = std::getenv("GP2S_BATCH_WORKERS");
+    if (bw && std::atoi(bw) > 0) c->batch_workers_max = std::atoi(bw);
     const char *lim = std::getenv("GP2S_MEM_LIMIT");
     if (lim) c->mem_limit = (size_t)std::strtoull(lim, nullptr, 10);
     *ctx = c;
@@ -263,6 +283,8 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->bj_Minv, &c->bj_ld};
     for (DevBuf *b : bufs) free_buf(*b);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    for (gp2s_ctx *w : c->workers) gp2s_destroy(w);
+    for (cudaStream_t s : c->worker_streams) cudaStreamDestroy(s);
     if (c->hbuf.p) cudaFreeHost(c->hbuf.p);
     delete c;
 }
@@ -472,3 +494,14 @@ gp2s_status gp2s_lml_grad(gp2s_ctx *c, int64_t n, const double *X, const double 
 }
 
 }  // extern "C"
+
+namespace gp2s {
+
+// One problem on one (worker) context: the engine of gp2s_lml / gp2s_lml_grad.
+gp2s_status lml_single(gp2s_ctx *c, int64_t n, const double *X, const double *y, const gp2s_hyper *h,
+                       const gp2s_opts *o, double *lml, double *grad, gp2s_lml_info *info)
+{
+    return lml_impl(c, n, X, y, h, o, lml, grad, info);
+}
+
+}  // namespace gp2s

@@ -105,6 +105,10 @@ struct gp2s_ctx {
     bool bj_valid = false;
     double bj_logdet = 0.0;
     bool probes_for_grad = false;   // the probe solves feed the Hutchinson gradient
+    // batched form: worker contexts (own stream and workspace each), created on first use
+    std::vector<gp2s_ctx *> workers;
+    std::vector<cudaStream_t> worker_streams;
+    int batch_workers_max = 16;
     // dense
     gp2s::DevBuf dense;
     // adjoint
@@ -138,6 +142,8 @@ gp2s_status set_err(gp2s_ctx *c, gp2s_status st, const std::string &msg);
 gp2s_status cuda_err(gp2s_ctx *c, cudaError_t e, const char *where);
 gp2s_status ensure(gp2s_ctx *c, DevBuf &b, size_t bytes);
 gp2s_status ensure_host(gp2s_ctx *c, HostPinned &b, size_t bytes);
+// Raise a kernel's dynamic shared-memory limit to at least smem bytes (thread-safe, grow-only).
+gp2s_status smem_attr(gp2s_ctx *c, const void *func, size_t smem);
 
 #define GP2S_CUDA(ctx, expr)                                     \
     do {                                                         \

@@ -918,7 +918,7 @@ gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride
 {
     const size_t smem = rb_smem<K>();
     auto kern = k_spmm_rb<K, true>;
-    GP2S_CUDA(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GP2S_TRY(smem_attr(c, (const void *)kern, smem));
     kern<<<nb, RBCfg<K>::threads, smem, c->stream>>>(c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
                                                      c->rb_val.as<float>(), c->A.n, c->rb_split.as<int32_t>(),
                                                      (const float *)B.py, (const float *)B.pz, (float *)B.qy,
@@ -1223,7 +1223,7 @@ gp2s_status build_block_jacobi(gp2s_ctx *c)
     int *bad = reinterpret_cast<int *>(c->counters.as<char>() + 208);
     GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
     const size_t smem = sizeof(double) * 2 * kBJ * (kBJ + 1);
-    GP2S_CUDA(c, cudaFuncSetAttribute(k_bj_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GP2S_TRY(smem_attr(c, (const void *)k_bj_build, smem));
     k_bj_build<<<(unsigned)nblk, kPCThreads, smem, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(),
                                                                 c->val64.as<double>(), n, c->bj_Minv.as<float>(),
                                                                 c->bj_ld.as<double>(), bad);
@@ -1318,9 +1318,9 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     const float *Minv = pc_avail ? c->bj_Minv.as<float>() : nullptr;
     if (pc_avail) {
         const size_t smem = pc_smem(m);
-        GP2S_CUDA(c, cudaFuncSetAttribute(k_pc_step<PC_INIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        GP2S_CUDA(c, cudaFuncSetAttribute(k_pc_step<PC_UPDATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        GP2S_CUDA(c, cudaFuncSetAttribute(k_pc_step<PC_RESTART>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_INIT>, smem));
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_UPDATE>, smem));
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_RESTART>, smem));
     }
 #define GP2S_PC(MODE, GZ, GY, MM)                                                                                \
     k_pc_step<MODE><<<(GZ) + (GY), kPCThreads, pc_smem(MM), c->stream>>>(                                       \

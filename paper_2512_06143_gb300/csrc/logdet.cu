@@ -363,7 +363,7 @@ gp2s_status slq_logdet(gp2s_ctx *c, int m, int ksteps, double *logdet_hat, doubl
     int *bad = reinterpret_cast<int *>(out + m);
     GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
     const size_t smem = sizeof(double) * 3 * (size_t)ksteps;
-    GP2S_CUDA(c, cudaFuncSetAttribute(k_slq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GP2S_TRY(smem_attr(c, (const void *)k_slq, smem));
     k_slq<<<m, 32, smem, c->stream>>>(c->rec.as<double>(), c->scal.as<double>(), m, ksteps, work, out, bad);
     GP2S_LAUNCH(c);
     std::vector<double> g(m);
