@@ -103,14 +103,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def make_workload(name: str, seed: int):
+def make_workload(name: str, seed: int, n: int | None = None):
+    """The named workload at its full size, or at n points with the same generator and the same
+    mean entries per row (a small case of the same kernels, for profiling captures)."""
     from paper_2512_06143_gb300 import workloads as W
+    kw = {} if n is None else {"n": n}
     if name == "clusters_3d":
-        return W.clusters_3d(seed), dict(probes=64, lanczos_steps=100)
+        return W.clusters_3d(seed, **kw), dict(probes=64, lanczos_steps=100)
     if name == "sphere_4d":
-        return W.sphere_4d(seed), dict(probes=32, lanczos_steps=100)
+        return W.sphere_4d(seed, **kw), dict(probes=32, lanczos_steps=100)
     if name == "small_2d":
-        return W.small_2d(seed), dict(probes=64, lanczos_steps=100)
+        return W.small_2d(seed, **kw), dict(probes=64, lanczos_steps=100)
     raise ValueError(name)
 
 
@@ -197,7 +200,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     build.build()
     gp.load()
-    w, wopts = make_workload(args.workload, seed=rank)
+    w, wopts = make_workload(args.workload, seed=rank, n=args.n)
     hyper = gp.Hyper(**w["hyper"])
     n = w["X"].shape[0]
     precision = gp.PREC_MIXED if args.workload != "small_2d" else gp.PREC_FP64
@@ -300,6 +303,8 @@ def main():
     ap.add_argument("--impl", default="gp2s", choices=["gp2s", "reference"])
     ap.add_argument("--workload", default="clusters_3d", choices=["clusters_3d", "sphere_4d", "small_2d", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None,
+                    help="points per problem (default: the workload's full size); smaller n = profiling case")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -279,7 +279,7 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->B64, &c->B32, &c->D64, &c->s64, &c->s32, &c->rowcnt, &c->rowptr, &c->col,
                       &c->val32, &c->val64, &c->counters, &c->vec, &c->vec64, &c->partials, &c->scal,
                       &c->Z, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
-                      &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_split,
+                      &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_tpart, &c->rb_seg,
                       &c->bj_Minv, &c->bj_ld};
     for (DevBuf *b : bufs) free_buf(*b);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);

@@ -97,7 +97,7 @@ struct gp2s_ctx {
     // Krylov
     gp2s::DevBuf vec, vec64, partials, scal, Z, rec, rsplit;
     // row-block (8 rows) copy of the FP32 matrix for the multi-RHS SpMM
-    gp2s::DevBuf rb_cnt, rb_ptr, rb_col, rb_val, rb_split;
+    gp2s::DevBuf rb_cnt, rb_ptr, rb_col, rb_val, rb_tpart, rb_seg;
     bool rb_valid = false;
     int64_t rb_entries = 0;
     // block-Jacobi preconditioner: FP32 M^{-1} per 64-row block and the block log-determinants

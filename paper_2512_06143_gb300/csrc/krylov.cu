@@ -26,6 +26,7 @@ namespace {
 constexpr int kSpmmThreads = 1024;
 constexpr int kSpmmWarps = kSpmmThreads / kWarp;
 constexpr int kMaxPartBlocks = 152 * 8;
+constexpr int kRBWorkOffset = 224;   // byte offset of the RB8 SpMM's tile counter in c->counters
 constexpr int kScal = 8;   // doubles per column in the scalar block
 constexpr int kMaxCols = 129;   // y + up to 128 probes
 
@@ -581,7 +582,7 @@ struct CGBuffers {
 };
 
 template <int K>
-gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb);
+gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts);
 
 // y-only SpMV (the y column after every probe column has stopped, and the refinement solves):
 // one warp per row, lanes over the row's entries, many warps per SM to keep enough independent
@@ -677,10 +678,10 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
     }
     if (rb_launch<T>(c, m, has_y)) {
         switch (K) {
-        case 1: GP2S_TRY(launch_rb<1>(c, B, part, pstride, nb)); break;
-        case 2: GP2S_TRY(launch_rb<2>(c, B, part, pstride, nb)); break;
-        case 3: GP2S_TRY(launch_rb<3>(c, B, part, pstride, nb)); break;
-        default: GP2S_TRY(launch_rb<4>(c, B, part, pstride, nb)); break;
+        case 1: GP2S_TRY(launch_rb<1>(c, B, part, pstride, nb, nparts)); break;
+        case 2: GP2S_TRY(launch_rb<2>(c, B, part, pstride, nb, nparts)); break;
+        case 3: GP2S_TRY(launch_rb<3>(c, B, part, pstride, nb, nparts)); break;
+        default: GP2S_TRY(launch_rb<4>(c, B, part, pstride, nb, nparts)); break;
         }
         if (c->profile) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
         return GP2S_OK;
@@ -789,49 +790,88 @@ template <int K> struct RBCfg {
     static constexpr int warps = threads / kWarp;
 };
 
+// Work distribution of the RB8 SpMM.  The row blocks are cut into tiles of `tile_blocks`
+// consecutive blocks; warps take tiles from a global counter in increasing order (the next index
+// is fetched while the current tile runs), so an SM that runs slower, or a warp that drew denser
+// blocks, takes fewer tiles instead of holding the whole launch back, and the tiles in flight stay
+// a narrow window of the Morton order whose gathered P rows stay in L2.  The partial dots must
+// not depend on which warp ran which tile: every tile writes its own (tpart[tile][col]), and the
+// warp that completes the last tile of a segment of `seg_tiles` tiles sums the segment's tiles in
+// tile order into part[col * pstride + segment], which the scalar kernels sum in segment order.
+// The last CTA to finish puts the tile counter back to zero for the next launch on the stream;
+// each segment's reducer does the same for its segment counter.
+struct RBWork {
+    unsigned long long next;   // next tile index
+    unsigned int done;         // CTAs finished
+    unsigned int pad;
+};
+
 template <int K, bool HAS_Y>
 __global__ void __launch_bounds__(RBCfg<K>::threads, 1)
 k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, const float *__restrict__ uval,
-          int64_t n, const int32_t *__restrict__ blk_split, const float *__restrict__ py,
-          const float *__restrict__ pz, float *__restrict__ qy, float *__restrict__ qz, double *__restrict__ part,
-          int pstride)
+          int64_t n, const float *__restrict__ py, const float *__restrict__ pz, float *__restrict__ qy,
+          float *__restrict__ qz, double *__restrict__ part, int pstride, RBWork *__restrict__ work,
+          int tile_blocks, int ntiles, double *__restrict__ tpart, int *__restrict__ seg_cnt, int seg_tiles)
 {
     constexpr int M = 32 * K;
     constexpr int W = RBCfg<K>::warps;
     extern __shared__ __align__(16) unsigned char rb_sh[];
     int *s_col = reinterpret_cast<int *>(rb_sh);                                    // W x 32
     float4 *s_val = reinterpret_cast<float4 *>(rb_sh + sizeof(int) * W * kWarp);  // W x 32 x 2
-    double *red = reinterpret_cast<double *>(rb_sh + sizeof(int) * W * kWarp + sizeof(float4) * W * kWarp * 2);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // Chunks of W consecutive row blocks go round-robin to the CTAs (one per SM), a warp per
-    // block: all SMs sweep the Morton order side by side, so the P rows gathered at any moment
-    // lie in a narrow window that stays resident in L2.
-    (void)blk_split;
     const int64_t nblk = (n + kRB - 1) / kRB;
-    Acc32 dz[K];
-    Acc32 dy;
-    for (int64_t chunk = blockIdx.x; chunk * W < nblk; chunk += gridDim.x) {
-        const int64_t b = chunk * W + wid;
-        if (b >= nblk) continue;
-        const int64_t r0 = b * kRB;
-        const int nrows = (int)(n - r0 < kRB ? n - r0 : kRB);
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(&work->next, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    while (t < (unsigned long long)ntiles) {
+        unsigned long long tn = 0;
+        if (lane == 0) tn = atomicAdd(&work->next, 1ull);
+        const int64_t bb = (int64_t)t * tile_blocks;
+        const int64_t be = bb + tile_blocks < nblk ? bb + tile_blocks : nblk;
+        Acc32 dz[K];
+        Acc32 dy;
+        // the tile's entries are contiguous: stream them in 32-entry batches that never straddle
+        // a block, the next batch's column and values loaded while the current one is consumed
+        int64_t b = bb;
+        int e1 = bptr[b + 1];
+        int eb = bptr[b];
+        int cj_n = (int)(b * kRB);
+        float4 v0_n = make_float4(0.f, 0.f, 0.f, 0.f), v1_n = v0_n;
+        if (eb + lane < e1) {
+            cj_n = ucol[eb + lane];
+            v0_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2];
+            v1_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2 + 1];
+        }
         float acc[kRB][K];
-#pragma unroll
-        for (int r = 0; r < kRB; ++r)
-#pragma unroll
-            for (int k = 0; k < K; ++k) acc[r][k] = 0.0f;
         float ay[kRB];
 #pragma unroll
-        for (int r = 0; r < kRB; ++r) ay[r] = 0.0f;
-        const int e0 = bptr[b], e1 = bptr[b + 1];
-        for (int eb = e0; eb < e1; eb += kWarp) {
-            const int e = eb + lane;
-            int cj = (int)r0;
-            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-            if (e < e1) {
-                cj = ucol[e];
-                v0 = reinterpret_cast<const float4 *>(uval)[(int64_t)e * 2];
-                v1 = reinterpret_cast<const float4 *>(uval)[(int64_t)e * 2 + 1];
+        for (int r = 0; r < kRB; ++r) {
+            ay[r] = 0.0f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[r][k] = 0.0f;
+        }
+        while (b < be) {
+            const int cj = cj_n;
+            const float4 v0 = v0_n, v1 = v1_n;
+            const int cnt = min(kWarp, e1 - eb);
+            const int64_t bcur = b;
+            // advance to the next batch and issue its loads
+            eb += kWarp;
+            const bool block_end = eb >= e1;
+            if (block_end) {
+                ++b;
+                if (b < be) {
+                    eb = e1;
+                    e1 = bptr[b + 1];
+                }
+            }
+            cj_n = (int)(b * kRB);
+            v0_n = make_float4(0.f, 0.f, 0.f, 0.f);
+            v1_n = v0_n;
+            if (b < be && eb + lane < e1) {
+                cj_n = ucol[eb + lane];
+                v0_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2];
+                v1_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2 + 1];
             }
             if (HAS_Y) {
                 const float yj = py[cj];
@@ -844,11 +884,10 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             s_val[(wid * kWarp + lane) * 2] = v0;
             s_val[(wid * kWarp + lane) * 2 + 1] = v1;
             __syncwarp();
-            const int cnt = min(kWarp, e1 - eb);
 #pragma unroll 8
-            for (int t = 0; t < cnt; ++t) {
-                const int j = s_col[wid * kWarp + t];
-                const float4 a0 = s_val[(wid * kWarp + t) * 2], a1 = s_val[(wid * kWarp + t) * 2 + 1];
+            for (int u = 0; u < cnt; ++u) {
+                const int j = s_col[wid * kWarp + u];
+                const float4 a0 = s_val[(wid * kWarp + u) * 2], a1 = s_val[(wid * kWarp + u) * 2 + 1];
                 float pv[K];
                 load_k<float, K>(pz + (int64_t)j * M + lane * K, pv);
                 const float vr[kRB] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
@@ -858,51 +897,82 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
                     for (int k = 0; k < K; ++k) acc[r][k] = fmaf(vr[r], pv[k], acc[r][k]);
             }
             __syncwarp();
-        }
+            if (block_end) {
+                // row block bcur is complete: store its rows and fold them into the tile's dots
+                const int64_t r0 = bcur * kRB;
+                const int nrows = (int)(n - r0 < kRB ? n - r0 : kRB);
 #pragma unroll
-        for (int r = 0; r < kRB; ++r) {
-            if (r < nrows) {
-                const int64_t i = r0 + r;
-                store_k<float, K>(qz + i * M + lane * K, acc[r]);
-                float pi[K];
-                load_k<float, K>(pz + i * M + lane * K, pi);
+                for (int r = 0; r < kRB; ++r) {
+                    if (r < nrows) {
+                        const int64_t i = r0 + r;
+                        store_k<float, K>(qz + i * M + lane * K, acc[r]);
+                        float pi[K];
+                        load_k<float, K>(pz + i * M + lane * K, pi);
 #pragma unroll
-                for (int k = 0; k < K; ++k) dz[k].fma2(pi[k], acc[r][k]);
-            }
-        }
-        if (HAS_Y) {
+                        for (int k = 0; k < K; ++k) dz[k].fma2(pi[k], acc[r][k]);
+                    }
 #pragma unroll
-            for (int r = 0; r < kRB; ++r) {
-                float v = ay[r];
+                    for (int k = 0; k < K; ++k) acc[r][k] = 0.0f;
+                }
+                if (HAS_Y) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0 && r < nrows) {
-                    qy[r0 + r] = v;
-                    dy.fma2(py[r0 + r], v);
+                    for (int r = 0; r < kRB; ++r) {
+                        float v = ay[r];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == 0 && r < nrows) {
+                            qy[r0 + r] = v;
+                            dy.fma2(py[r0 + r], v);
+                        }
+                        ay[r] = 0.0f;
+                    }
                 }
             }
         }
-    }
-    // block reduction of the partial dots (two halves, fixed order)
-    constexpr int HW = W / 2;
-    if (wid >= HW) {
-        if (HAS_Y && lane == 0) red[(wid - HW) * (M + 1) + M] = dy.value();
+        // the tile's partial dots, then the segment count; the segment's last tile reduces it
+        double *tp = tpart + (int64_t)t * (M + 1);
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[(wid - HW) * (M + 1) + lane * K + k] = dz[k].value();
-    }
-    __syncthreads();
-    if (wid < HW) {
-        if (HAS_Y && lane == 0) red[wid * (M + 1) + M] += dy.value();
+        for (int k = 0; k < K; ++k) tp[1 + lane * K + k] = dz[k].value();
+        if (lane == 0) tp[0] = HAS_Y ? dy.value() : 0.0;
+        __threadfence();
+        __syncwarp();
+        const int sg = (int)(t / (unsigned long long)seg_tiles);
+        const int nseg = (ntiles + seg_tiles - 1) / seg_tiles;
+        const int need = sg == nseg - 1 ? ntiles - sg * seg_tiles : seg_tiles;
+        int last = 0;
+        if (lane == 0) last = atomicAdd(&seg_cnt[sg], 1) == need - 1;
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {
+            __threadfence();
+            const double *q = tpart + (int64_t)sg * seg_tiles * (M + 1);
+            double sz[K], sy = 0.0;
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[wid * (M + 1) + lane * K + k] += dz[k].value();
+            for (int k = 0; k < K; ++k) sz[k] = 0.0;
+#pragma unroll 4
+            for (int i = 0; i < need; ++i) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) sz[k] += __ldcg(q + (int64_t)i * (M + 1) + 1 + lane * K + k);
+                if (lane == 0) sy += __ldcg(q + (int64_t)i * (M + 1));
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) part[(int64_t)(1 + lane * K + k) * pstride + sg] = sz[k];
+            if (lane == 0) {
+                part[sg] = sy;
+                seg_cnt[sg] = 0;
+            }
+        }
+        t = __shfl_sync(0xffffffffu, tn, 0);
     }
+    // every warp of this CTA has made its last (failed) grab: count the CTA out, and let the last
+    // one reset the counter for the next launch
     __syncthreads();
-    for (int cidx = threadIdx.x; cidx < M + 1; cidx += RBCfg<K>::threads) {
-        if (cidx == M && !HAS_Y) continue;
-        double s = 0.0;
-        for (int w = 0; w < HW; ++w) s += red[w * (M + 1) + cidx];
-        const int c = cidx == M ? 0 : cidx + 1;
-        part[(int64_t)c * pstride + blockIdx.x] = s;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(&work->done, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&work->next, 0ull);
+            atomicExch(&work->done, 0u);
+        }
     }
 }
 
@@ -910,20 +980,43 @@ template <int K>
 size_t rb_smem()
 {
     constexpr int W = RBCfg<K>::warps;
-    return sizeof(int) * W * kWarp + sizeof(float4) * W * kWarp * 2 + sizeof(double) * (W / 2) * (32 * K + 1);
+    return sizeof(int) * W * kWarp + sizeof(float4) * W * kWarp * 2;
+}
+
+// Tiles of the RB8 SpMM: about 32 per warp of the grid (a warp's last tile is a small share of
+// its work, so the SMs finish together), and segments of seg_tiles tiles, at most kMaxPartBlocks
+// of them (the partial-dot stride).
+struct RBTiles {
+    int tile_blocks, ntiles, seg_tiles, nseg;
+};
+inline RBTiles rb_tiles(int64_t nblk, int nb)
+{
+    RBTiles t;
+    const int64_t want = (int64_t)nb * RBCfg<1>::warps * 32;
+    const int64_t tb = std::max<int64_t>(1, ceil_div(nblk, want));
+    t.tile_blocks = (int)tb;
+    t.ntiles = (int)ceil_div(nblk, tb);
+    t.seg_tiles = (int)ceil_div(t.ntiles, kMaxPartBlocks);
+    t.nseg = (int)ceil_div(t.ntiles, t.seg_tiles);
+    return t;
 }
 
 template <int K>
-gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb)
+gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts)
 {
     const size_t smem = rb_smem<K>();
     auto kern = k_spmm_rb<K, true>;
     GP2S_TRY(smem_attr(c, (const void *)kern, smem));
+    const RBTiles tl = rb_tiles(ceil_div(c->A.n, kRB), nb);
+    GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (32 * K + 1)));
+    RBWork *work = reinterpret_cast<RBWork *>(c->counters.as<char>() + kRBWorkOffset);
     kern<<<nb, RBCfg<K>::threads, smem, c->stream>>>(c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
-                                                     c->rb_val.as<float>(), c->A.n, c->rb_split.as<int32_t>(),
-                                                     (const float *)B.py, (const float *)B.pz, (float *)B.qy,
-                                                     (float *)B.qz, part, pstride);
+                                                     c->rb_val.as<float>(), c->A.n, (const float *)B.py,
+                                                     (const float *)B.pz, (float *)B.qy, (float *)B.qz, part,
+                                                     pstride, work, tl.tile_blocks, tl.ntiles,
+                                                     c->rb_tpart.as<double>(), c->rb_seg.as<int>(), tl.seg_tiles);
     GP2S_LAUNCH(c);
+    *nparts = tl.nseg;
     return GP2S_OK;
 }
 
@@ -1262,10 +1355,11 @@ gp2s_status build_rb8(gp2s_ctx *c)
                                                 n, nblk, nullptr, c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
                                                 c->rb_val.as<float>());
     GP2S_LAUNCH(c);
-    const int nb = std::max(1, std::min(kMaxPartBlocks, c->num_sms));
-    GP2S_TRY(ensure(c, c->rb_split, sizeof(int32_t) * (size_t)(nb + 1)));
-    k_row_split<<<1, 1024, 0, c->stream>>>(c->rb_ptr.as<int32_t>(), nblk, nb, c->rb_split.as<int32_t>());
-    GP2S_LAUNCH(c);
+    // the SpMM's tile and segment counters start at zero (each launch leaves them there)
+    GP2S_TRY(ensure(c, c->counters, 256));
+    GP2S_CUDA(c, cudaMemsetAsync(c->counters.as<char>() + kRBWorkOffset, 0, sizeof(RBWork), c->stream));
+    GP2S_TRY(ensure(c, c->rb_seg, sizeof(int) * kMaxPartBlocks));
+    GP2S_CUDA(c, cudaMemsetAsync(c->rb_seg.p, 0, sizeof(int) * kMaxPartBlocks, c->stream));
     c->rb_entries = nu;
     c->rb_valid = true;
     return GP2S_OK;
