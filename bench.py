@@ -272,14 +272,18 @@ def run_gpu(args):
                        "nnz": int(i0["nnz"]), "probes": int(opts.probes), "lanczos_steps": int(opts.lanczos_steps),
                        "precision": "mixed" if precision == gp.PREC_MIXED else "fp64", "l2": "flushed (256 MB write) between steps",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": {"kernel": "k_spmm (multi-RHS CSR SpMM, Krylov solves)", "bound": "hbm",
+            "roofline": {"kernel": "k_spmm_rb (multi-RHS RB8 SpMM of the Krylov solves)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
                          "peak_source": f"{peak_src} hbm_gbs",
                          "launches_per_step": spmm_launches / args.steps,
                          "bytes_per_launch": spmm_bytes / max(spmm_launches, 1),
                          "ms_per_launch": spmm_ms / max(spmm_launches, 1),
-                         "share_of_step": spmm_ms / total_ms if total_ms > 0 else None},
+                         "share_of_step": spmm_ms / total_ms if total_ms > 0 else None,
+                         "bytes_definition": "8 B per stored entry (FP32 value + int32 column) + 4 B per row "
+                                             "pointer + 4 B per input and per output vector element"},
+            "assembly": {"ms": i0["ms_assemble"], "gnnz_per_s": i0["nnz"] / (i0["ms_assemble"] * 1e6)
+                         if i0["ms_assemble"] > 0 else None},
             "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": int(Xh.numel() * 8 + yh.numel() * 8),
                     "d2h_bytes_per_step": int(8 + 8 * hyper.nparams)},

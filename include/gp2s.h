@@ -137,10 +137,11 @@ typedef struct {
     int32_t iters_y, iters_probes, outer, logdet_method;
     float ms_assemble, ms_solve, ms_logdet, ms_grad, ms_total;
     int64_t launches;        /* kernels this call launched */
-    int64_t spmm_launches;   /* SpMM launches of the Krylov solves */
+    int64_t spmm_launches;   /* multi-RHS SpMM launches of the Krylov solves (y plus probe
+                                columns; the y-only SpMV launches are not counted) */
     double spmm_bytes;       /* algorithmic bytes of those launches: CSR values + indices + row
                                 pointers + each input and output vector element once */
-    float ms_spmm;           /* summed CUDA-event time of the SpMM launches (opts.profile = 1) */
+    float ms_spmm;           /* summed CUDA-event time of those launches (opts.profile = 1) */
     float reserved_f;
 } gp2s_lml_info;
 
@@ -228,10 +229,15 @@ gp2s_status gp2s_lml_grad(gp2s_ctx *ctx, int64_t n, const double *X, const doubl
 
 /*
  * Many independent problems in one call (the batched form): problem b has n[b] points of
- * dimension hyper[b].d, X[b] (n[b] x d) and y[b] (n[b]), host or device.  All problems are
- * assembled into one block-diagonal CSR and solved together by multi-RHS CG (y plus
- * opts->probes probe columns each, per-problem scalars); log|A_b| by SLQ (or EXACT when
- * opts->logdet == EXACT).  lml_host: B doubles.  info_host: optional, B entries.
+ * dimension hyper[b].d, X[b] (n[b] x d) and y[b] (n[b]), host or device.  Each problem runs the
+ * gp2s_lml path (assembly, multi-RHS CG over y plus opts->probes probe columns, FP64 refinement,
+ * SLQ; EXACT only when opts->logdet == EXACT, AUTO is read as SLQ).  The problems are spread over
+ * a pool of worker contexts owned by ctx, each with its own CUDA stream and workspace (at most 16,
+ * or GP2S_BATCH_WORKERS), largest problems first; the call first synchronises ctx's stream so
+ * that device inputs produced there are complete.  Results equal those of single gp2s_lml calls
+ * with the same options bit for bit.  lml_host: B doubles (NaN for a failed problem).
+ * info_host: optional, B entries.  On failure the status and message are those of the first
+ * failing problem ("problem b: ...").
  */
 gp2s_status gp2s_lml_batched(gp2s_ctx *ctx, int32_t B, const int64_t *n, const double *const *X,
                              const double *const *y, const gp2s_hyper *hyper,

@@ -658,12 +658,16 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
     k_spmm<T, V, KK, HY><<<nb, kSpmmThreads, 0, c->stream>>>(rp, cl, val, A.n, rsplit, py, pz, qy, qz, \
                                                              part, pstride, active)
     int K = m / 32;
-    // algorithmic bytes: values + column indices + row pointers + every input and output element once
-    c->spmm_bytes += (double)A.nnz * (sizeof(V) + sizeof(int32_t)) + 4.0 * (double)(A.n + 1) +
-                     2.0 * (double)A.n * (double)(m + (has_y ? 1 : 0)) * sizeof(T);
-    ++c->spmm_launches;
+    // multi-RHS launches: algorithmic bytes = values + column indices + row pointers + every input
+    // and output element once
+    const bool counted = m > 0;
+    if (counted) {
+        c->spmm_bytes += (double)A.nnz * (sizeof(V) + sizeof(int32_t)) + 4.0 * (double)(A.n + 1) +
+                         2.0 * (double)A.n * (double)(m + (has_y ? 1 : 0)) * sizeof(T);
+        ++c->spmm_launches;
+    }
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
-    if (c->profile) {
+    if (c->profile && counted) {
         if (c->prof_used + 2 > c->prof_ev.size()) {
             for (int k = 0; k < 64; ++k) {
                 cudaEvent_t e;
@@ -683,7 +687,7 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
         case 3: GP2S_TRY(launch_rb<3>(c, B, part, pstride, nb, nparts)); break;
         default: GP2S_TRY(launch_rb<4>(c, B, part, pstride, nb, nparts)); break;
         }
-        if (c->profile) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
+        if (ev_b) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
         return GP2S_OK;
     }
     if (has_y && K == 0) {
@@ -692,7 +696,7 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
         k_spmv_y<T, V><<<nbv, kSpmvThreads, 0, c->stream>>>(rp, cl, val, A.n, py, qy, part);
         GP2S_LAUNCH(c);
         *nparts = nbv;
-        if (c->profile) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
+        if (ev_b) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
         return GP2S_OK;
     }
     if (has_y) {
@@ -713,7 +717,7 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
     }
 #undef GP2S_SPMM_CASE
     GP2S_LAUNCH(c);
-    if (c->profile) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
+    if (ev_b) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
     return GP2S_OK;
 }
 
@@ -842,14 +846,16 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             v0_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2];
             v1_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2 + 1];
         }
-        float acc[kRB][K];
+        // accumulators of row pairs (2p, 2p + 1) for each column: one packed FP32x2 FMA per pair
+        // (each half rounds exactly like a scalar fmaf)
+        float2 acc[kRB / 2][K];
         float ay[kRB];
 #pragma unroll
-        for (int r = 0; r < kRB; ++r) {
-            ay[r] = 0.0f;
+        for (int r = 0; r < kRB; ++r) ay[r] = 0.0f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc[r][k] = 0.0f;
-        }
+        for (int rp = 0; rp < kRB / 2; ++rp)
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
         while (b < be) {
             const int cj = cj_n;
             const float4 v0 = v0_n, v1 = v1_n;
@@ -884,17 +890,20 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             s_val[(wid * kWarp + lane) * 2] = v0;
             s_val[(wid * kWarp + lane) * 2 + 1] = v1;
             __syncwarp();
-#pragma unroll 8
+#pragma unroll (K > 2 ? 4 : 8)
             for (int u = 0; u < cnt; ++u) {
                 const int j = s_col[wid * kWarp + u];
                 const float4 a0 = s_val[(wid * kWarp + u) * 2], a1 = s_val[(wid * kWarp + u) * 2 + 1];
                 float pv[K];
                 load_k<float, K>(pz + (int64_t)j * M + lane * K, pv);
-                const float vr[kRB] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float2 vp[kRB / 2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                                            make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
 #pragma unroll
-                for (int r = 0; r < kRB; ++r)
+                for (int k = 0; k < K; ++k) {
+                    const float2 pk = make_float2(pv[k], pv[k]);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc[r][k] = fmaf(vr[r], pv[k], acc[r][k]);
+                    for (int rp = 0; rp < kRB / 2; ++rp) acc[rp][k] = __ffma2_rn(vp[rp], pk, acc[rp][k]);
+                }
             }
             __syncwarp();
             if (block_end) {
@@ -905,15 +914,20 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
                 for (int r = 0; r < kRB; ++r) {
                     if (r < nrows) {
                         const int64_t i = r0 + r;
-                        store_k<float, K>(qz + i * M + lane * K, acc[r]);
+                        float qr[K];
+#pragma unroll
+                        for (int k = 0; k < K; ++k) qr[k] = (r & 1) ? acc[r / 2][k].y : acc[r / 2][k].x;
+                        store_k<float, K>(qz + i * M + lane * K, qr);
                         float pi[K];
                         load_k<float, K>(pz + i * M + lane * K, pi);
 #pragma unroll
-                        for (int k = 0; k < K; ++k) dz[k].fma2(pi[k], acc[r][k]);
+                        for (int k = 0; k < K; ++k) dz[k].fma2(pi[k], qr[k]);
                     }
-#pragma unroll
-                    for (int k = 0; k < K; ++k) acc[r][k] = 0.0f;
                 }
+#pragma unroll
+                for (int rp = 0; rp < kRB / 2; ++rp)
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
                 if (HAS_Y) {
 #pragma unroll
                     for (int r = 0; r < kRB; ++r) {
@@ -1113,20 +1127,32 @@ __device__ __forceinline__ void bj_tile_mm(const float *__restrict__ MT, const f
     for (int tt = threadIdx.x; tt < tiles; tt += blockDim.x) {
         const int rg = tt / cgroups, cg = tt - rg * cgroups;
         const int i0 = rg * 4, c0 = cg * 4;
-        float acc[4][4];
+        // row pairs (0,1), (2,3) accumulate with packed FP32x2 FMAs (each half rounds like fmaf)
+        float2 acc2[2][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[a][q] = 0.0f;
+            for (int q = 0; q < 4; ++q) acc2[a][q] = make_float2(0.0f, 0.0f);
 #pragma unroll 8
         for (int k = 0; k < kBJ; ++k) {
             const float4 mv = *reinterpret_cast<const float4 *>(MT + k * kBJ + i0);
             const float4 iv = *reinterpret_cast<const float4 *>(In + k * m + c0);
-            const float ma[4] = {mv.x, mv.y, mv.z, mv.w}, ia[4] = {iv.x, iv.y, iv.z, iv.w};
+            const float2 mp[2] = {make_float2(mv.x, mv.y), make_float2(mv.z, mv.w)};
+            const float ia[4] = {iv.x, iv.y, iv.z, iv.w};
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int q = 0; q < 4; ++q) {
+                const float2 iq = make_float2(ia[q], ia[q]);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[a][q] = fmaf(ma[a], ia[q], acc[a][q]);
+                for (int a = 0; a < 2; ++a) acc2[a][q] = __ffma2_rn(mp[a], iq, acc2[a][q]);
+            }
+        }
+        float acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            acc[0][q] = acc2[0][q].x;
+            acc[1][q] = acc2[0][q].y;
+            acc[2][q] = acc2[1][q].x;
+            acc[3][q] = acc2[1][q].y;
         }
         emit(i0, c0, acc);
     }
