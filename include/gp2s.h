@@ -4,9 +4,9 @@
  *
  * The problem (Sec. 3, Background): data X (n points in R^d) and observations y; a compactly
  * supported non-stationary kernel
- *     k(xi, xj) = phi(|xi - xj| / r) * ( sum_l b_l(xi) b_l(xj) + w0 )            (Sec. 3.1, 3.3)
- * with the Wendland taper phi (eq. wendland; "C2" reading by default), bump functions
- *     b_l(x) = a_l exp(beta (1 - 1/(1 - |x - c_l|^2 / rho_l^2)))   inside |x - c_l| < rho_l (eq. bump)
+ *     k(xi, xj) = phi(|xi - xj| / r) * ( sum_l b_l(xi) b_l(xj) + w0 )            (Sec. 4.1, 4.3)
+ * with the Wendland taper phi (Eq. 3; "C2" reading by default), bump functions
+ *     b_l(x) = a_l exp(beta (1 - 1/(1 - |x - c_l|^2 / rho_l^2)))   inside |x - c_l| < rho_l (Eq. 7)
  * and noise V = sigma2 I.  A = K + sigma2 I is sparse because phi vanishes for |xi - xj| >= r.
  * The engine evaluates
  *     LML = -1/2 y^T A^{-1} y - 1/2 log|A| - n/2 log(2 pi)                          (Sec. 3)
@@ -51,7 +51,7 @@ typedef enum {
 
 typedef enum {
     GP2S_WENDLAND_C2 = 0,        /* (1-t)^4 (4t+1) for d <= 3, (1-t)^5 (5t+1) for d = 4 */
-    GP2S_WENDLAND_C6_PAPER = 1   /* eq. wendland: (1-t)^8 (32t^3 + 25t^2 + 8t + 1), d <= 3 */
+    GP2S_WENDLAND_C6_PAPER = 1   /* Eq. 3: (1-t)^8 (32t^3 + 25t^2 + 8t + 1), d <= 3 */
 } gp2s_wendland;
 
 typedef enum {
@@ -66,7 +66,7 @@ typedef enum {
     GP2S_LOGDET_SLQ = 2     /* stochastic Lanczos quadrature on D^{-1/2} A D^{-1/2} */
 } gp2s_logdet_method;
 
-/* Kernel hyperparameters (eq. wendland, eq. bump, Sec. 3.3) and noise (Sec. 3).  Host memory. */
+/* Kernel hyperparameters (Eq. 3, Eq. 7, Sec. 4.3) and noise (Sec. 3).  Host memory. */
 typedef struct {
     int32_t d;               /* input dimension, 1..4 */
     int32_t L;               /* number of bumps, 0..32 */
@@ -164,7 +164,7 @@ void gp2s_destroy(gp2s_ctx *ctx);
 const char *gp2s_last_error(const gp2s_ctx *ctx);
 
 /*
- * Sec. 3.6 (covariance computation) re-designed: assemble A = K + sigma2 I as CSR.
+ * Sec. 4.6 (covariance computation) re-designed: assemble A = K + sigma2 I as CSR.
  * Points are sorted along a Morton curve of a uniform cell grid with edge h >= r; a pair (i, j)
  * is stored iff i == j or d2(i, j) < r*r with d2 = ((D0*D0 + D1*D1) + D2*D2) + ... in FP64
  * (round to nearest, no fused multiply-add).  Rows and columns use the sorted numbering;
@@ -195,12 +195,12 @@ gp2s_status gp2s_csr(gp2s_ctx *ctx, gp2s_csr_view *view);
  * Sec. 3 / App. B.7 "K^{-1} y": solve A a = y on the last assembled matrix by Jacobi-scaled
  * conjugate gradients; MIXED precision runs FP32 inner CG and FP64 residual refinement until
  * |y - A a| / |y| <= opts->tol_refine (FP64 values).  y, a: n FP64 in ORIGINAL point order,
- * host or device.  The solution is also kept in the context (App. B.6 stores K^{-1} y).
+ * host or device.  The solution is also kept in the context (App. B.7 keeps K^{-1} y).
  */
 gp2s_status gp2s_solve(gp2s_ctx *ctx, const double *y, double *a, gp2s_solve_info *info);
 
 /*
- * log|A| of the last assembled matrix (Sec. 3; the method is left open in Sec. 3.6 / App. B.7):
+ * log|A| of the last assembled matrix (Sec. 3; the method is left open in Sec. 4.6 / App. B.7):
  * EXACT = dense FP64 Cholesky; SLQ = stochastic Lanczos quadrature with opts->probes Rademacher
  * probes (SplitMix64, seed) and opts->lanczos_steps steps on Ah, plus sum log D_ii.
  *   logdet: host.  stderr_hat: host, optional (0 for EXACT).

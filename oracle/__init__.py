@@ -8,12 +8,12 @@ the order the paper states the method, using numpy / scipy library routines (Cho
 symmetric eigensolver, a k-d tree candidate search) as single steps.
 
 What each function follows:
-  * ``assemble``        -- Sec. 3.6: every pair is evaluated; A = K + sigma^2 I (Sec. 3).
+  * ``assemble``        -- Sec. 4.6: every pair is evaluated; A = K + sigma^2 I (Sec. 3).
   * ``lml_exact``       -- the LML of Sec. 3 (Background) with m = 0, V = sigma^2 I, by a dense
                            Cholesky factorisation (solve and log-determinant exactly).
   * ``grad_exact``      -- the standard LML derivative 1/2 a^T dA a - 1/2 tr(A^{-1} dA) with the
                            dense inverse (exact trace).
-  * ``lml_slq``         -- where the paper leaves the log-determinant method open (Sec. 3.6,
+  * ``lml_slq``         -- where the paper leaves the log-determinant method open (Sec. 4.6,
                            App. B.7): Jacobi-scaled conjugate gradients for a = A^{-1} y,
                            stochastic Lanczos quadrature (Ubaru, Chen & Saad 2017) with
                            Rademacher probes for log|A|, Hutchinson's estimator for the trace.
@@ -102,7 +102,7 @@ def _p(a):
 # ----------------------------------------------------------------------------------------
 @dataclass
 class Hyper:
-    """Kernel + noise hyperparameters (eq. wendland, eq. bump, Sec. 3 noise)."""
+    """Kernel + noise hyperparameters (Eq. 3, Eq. 7, Sec. 3 noise)."""
     d: int
     r: float
     sigma2: float
@@ -111,7 +111,7 @@ class Hyper:
     amps: np.ndarray             # L
     beta: float = 1.0
     w0: float = 0.0
-    kind: int = 0                # 0 = Wendland C2 reading, 1 = eq. (wendland) C6
+    kind: int = 0                # 0 = Wendland C2 reading, 1 = Eq. 3 C6
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -188,7 +188,7 @@ def kernel(h: Hyper, xi, xj) -> float:
 
 
 # ----------------------------------------------------------------------------------------
-# Assembly (Sec. 3.6) -> CSR of A = K + sigma^2 I in original index order, columns ascending
+# Assembly (Sec. 4.6) -> CSR of A = K + sigma^2 I in original index order, columns ascending
 # ----------------------------------------------------------------------------------------
 @dataclass
 class CSR:
@@ -223,7 +223,7 @@ class CSR:
 
 
 def assemble(X, h: Hyper, method: str = "auto") -> CSR:
-    """A = K + sigma^2 I as CSR.  method: 'brute' (all n^2 pairs, Sec. 3.6), 'tree'
+    """A = K + sigma^2 I as CSR.  method: 'brute' (all n^2 pairs, Sec. 4.6), 'tree'
     (k-d-tree candidates, each decided by the same exact FP64 test), or 'auto'."""
     X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, h.d))
     n = X.shape[0]

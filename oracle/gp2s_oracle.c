@@ -9,19 +9,19 @@
  *
  * Everything here is the plain definition, written out in FP64, one pair / one row at a
  * time, in the order the paper states it:
- *   - eq. (wendland), Sec. 3.1: the compactly supported Wendland taper, strict support t < 1;
- *   - eq. (bump), Sec. 3.3: bump functions b(x) = a exp(beta (1 - 1/(1 - s))), s = |x-c|^2/rho^2;
- *   - the product kernel of Sec. 3.1 with a rank-<=L bump factor (Sec. 3.3, Theorem 1):
+ *   - Eq. 3, Sec. 4.1: the compactly supported Wendland taper, strict support t < 1;
+ *   - Eq. 7, Sec. 4.3: bump functions b(x) = a exp(beta (1 - 1/(1 - s))), s = |x-c|^2/rho^2;
+ *   - the product kernel of Sec. 4.1 with a rank-<=L bump factor (Sec. 4.3, Theorem 1):
  *       k(xi, xj) = phi(|xi - xj| / r) * (sum_l b_l(xi) b_l(xj) + w0);
  *   - Sec. 3 (Background): A = K + sigma^2 I, the LML needs a = A^{-1} y and log|A|;
- *   - Sec. 3.6: "all covariance entries must be computed" -> brute-force all-pairs assembly.
+ *   - Sec. 4.6: the paper evaluates every covariance entry -> brute-force all-pairs assembly.
  * Krylov pieces (conjugate gradients, Lanczos) follow their textbook definitions; they are
- * used only where the paper leaves the log-determinant method open (Sec. 3.6, App. B.7).
+ * used only where the paper leaves the log-determinant method open (Sec. 4.6, App. B.7).
  *
  * Readings taken where the paper is silent or garbled (each is listed in the design doc):
  *   - "Wendland C2" = phi(t) = (1-t)^4 (4t+1) for d <= 3 and (1-t)^5 (5t+1) for d = 4;
- *     eq. (wendland)'s own C6 form (1-t)^8 (32t^3+25t^2+8t+1) is kind 1.
- *   - bump support is s = |x-c|^2 / rho^2 < 1 (eq. (bump) prints "|x-c|^2 < r").
+ *     Eq. 3's own C6 form (1-t)^8 (32t^3+25t^2+8t+1) is kind 1.
+ *   - bump support is s = |x-c|^2 / rho^2 < 1 (Eq. 7 prints "|x-c|^2 < r").
  *   - the pattern is structural: (i, j) is stored iff i == j or d2(i, j) < r*r, where
  *     d2 = ((D0*D0 + D1*D1) + D2*D2) + ...,  Dk = xi[k] - xj[k], every operation one FP64
  *     round-to-nearest step and no fused multiply-add (build with -ffp-contract=off).
@@ -37,16 +37,16 @@
 #include <omp.h>
 #endif
 
-/* Hyperparameters of the kernel (Sec. 3.1 + Sec. 3.3) and the noise (Sec. 3). */
+/* Hyperparameters of the kernel (Sec. 4.1 + Sec. 4.3) and the noise (Sec. 3). */
 typedef struct {
     int d;                 /* input dimension, 1..4 */
-    int L;                 /* number of bumps (U = L groups with P = 1 bump each, Sec. 3.3) */
-    int kind;              /* 0 = Wendland C2 (reading), 1 = eq. (wendland) C6 */
+    int L;                 /* number of bumps (U = L groups with P = 1 bump each, Sec. 4.3) */
+    int kind;              /* 0 = Wendland C2 (reading), 1 = Eq. 3 C6 */
     int pad_;
     double r;              /* Wendland support radius r0 */
     double sigma2;         /* noise variance: V = sigma2 * I */
     double beta;           /* bump shape parameter */
-    double w0;             /* constant added to the bump sum (stationary floor, Sec. 3.3) */
+    double w0;             /* constant added to the bump sum (stationary floor, Sec. 4.3) */
     const double *centers; /* L x d, row-major */
     const double *radii;   /* L */
     const double *amps;    /* L */
@@ -78,14 +78,14 @@ void orc_rademacher(int64_t n, int m, uint64_t seed, double *z)
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Wendland taper phi(t), t = |xi - xj| / r (eq. (wendland)), and d phi / d t.          */
+/* Wendland taper phi(t), t = |xi - xj| / r (Eq. 3), and d phi / d t.          */
 /* ------------------------------------------------------------------------------------ */
 double orc_phi(int kind, int d, double t)
 {
     if (!(t < 1.0)) return 0.0;          /* compact support: zero for t >= 1 */
     if (t < 0.0) t = 0.0;
     double u = 1.0 - t;
-    if (kind == 1) {                     /* eq. (wendland): (1-t)^8 (32 t^3 + 25 t^2 + 8 t + 1) */
+    if (kind == 1) {                     /* Eq. 3: (1-t)^8 (32 t^3 + 25 t^2 + 8 t + 1) */
         double u2 = u * u, u4 = u2 * u2, u8 = u4 * u4;
         return u8 * (32.0 * t * t * t + 25.0 * t * t + 8.0 * t + 1.0);
     }
@@ -104,7 +104,7 @@ double orc_dphi(int kind, int d, double t)
     if (!(t < 1.0)) return 0.0;
     if (t < 0.0) t = 0.0;
     double u = 1.0 - t;
-    if (kind == 1) {                     /* derivative of eq. (wendland) */
+    if (kind == 1) {                     /* derivative of Eq. 3 */
         double u2 = u * u, u4 = u2 * u2, u7 = u4 * u2 * u;
         return -22.0 * t * u7 * (16.0 * t * t + 7.0 * t + 1.0);
     }
@@ -113,7 +113,7 @@ double orc_dphi(int kind, int d, double t)
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Bump functions of eq. (bump): b_l(x) = a_l exp(beta (1 - 1/(1 - s))), s = |x-c_l|^2/rho_l^2,
+/* Bump functions of Eq. 7: b_l(x) = a_l exp(beta (1 - 1/(1 - s))), s = |x-c_l|^2/rho_l^2,
  * zero for s >= 1.  Optionally the derivatives with respect to the bump's parameters,
  * db[l*(d+2) + k] = d b_l / d c_{l,k} (k < d), db[l*(d+2)+d] = d b_l / d rho_l,
  * db[l*(d+2)+d+1] = d b_l / d a_l.                                                     */
@@ -163,7 +163,7 @@ double orc_sqdist(int d, const double *xi, const double *xj)
     return q;
 }
 
-/* Structural pattern test: stored iff i == j or d2 < r*r (strict, eq. (wendland)). */
+/* Structural pattern test: stored iff i == j or d2 < r*r (strict, Eq. 3). */
 int orc_in_pattern(int d, const double *xi, const double *xj, double r)
 {
     double r2 = r * r;
@@ -202,7 +202,7 @@ static double *bump_table(int64_t n, const double *X, const orc_hyper *h)
 
 /* ------------------------------------------------------------------------------------ */
 /* Brute-force all-pairs assembly of A = K + sigma^2 I in CSR, original index order,    */
-/* columns ascending (Sec. 3.6: every pair is evaluated).                               */
+/* columns ascending (Sec. 4.6: every pair is evaluated).                               */
 /*   rowptr: n+1 int64 (always written).  col/val: written when non-NULL (pass NULL on  */
 /*   a first call to learn nnz = rowptr[n]).  Returns nnz, or -1 on allocation failure. */
 /* ------------------------------------------------------------------------------------ */

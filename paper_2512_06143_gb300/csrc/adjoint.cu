@@ -10,7 +10,7 @@
 //     g_r  = 1/2 sum_ij (sum_l b_l(x_i) b_l(x_j) + w0) dphi_ij/dr W_ij
 //     g_s2 = 1/2 sum_i W_ii
 // and a per-point pass finishes g_{l,p} = sum_i (d b_l(x_i) / d theta_{l,p}) H_il with the bump
-// derivatives of eq. (bump).
+// derivatives of Eq. 7.
 #include <cmath>
 #include <cstring>
 #include <vector>

@@ -1,5 +1,5 @@
-// assemble.cu -- count -> scan -> fill assembly of A = K + sigma^2 I into CSR (Sec. 3.6 redesigned),
-// the bump tables (eq. bump), the Jacobi diagonal, and the FP64 values pass.
+// assemble.cu -- count -> scan -> fill assembly of A = K + sigma^2 I into CSR (Sec. 4.6 redesigned),
+// the bump tables (Eq. 7), the Jacobi diagonal, and the FP64 values pass.
 //
 // One CTA per work item (a run of at most kRowsPerItem rows of one occupied cell).  The CTA finds
 // the 3^d neighbour cells by binary search in the sorted cell-key table, orders their point ranges
@@ -268,7 +268,7 @@ size_t asm_smem_bytes(int D, bool fill, int L)
     return b + 16;
 }
 
-// Bump tables (eq. bump) in FP64 (+ an FP32 copy), the diagonal D_i = A_ii = (sum_l b_l^2 + w0)
+// Bump tables (Eq. 7) in FP64 (+ an FP32 copy), the diagonal D_i = A_ii = (sum_l b_l^2 + w0)
 // + sigma^2 and the Jacobi scales s_i = D_i^{-1/2}.
 template <int D>
 __global__ void k_bumps(const double4 *__restrict__ X64, int64_t n, KernelParams kp,
@@ -415,7 +415,7 @@ gp2s_status validate_hyper(gp2s_ctx *c, const gp2s_hyper *h)
     if (!(h->sigma2 >= 0.0) || !std::isfinite(h->sigma2)) return set_err(c, GP2S_EINVAL, "sigma2 must be finite and >= 0");
     if (!std::isfinite(h->beta) || !std::isfinite(h->w0)) return set_err(c, GP2S_EINVAL, "beta / w0 must be finite");
     if (h->kind != GP2S_WENDLAND_C2 && h->kind != GP2S_WENDLAND_C6_PAPER) return set_err(c, GP2S_EINVAL, "unknown Wendland kind");
-    if (h->kind == GP2S_WENDLAND_C6_PAPER && h->d > 3) return set_err(c, GP2S_EINVAL, "eq. (wendland) C6 form is positive definite only for d <= 3");
+    if (h->kind == GP2S_WENDLAND_C6_PAPER && h->d > 3) return set_err(c, GP2S_EINVAL, "Eq. 3 C6 form is positive definite only for d <= 3");
     if (h->L > 0 && (!h->centers || !h->radii || !h->amps)) return set_err(c, GP2S_EINVAL, "bump arrays are NULL");
     for (int l = 0; l < h->L; ++l) {
         if (!(h->radii[l] > 0.0) || !std::isfinite(h->radii[l]) || !std::isfinite(h->amps[l]))

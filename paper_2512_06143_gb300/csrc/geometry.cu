@@ -1,8 +1,8 @@
 // geometry.cu -- bounding box, Morton keys of a uniform cell grid, point permutation, cell table.
 //
-// This replaces the paper's all-pairs block decomposition (Sec. 3.6, App. B.6: every block of the
+// This replaces the paper's all-pairs block decomposition (Sec. 4.6, App. B.7: every block of the
 // n x n covariance is evaluated because the non-zeros are not known in advance).  The kernel of
-// Sec. 3.1 carries the Wendland factor phi(|xi - xj| / r), which is zero for |xi - xj| >= r, so a
+// Sec. 4.1 carries the Wendland factor phi(|xi - xj| / r), which is zero for |xi - xj| >= r, so a
 // uniform grid of cells with edge h >= r puts every stored pair into two cells whose integer
 // coordinates differ by at most one per dimension.  Sorting the points along a Morton curve of a
 // finer grid (2^F sub-cells per cell edge) keeps each cell contiguous and orders the points inside a

@@ -17,7 +17,7 @@ constexpr int kMaxBumps = 32;
 constexpr int kWarp = 32;
 
 // ------------------------------------------------------------------------------------------
-// Kernel hyperparameters passed by value to kernels (eq. wendland, eq. bump, Sec. 3.3).
+// Kernel hyperparameters passed by value to kernels (Eq. 3, Eq. 7, Sec. 4.3).
 // ------------------------------------------------------------------------------------------
 struct KernelParams {
     int d, L, kind, pad;

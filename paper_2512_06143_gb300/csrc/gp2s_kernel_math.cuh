@@ -1,13 +1,13 @@
 // gp2s_kernel_math.cuh -- device evaluation of the kernel pieces shared by the assembly, value and
-// adjoint kernels: the Wendland taper (eq. wendland and the "C2" reading) and its derivative.
+// adjoint kernels: the Wendland taper (Eq. 3 and the "C2" reading) and its derivative.
 #pragma once
 
 #include <cuda_runtime.h>
 
 namespace gp2s {
 
-// phi(t) for t = |xi - xj| / r; zero for t >= 1 (strict support, eq. wendland).
-//   kind 1 (eq. wendland):        (1-t)^8 (32 t^3 + 25 t^2 + 8 t + 1)
+// phi(t) for t = |xi - xj| / r; zero for t >= 1 (strict support, Eq. 3).
+//   kind 1 (Eq. 3):        (1-t)^8 (32 t^3 + 25 t^2 + 8 t + 1)
 //   kind 0, d <= 3 (C2 reading):  (1-t)^4 (4 t + 1)
 //   kind 0, d == 4 (C2 reading):  (1-t)^5 (5 t + 1)
 template <class T>

@@ -3,7 +3,7 @@
 // stochastic Lanczos quadrature needs.
 //
 // The paper solves K^{-1} y by MINRES on the host (App. B.7) and leaves the log-determinant method
-// open (Sec. 3.6).  A = K + sigma^2 I is symmetric positive definite, so conjugate gradients solve
+// open (Sec. 4.6).  A = K + sigma^2 I is symmetric positive definite, so conjugate gradients solve
 // the same system; running the y column and the m probe columns together lets one pass over the CSR
 // serve all of them (the SpMM), and the CG step lengths / direction coefficients of each probe column
 // are its Lanczos tridiagonal (the CG-Lanczos relation), which is what SLQ needs.

@@ -1,4 +1,4 @@
-// logdet.cu -- log|A| (Sec. 3; the method is left open in Sec. 3.6 / App. B.7):
+// logdet.cu -- log|A| (Sec. 3; the method is left open in Sec. 4.6 / App. B.7):
 //   * SLQ: stochastic Lanczos quadrature (Ubaru, Chen & Saad 2017) on Ah = D^{-1/2} A D^{-1/2}.
 //     For every probe z_s the tridiagonal T_s comes from the recorded CG coefficients (CG-Lanczos
 //     relation); its eigenvalues theta_j and eigenvector first components tau_j come from an

@@ -23,8 +23,8 @@ Workloads (the datasets of the paper are not available; these stand in for them)
                       with points uniform on the sphere, time ~ U[0,1] and elevation a smooth
                       16-mode random Fourier field of (lon, lat) scaled to [0,1]; L = 8 bumps
                       (radii 0.3), r tuned for ~60 entries per row, sigma^2 = 4e-4 (the shape of
-                      the 10-million-point temperature run, Sec. 4.5 / App. B.5).
-  * ``f1_1d``      -- the 1-D test function of Sec. 4.1, f1(x) = sin 5x + cos 20x
+                      the 10-million-point temperature run, Sec. 5.5 / App. B.5).
+  * ``f1_1d``      -- the 1-D test function of Sec. 5.1, f1(x) = sin 5x + cos 20x
                       + 2 (x - 0.4)^2 cos 400x, on N uniform points in [0, 1].
 """
 from __future__ import annotations
@@ -165,7 +165,7 @@ def batch(seed: int = 0, count: int = 256, n_range=(2048, 65536), nnz_range=(10.
 
 
 def f1(x):
-    """Sec. 4.1's 1-D test function."""
+    """Sec. 5.1's 1-D test function."""
     x = np.asarray(x, np.float64)
     return np.sin(5 * x) + np.cos(20 * x) + 2 * (x - 0.4) ** 2 * np.cos(400 * x)
 

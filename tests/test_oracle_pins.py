@@ -49,7 +49,7 @@ def test_rademacher_probes_definition(orc):
 
 
 # ---------------------------------------------------------------------------------------
-# Wendland tapers: eq. (wendland) and the C2 reading
+# Wendland tapers: Eq. 3 and the C2 reading
 # ---------------------------------------------------------------------------------------
 def test_wendland_hand_values(orc):
     rows = [l.split() for l in open(os.path.join(GOLD, "wendland_values.txt")) if l.strip() and l[0] != "#"]
@@ -65,7 +65,7 @@ def test_wendland_support_and_endpoints(orc, kind, d):
     for t in [1.0, 1.0 + 1e-12, 1.5, 10.0]:
         assert float(orc.phi(kind, d, t)) == 0.0
         assert float(orc.dphi(kind, d, t)) == 0.0
-    # order of vanishing at t = 1: C2 (d<=3) ~ 5 e^4, C2 (d=4) ~ 6 e^5, eq. (wendland) ~ 66 e^8
+    # order of vanishing at t = 1: C2 (d<=3) ~ 5 e^4, C2 (d=4) ~ 6 e^5, Eq. 3 ~ 66 e^8
     e = 1e-3
     if kind == 1:
         lead, p = 66.0, 8
@@ -101,7 +101,7 @@ def test_wendland_gram_is_positive_semidefinite(orc, kind, d):
 
 
 # ---------------------------------------------------------------------------------------
-# Bump functions: eq. (bump)
+# Bump functions: Eq. 7
 # ---------------------------------------------------------------------------------------
 def _bump_hyper(orc, d=3, beta=1.3):
     return orc.Hyper(d=d, r=0.1, sigma2=1e-3, centers=np.array([[0.2, 0.4, 0.6][:d], [0.5] * d]),
@@ -150,7 +150,7 @@ def test_bump_derivatives_match_finite_differences(orc):
 
 
 # ---------------------------------------------------------------------------------------
-# Kernel: product of a Wendland taper and the rank-L bump kernel (Sec. 3.1, 3.3, Thm 1)
+# Kernel: product of a Wendland taper and the rank-L bump kernel (Sec. 4.1, 3.3, Thm 1)
 # ---------------------------------------------------------------------------------------
 @pytest.mark.parametrize("d,kind", [(1, 0), (2, 0), (3, 1), (4, 0)])
 def test_kernel_symmetric_psd_compact(orc, d, kind):
