@@ -94,13 +94,17 @@ typedef struct {
     double tol_probe;        /* relative residual of the probe solves used by the gradient, default 1e-5 */
     uint64_t seed;           /* probe seed, default 0 */
     int32_t precond;         /* 1 = Jacobi scaling Ah = D^{-1/2} A D^{-1/2} (0 is read as 1);
-                                2 = block-Jacobi on Morton-consecutive 64-row blocks of Ah on top of
-                                it (MIXED precision; FP64 precision runs 1).  Default 2. */
+                                2 = block-Jacobi on Morton-consecutive blocks of bj_block rows of
+                                Ah on top of it (MIXED precision; FP64 precision runs 1).
+                                Default 2. */
     int32_t exact_support;   /* 1 = skip the FP32 guard-band pre-test (every candidate pair is
                                 decided by the FP64 test); default 0 */
     int32_t max_outer;       /* refinement steps cap, default 8 */
     int32_t profile;         /* 1 = time every SpMM launch with CUDA events (gp2s_lml_info.ms_spmm); default 0 */
-    int32_t reserved[2];
+    int32_t bj_block;        /* rows per block-Jacobi block (precond = 2): 64, 128, or 0 =
+                                automatic (128 when A has at least 64 stored entries per row, else
+                                64); default 0 */
+    int32_t reserved;
 } gp2s_opts;
 
 typedef struct {
@@ -218,9 +222,10 @@ gp2s_status gp2s_lml(gp2s_ctx *ctx, int64_t n, const double *X, const double *y,
 /*
  * LML and its gradient d LML / d theta = 1/2 a^T (dA/dtheta) a - 1/2 tr(A^{-1} dA/dtheta),
  * theta = [centers (L x d), radii (L), amps (L), r, sigma2].  The trace uses Hutchinson's
- * estimator with the same probes as SLQ (u_s = A^{-1} z_s from the shared multi-RHS CG) in SLQ
- * mode, and the exact dense inverse in EXACT mode.  dA/dtheta is formed pair by pair on A's
- * pattern and contracted on the fly; it is never stored.
+ * estimator with opts->probes Rademacher probes in both log-determinant modes (u_s = A^{-1} z_s
+ * are the probe columns of the shared multi-RHS CG; in SLQ mode they are the SLQ probes, solved
+ * to opts->tol_probe); the quadratic term a^T dA a is exact.  dA/dtheta is formed pair by pair
+ * on A's pattern and contracted on the fly; it is never stored.
  *   grad_host: host, gp2s_num_params(d, L) doubles.
  */
 gp2s_status gp2s_lml_grad(gp2s_ctx *ctx, int64_t n, const double *X, const double *y,

@@ -45,7 +45,8 @@ class Opts(ctypes.Structure):
                 ("probes", ctypes.c_int32), ("lanczos_steps", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("tol_inner", ctypes.c_double), ("tol_refine", ctypes.c_double), ("tol_probe", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("precond", ctypes.c_int32), ("exact_support", ctypes.c_int32),
-                ("max_outer", ctypes.c_int32), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("max_outer", ctypes.c_int32), ("profile", ctypes.c_int32), ("bj_block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class AssembleInfo(ctypes.Structure):

@@ -266,9 +266,8 @@ gp2s_status dispatch_adjoint(gp2s_ctx *c, int d, const AdjArgs &g, const KernelP
 
 }  // namespace
 
-gp2s_status adjoint_gradient(gp2s_ctx *c, int m, bool exact_inverse, double *grad_host)
+gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
 {
-    (void)exact_inverse;
     const Assembled &A = c->A;
     const int64_t n = A.n;
     const int d = A.d, L = A.L;

@@ -165,6 +165,8 @@ static gp2s_status validate_opts(gp2s_ctx *c, const gp2s_opts *o)
     if (!(o->tol_inner > 0.0) || !(o->tol_refine > 0.0) || !(o->tol_probe > 0.0)) return set_err(c, GP2S_EINVAL, "tolerances must be > 0");
     if (o->max_outer < 0) return set_err(c, GP2S_EINVAL, "max_outer must be >= 0");
     if (o->precond < 0 || o->precond > 2) return set_err(c, GP2S_EINVAL, "precond must be 0, 1 or 2");
+    if (o->bj_block != 0 && o->bj_block != 64 && o->bj_block != 128)
+        return set_err(c, GP2S_EINVAL, "bj_block must be 0, 64 or 128");
     return GP2S_OK;
 }
 
@@ -280,7 +282,7 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->val32, &c->val64, &c->counters, &c->vec, &c->vec64, &c->partials, &c->scal,
                       &c->Z, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
                       &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_tpart, &c->rb_seg,
-                      &c->bj_Minv, &c->bj_ld};
+                      &c->bj_Minv, &c->bj_ld, &c->bj_Minv_y};
     for (DevBuf *b : bufs) free_buf(*b);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (gp2s_ctx *w : c->workers) gp2s_destroy(w);
@@ -442,7 +444,7 @@ static gp2s_status lml_impl(gp2s_ctx *c, int64_t n, const double *X, const doubl
     GP2S_TRY(dot_f64(c, c->ys64.as<double>(), c->vec64.as<double>() + 3 * A.n, A.n, &quad));
     const double logdet = ldiag + lhat;
     const double val = -0.5 * quad - 0.5 * logdet - 0.5 * (double)A.n * std::log(2.0 * M_PI);
-    if (grad) GP2S_TRY(adjoint_gradient(c, m, false, grad));
+    if (grad) GP2S_TRY(adjoint_gradient(c, m, grad));
     cudaEventRecord(e4.e, c->stream);
     GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
     *lml = val;

@@ -101,8 +101,10 @@ struct gp2s_ctx {
     bool rb_valid = false;
     int64_t rb_entries = 0;
     // block-Jacobi preconditioner: FP32 M^{-1} per 64-row block and the block log-determinants
-    gp2s::DevBuf bj_Minv, bj_ld;
+    gp2s::DevBuf bj_Minv, bj_ld, bj_Minv_y;
     bool bj_valid = false;
+    int bj_size = 64;               // rows per block-Jacobi block of the probe columns
+    int bj_size_y = 64;             // rows per block of the y column (64 or 128)
     double bj_logdet = 0.0;
     bool probes_for_grad = false;   // the probe solves feed the Hutchinson gradient
     // batched form: worker contexts (own stream and workspace each), created on first use
@@ -193,7 +195,7 @@ gp2s_status sum_log_diag(gp2s_ctx *c, double *out_host);
 gp2s_status dot_f64(gp2s_ctx *c, const double *a, const double *b, int64_t n, double *out_host);
 
 // Adjoint (adjoint.cu) ---------------------------------------------------------------------------
-gp2s_status adjoint_gradient(gp2s_ctx *c, int m, bool exact_inverse, double *grad_host);
+gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host);
 
 // Batched engine (batched.cu) ----------------------------------------------------------------
 gp2s_status batched_lml(gp2s_ctx *c, int32_t B, const int64_t *n, const double *const *X,

@@ -1035,37 +1035,36 @@ gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride
 }
 
 // ---------------------------------------------------------------------------------------------
-// Block-Jacobi preconditioner on Morton-consecutive blocks of kBJ rows.
+// Block-Jacobi preconditioner on Morton-consecutive blocks of BJ = 64 or 128 rows.
 //
 // The paper leaves the solver's preconditioning open.  M = blockdiag(Ah_bb) = L L^T over blocks
-// of kBJ consecutive rows of the Morton order: spatially close points whose mutual covariances are
+// of BJ consecutive rows of the Morton order: spatially close points whose mutual covariances are
 // the largest entries of their rows, so these small dense blocks cut the iteration count
 // several-fold against plain Jacobi scaling.  The probe columns run their first k steps as plain
 // CG on Ah (those coefficients are Ah's Lanczos tridiagonal for SLQ; SLQ on the preconditioned
 // operator L^{-1} Ah L^{-T} would have a far larger probe variance) and are then restarted as PCG
 // with M to finish the solves the gradient needs; the y column runs PCG throughout.
 // ---------------------------------------------------------------------------------------------
-constexpr int kBJ = 64;
 constexpr int kPCThreads = 256;
 
-// One CTA per block: dense FP64 block from the CSR, Cholesky, L^{-1}; writes M^{-1} = L^{-T} L^{-1}
-// (FP32, symmetric) and the block's log|M_b|.
+// One CTA per block of BJ rows (BJ = 64 or 128): dense FP64 block from the CSR, Cholesky
+// L L^T, L^{-1} in place, then M^{-1} = L^{-T} L^{-1} (FP32, symmetric) and the block's log|M_b|.
 // Rows beyond n (last block) are padded with the identity.
+template <int BJ>
 __global__ void __launch_bounds__(kPCThreads)
 k_bj_build(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const double *__restrict__ val64,
            int64_t n, float *__restrict__ Minv32, double *__restrict__ logdet_blk,
            int *__restrict__ bad)
 {
     extern __shared__ double bj_sh[];
-    double (*S)[kBJ + 1] = reinterpret_cast<double (*)[kBJ + 1]>(bj_sh);                    // L
-    double (*V)[kBJ + 1] = reinterpret_cast<double (*)[kBJ + 1]>(bj_sh + kBJ * (kBJ + 1));  // L^{-1}
+    double (*S)[BJ + 1] = reinterpret_cast<double (*)[BJ + 1]>(bj_sh);   // L, then L^{-1} (lower)
+    double *tmp = bj_sh + BJ * (BJ + 1);                                 // one column of L
     const int64_t b = blockIdx.x;
-    const int64_t i0 = b * kBJ;
-    const int nb = (int)(n - i0 < kBJ ? n - i0 : kBJ);
-    for (int t = threadIdx.x; t < kBJ * kBJ; t += blockDim.x) {
-        int i = t / kBJ, j = t % kBJ;
+    const int64_t i0 = b * BJ;
+    const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
+    for (int t = threadIdx.x; t < BJ * BJ; t += blockDim.x) {
+        int i = t / BJ, j = t % BJ;
         S[i][j] = (i == j && i >= nb) ? 1.0 : 0.0;
-        V[i][j] = 0.0;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1076,54 +1075,59 @@ k_bj_build(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, 
         }
     }
     __syncthreads();
-    for (int j = 0; j < kBJ; ++j) {
+    // right-looking Cholesky of the lower triangle
+    for (int j = 0; j < BJ; ++j) {
         if (threadIdx.x == 0) {
             double d = S[j][j];
             if (!(d > 0.0)) { atomicOr(bad, 1); d = 1.0; }
             S[j][j] = sqrt(d);
         }
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < kBJ; i += blockDim.x) S[i][j] /= S[j][j];
+        for (int i = j + 1 + threadIdx.x; i < BJ; i += blockDim.x) S[i][j] /= S[j][j];
         __syncthreads();
-        for (int t = threadIdx.x; t < kBJ * kBJ; t += blockDim.x) {
-            int i = t / kBJ, k = t % kBJ;
+        for (int t = threadIdx.x; t < BJ * BJ; t += blockDim.x) {
+            int i = t / BJ, k = t % BJ;
             if (i > j && k > j && k <= i) S[i][k] -= S[i][j] * S[k][j];
         }
         __syncthreads();
-    }
-    // L^{-1}: column c solves L v = e_c by forward substitution (one thread per column)
-    if (threadIdx.x < kBJ) {
-        const int cc = threadIdx.x;
-        V[cc][cc] = 1.0 / S[cc][cc];
-        for (int i = cc + 1; i < kBJ; ++i) {
-            double s = 0.0;
-            for (int k = cc; k < i; ++k) s += S[i][k] * V[k][cc];
-            V[i][cc] = -s / S[i][i];
-        }
-    }
-    __syncthreads();
-    float *Mb = Minv32 + b * kBJ * kBJ;
-    for (int t = threadIdx.x; t < kBJ * kBJ; t += blockDim.x) {
-        int i = t / kBJ, j = t % kBJ;
-        // (L^{-T} L^{-1})_ij = sum_k V[k][i] V[k][j], k >= max(i, j)
-        double s = 0.0;
-        for (int k = i > j ? i : j; k < kBJ; ++k) s += V[k][i] * V[k][j];
-        Mb[t] = (float)s;
     }
     if (threadIdx.x == 0) {
         double ld = 0.0;
         for (int i = 0; i < nb; ++i) ld += log(S[i][i]);
         logdet_blk[b] = 2.0 * ld;
     }
+    // V = L^{-1} in place, columns from the last to the first: V L = I gives V_jj = 1 / L_jj and
+    // V_ij = -(sum_{k=j+1..i} V_ik L_kj) / L_jj, which needs only the columns of V to the right of
+    // j (already in place) and column j of L (saved in tmp first).
+    for (int j = BJ - 1; j >= 0; --j) {
+        for (int k = j + threadIdx.x; k < BJ; k += blockDim.x) tmp[k] = S[k][j];
+        __syncthreads();
+        const double ljj = tmp[j];
+        for (int i = j + 1 + threadIdx.x; i < BJ; i += blockDim.x) {
+            double s = 0.0;
+            for (int k = j + 1; k <= i; ++k) s += S[i][k] * tmp[k];
+            S[i][j] = -s / ljj;
+        }
+        if (threadIdx.x == 0) S[j][j] = 1.0 / ljj;
+        __syncthreads();
+    }
+    float *Mb = Minv32 + b * BJ * BJ;
+    for (int t = threadIdx.x; t < BJ * BJ; t += blockDim.x) {
+        int i = t / BJ, j = t % BJ;
+        // (L^{-T} L^{-1})_ij = sum_k V[k][i] V[k][j], k >= max(i, j)
+        double s = 0.0;
+        for (int k = i > j ? i : j; k < BJ; ++k) s += S[k][i] * S[k][j];
+        Mb[t] = (float)s;
+    }
 }
 
-// Out (kBJ x m, row stride m) = Mat (kBJ x kBJ, given transposed in shared memory: MT[k][i] =
-// Mat[i][k]) x In (kBJ x m in shared memory).  Each thread owns 4 x 4 output tiles.
-template <class Fn>
+// Out (BJ x m, row stride m) = Mat (BJ x BJ, given transposed in shared memory: MT[k][i] =
+// Mat[i][k]) x In (BJ x m in shared memory).  Each thread owns 4 x 4 output tiles.
+template <int BJ, class Fn>
 __device__ __forceinline__ void bj_tile_mm(const float *__restrict__ MT, const float *__restrict__ In, int m, Fn &&emit)
 {
     const int cgroups = m / 4;
-    const int tiles = (kBJ / 4) * cgroups;
+    const int tiles = (BJ / 4) * cgroups;
     for (int tt = threadIdx.x; tt < tiles; tt += blockDim.x) {
         const int rg = tt / cgroups, cg = tt - rg * cgroups;
         const int i0 = rg * 4, c0 = cg * 4;
@@ -1134,8 +1138,8 @@ __device__ __forceinline__ void bj_tile_mm(const float *__restrict__ MT, const f
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc2[a][q] = make_float2(0.0f, 0.0f);
 #pragma unroll 8
-        for (int k = 0; k < kBJ; ++k) {
-            const float4 mv = *reinterpret_cast<const float4 *>(MT + k * kBJ + i0);
+        for (int k = 0; k < BJ; ++k) {
+            const float4 mv = *reinterpret_cast<const float4 *>(MT + k * BJ + i0);
             const float4 iv = *reinterpret_cast<const float4 *>(In + k * m + c0);
             const float2 mp[2] = {make_float2(mv.x, mv.y), make_float2(mv.z, mv.w)};
             const float ia[4] = {iv.x, iv.y, iv.z, iv.w};
@@ -1158,12 +1162,12 @@ __device__ __forceinline__ void bj_tile_mm(const float *__restrict__ MT, const f
     }
 }
 
-// Fused PCG step on kBJ-row blocks.  INIT: x = 0, r = rhs, z = M^{-1} r, p = z.  UPDATE:
+// Fused PCG step on BJ-row blocks.  INIT: x = 0, r = rhs, z = M^{-1} r, p = z.  UPDATE:
 // x += alpha p, r -= alpha q, z = M^{-1} r.  RESTART (a CG column switching to PCG): x and r kept,
 // z = M^{-1} r, p = z.  All emit per-CTA partial dots r^T z and r^T r per column.
 // CTAs [0, gz) work on the probe group (n x m), CTAs [gz, gridDim) on the y column.
 enum { PC_INIT = 0, PC_UPDATE = 1, PC_RESTART = 2 };
-template <int MODE>
+template <int MODE, int BJ>
 __global__ void __launch_bounds__(kPCThreads, 3)
 k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv32, float *__restrict__ xz,
           float *__restrict__ rz, float *__restrict__ pz, const float *__restrict__ qz, float *__restrict__ zz,
@@ -1171,13 +1175,12 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
           float *__restrict__ zy, const double *__restrict__ rhs_y, const double *__restrict__ sc,
           double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride)
 {
-    constexpr bool INIT = MODE == PC_INIT;
     constexpr bool SETP = MODE != PC_UPDATE;   // p = z (INIT, RESTART)
     extern __shared__ __align__(16) float pc_sh[];
     if ((int)blockIdx.x < gz) {
         float *MT = pc_sh;                       // M^{-1} (symmetric, so no transpose)
-        float *R = pc_sh + kBJ * kBJ;            // kBJ x m residual block
-        float *Pd = R + kBJ * m;                 // 16 x m partial dot rows (r^T z), then (r^T r)
+        float *R = pc_sh + BJ * BJ;              // BJ x m residual block
+        float *Pd = R + BJ * m;                  // (BJ / 4) x m partial dot rows (r^T z)
         double acc_rz = 0.0, acc_rr = 0.0;       // thread c < m: this CTA's column sums
         // elementwise phase: thread t owns the 4 columns 4 (t % cgs) .. +3 of rows t / cgs + k rps
         const int cgs = m / 4;
@@ -1189,12 +1192,12 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
         for (int q = 0; q < 4; ++q)
             a4[q] = MODE == PC_UPDATE ? (float)sc[(ecg * 4 + q + 1) * kScal + S_ALPHA] : 0.0f;
         for (int64_t b = blockIdx.x; b < nblk; b += gz) {
-            const int64_t i0 = b * kBJ;
-            const int nb = (int)(n - i0 < kBJ ? n - i0 : kBJ);
-            const float4 *Mg = reinterpret_cast<const float4 *>(Minv32 + b * kBJ * kBJ);
-            for (int t = threadIdx.x; t < kBJ * kBJ / 4; t += blockDim.x) reinterpret_cast<float4 *>(MT)[t] = Mg[t];
+            const int64_t i0 = b * BJ;
+            const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
+            const float4 *Mg = reinterpret_cast<const float4 *>(Minv32 + b * BJ * BJ);
+            for (int t = threadIdx.x; t < BJ * BJ / 4; t += blockDim.x) reinterpret_cast<float4 *>(MT)[t] = Mg[t];
             if (eth) {
-                for (int i = er0; i < kBJ; i += rps) {
+                for (int i = er0; i < BJ; i += rps) {
                     float r4[4] = {0.f, 0.f, 0.f, 0.f};
                     if (i < nb) {
                         const int64_t e = (i0 + i) * m + ecg * 4;
@@ -1221,7 +1224,7 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
             }
             __syncthreads();
             // z = M^{-1} r, written with the partial dots of this block
-            bj_tile_mm(MT, R, m, [&](int it, int c0, float (&acc)[4][4]) {
+            bj_tile_mm<BJ>(MT, R, m, [&](int it, int c0, float (&acc)[4][4]) {
                 float drz[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int a = 0; a < 4; ++a) {
@@ -1239,7 +1242,7 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
             __syncthreads();
             if ((int)threadIdx.x < m) {
                 float srz = 0.0f, srr = 0.0f;
-                for (int g = 0; g < 16; ++g) srz += Pd[g * m + threadIdx.x];
+                for (int g = 0; g < BJ / 4; ++g) srz += Pd[g * m + threadIdx.x];
                 for (int i = 0; i < nb; ++i) {
                     const float rv = R[i * m + threadIdx.x];
                     srr = fmaf(rv, rv, srr);
@@ -1254,24 +1257,24 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
             part_rr[(int64_t)(threadIdx.x + 1) * pstride + blockIdx.x] = acc_rr;
         }
     } else {
-        // y column: the CTA's four 64-thread groups each take one block; thread i of a group owns
+        // y column: the CTA's BJ-thread groups each take one block; thread i of a group owns
         // row i and forms z_i = sum_k Minv[k][i] r_k (coalesced rows of the symmetric M^{-1})
-        constexpr int G = kPCThreads / kBJ;
-        float *R = pc_sh;                         // G x kBJ
+        constexpr int G = kPCThreads / BJ;
+        float *R = pc_sh;                         // G x BJ
         __shared__ double red[2][kPCThreads / kWarp];
         const int gy = gridDim.x - gz;
         const int cb = blockIdx.x - gz;
-        const int sub = threadIdx.x / kBJ;
+        const int sub = threadIdx.x / BJ;
         double arz = 0.0, arr = 0.0;
         const double alpha = MODE == PC_UPDATE ? sc[S_ALPHA] : 0.0;
         const float a = (float)alpha;
         for (int64_t bg = cb; bg * G < nblk; bg += gy) {
             const int64_t b = bg * G + sub;
             const bool live = b < nblk;
-            const int64_t i0 = b * kBJ;
-            const int nb = live ? (int)(n - i0 < kBJ ? n - i0 : kBJ) : 0;
+            const int64_t i0 = b * BJ;
+            const int nb = live ? (int)(n - i0 < BJ ? n - i0 : BJ) : 0;
             {
-                const int i = threadIdx.x % kBJ;
+                const int i = threadIdx.x % BJ;
                 float r = 0.0f;
                 if (i < nb) {
                     const int64_t e = i0 + i;
@@ -1290,16 +1293,16 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
                         }
                     }
                 }
-                R[sub * kBJ + i] = r;
+                R[sub * BJ + i] = r;
             }
             __syncthreads();
             if (live) {
-                const int i = threadIdx.x % kBJ;
+                const int i = threadIdx.x % BJ;
                 float z = 0.0f;
-                const float *Mb = Minv32 + b * kBJ * kBJ;
-                const float *Rb = R + sub * kBJ;
+                const float *Mb = Minv32 + b * BJ * BJ;
+                const float *Rb = R + sub * BJ;
 #pragma unroll 8
-                for (int k = 0; k < kBJ; ++k) z = fmaf(Mb[k * kBJ + i], Rb[k], z);
+                for (int k = 0; k < BJ; ++k) z = fmaf(Mb[k * BJ + i], Rb[k], z);
                 if (i < nb) {
                     zy[i0 + i] = z;
                     if (SETP) py[i0 + i] = z;
@@ -1329,23 +1332,50 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
     }
 }
 
-size_t pc_smem(int m) { return sizeof(float) * ((size_t)kBJ * kBJ + (size_t)kBJ * (m > 0 ? m : 1) + 16 * (size_t)(m > 0 ? m : 1)) + 64; }
+// Dynamic shared memory of k_pc_step: the probe group stages the block's M^{-1} (BJ x BJ), the
+// BJ x m residual block and the (BJ / 4) x m partial dots; the y column stages kPCThreads
+// residuals (kPCThreads / BJ blocks of BJ rows).  The launch covers both.
+size_t pc_smem(int m, int bj)
+{
+    const size_t z = m > 0 ? (size_t)bj * bj + (size_t)bj * m + (size_t)(bj / 4) * m : 0;
+    const size_t y = (size_t)kPCThreads;
+    return sizeof(float) * (z > y ? z : y) + 64;
+}
 
-// Build the block-Jacobi factors of the current matrix (FP64 blocks -> FP32 L and M^{-1}).
-gp2s_status build_block_jacobi(gp2s_ctx *c)
+// Block size of the block-Jacobi preconditioner: opts.bj_block when set, else 128 rows for
+// matrices with at least 64 stored entries per row (there the larger blocks cut the iteration
+// count by about a fifth, which outweighs the dearer step), else 64 (with fewer entries per row
+// 64-row blocks already capture the neighbourhoods).  The probe columns and the y column can use
+// different sizes (two sets of factors); the automatic choice gives both the same.
+int bj_block_size(const gp2s_ctx *c)
+{
+    const int req = c->A.opts.bj_block;
+    if (req == 64 || req == 128) return req;
+    return c->A.nnz >= 64 * c->A.n ? 128 : 64;
+}
+
+// Build one set of block-Jacobi factors (FP64 blocks -> FP32 M^{-1}) with blocks of bj rows.
+static gp2s_status build_bj_set(gp2s_ctx *c, int bj, DevBuf &minv, double *logdet)
 {
     const int64_t n = c->A.n;
-    const int64_t nblk = ceil_div(n, kBJ);
-    GP2S_TRY(ensure(c, c->bj_Minv, sizeof(float) * (size_t)nblk * kBJ * kBJ));
+    const int64_t nblk = ceil_div(n, bj);
+    GP2S_TRY(ensure(c, minv, sizeof(float) * (size_t)nblk * bj * bj));
     GP2S_TRY(ensure(c, c->bj_ld, sizeof(double) * (size_t)nblk + 64));
     GP2S_TRY(ensure(c, c->counters, 256));
     int *bad = reinterpret_cast<int *>(c->counters.as<char>() + 208);
     GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-    const size_t smem = sizeof(double) * 2 * kBJ * (kBJ + 1);
-    GP2S_TRY(smem_attr(c, (const void *)k_bj_build, smem));
-    k_bj_build<<<(unsigned)nblk, kPCThreads, smem, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(),
-                                                                c->val64.as<double>(), n, c->bj_Minv.as<float>(),
-                                                                c->bj_ld.as<double>(), bad);
+    const size_t smem = sizeof(double) * ((size_t)bj * (bj + 1) + bj);
+    if (bj == 128) {
+        GP2S_TRY(smem_attr(c, (const void *)k_bj_build<128>, smem));
+        k_bj_build<128><<<(unsigned)nblk, kPCThreads, smem, c->stream>>>(
+            c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val64.as<double>(), n, minv.as<float>(),
+            c->bj_ld.as<double>(), bad);
+    } else {
+        GP2S_TRY(smem_attr(c, (const void *)k_bj_build<64>, smem));
+        k_bj_build<64><<<(unsigned)nblk, kPCThreads, smem, c->stream>>>(
+            c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val64.as<double>(), n, minv.as<float>(),
+            c->bj_ld.as<double>(), bad);
+    }
     GP2S_LAUNCH(c);
     // log|M| = sum of the block log-determinants (fixed-order host sum)
     std::vector<double> ld((size_t)nblk);
@@ -1356,7 +1386,22 @@ gp2s_status build_block_jacobi(gp2s_ctx *c)
     if (hbad) return set_err(c, GP2S_ENOTPD, "block-Jacobi: a diagonal block is not positive definite");
     double s = 0.0;
     for (double v : ld) s += v;
-    c->bj_logdet = s;
+    *logdet = s;
+    return GP2S_OK;
+}
+
+// Build the block-Jacobi factors of the current matrix: one set for the probe columns and, when
+// the y column uses another block size, a second set for it.
+gp2s_status build_block_jacobi(gp2s_ctx *c)
+{
+    const int bjz = bj_block_size(c), bjy = bjz;
+    GP2S_TRY(build_bj_set(c, bjz, c->bj_Minv, &c->bj_logdet));
+    if (bjy != bjz) {
+        double ldy = 0.0;
+        GP2S_TRY(build_bj_set(c, bjy, c->bj_Minv_y, &ldy));
+    }
+    c->bj_size = bjz;
+    c->bj_size_y = bjy;
     c->bj_valid = true;
     return GP2S_OK;
 }
@@ -1428,32 +1473,58 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     const bool pc_avail = std::is_same<T, float>::value && c->bj_valid;
     bool pcy = pc_avail;
     bool pcz = pc_avail && kmin_probe == 0;
-    const int64_t nblk = ceil_div(n, kBJ);
-    // probe group: one 64-row block per CTA step, ~6 CTAs per SM; y column: 4 blocks per CTA step
-    const int pgz = m > 0 ? (int)std::min<int64_t>((int64_t)c->num_sms * 6, nblk) : 0;
-    const int pgy = (int)std::min<int64_t>(kMaxPartBlocks, ceil_div(nblk, kPCThreads / kBJ));
+    // probe group: bjz-row blocks, one block per CTA step, ~6 CTAs per SM; y column: bjy-row
+    // blocks, kPCThreads / bjy blocks per CTA step
+    const int bjz = c->bj_size, bjy = c->bj_size_y;
+    const int64_t nblkz = ceil_div(n, bjz), nblky = ceil_div(n, bjy);
+    const int pgz = m > 0 ? (int)std::min<int64_t>((int64_t)c->num_sms * 6, nblkz) : 0;
+    const int pgy = (int)std::min<int64_t>(kMaxPartBlocks, ceil_div(nblky, kPCThreads / bjy));
     GP2S_TRY(ensure(c, c->partials, sizeof(double) * (size_t)pstride * kMaxCols * 2));
     part = c->partials.as<double>();
     double *part_rr = part + (size_t)pstride * kMaxCols;
-    const float *Minv = pc_avail ? c->bj_Minv.as<float>() : nullptr;
+    const float *Minvz = pc_avail ? c->bj_Minv.as<float>() : nullptr;
+    const float *Minvy = pc_avail ? (bjy == bjz ? c->bj_Minv.as<float>() : c->bj_Minv_y.as<float>()) : nullptr;
     if (pc_avail) {
-        const size_t smem = pc_smem(m);
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_INIT>, smem));
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_UPDATE>, smem));
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_RESTART>, smem));
+        const size_t smem = pc_smem(m, bjz);
+        if (bjz == 128) {
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_INIT, 128>, smem));
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_UPDATE, 128>, smem));
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_RESTART, 128>, smem));
+        } else {
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_INIT, 64>, smem));
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_UPDATE, 64>, smem));
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_step<PC_RESTART, 64>, smem));
+        }
     }
-#define GP2S_PC(MODE, GZ, GY, MM)                                                                                \
-    k_pc_step<MODE><<<(GZ) + (GY), kPCThreads, pc_smem(MM), c->stream>>>(                                       \
-        n, MM, nblk, GZ, Minv, (float *)B.xz, (float *)B.rz, (float *)B.pz, (const float *)B.qz, (float *)B.zz, \
-        (float *)B.xy, (float *)B.ry, (float *)B.py, (const float *)B.qy, (float *)B.zy, rhs_y, sc, part, part_rr, pstride)
+    // probe group (bjz-row blocks) and y column (bjy-row blocks) launches
+#define GP2S_PCZ_BJ(MODE, BJ, MM)                                                                                   \
+    k_pc_step<MODE, BJ><<<pgz, kPCThreads, pc_smem(MM, BJ), c->stream>>>(                                          \
+        n, MM, nblkz, pgz, Minvz, (float *)B.xz, (float *)B.rz, (float *)B.pz, (const float *)B.qz, (float *)B.zz, \
+        (float *)B.xy, (float *)B.ry, (float *)B.py, (const float *)B.qy, (float *)B.zy, rhs_y, sc, part, part_rr,  \
+        pstride)
+#define GP2S_PCZ(MODE, MM)                                                                                          \
+    do {                                                                                                            \
+        if (bjz == 128) GP2S_PCZ_BJ(MODE, 128, MM);                                                                 \
+        else GP2S_PCZ_BJ(MODE, 64, MM);                                                                             \
+    } while (0)
+#define GP2S_PCY_BJ(MODE, BJ)                                                                                       \
+    k_pc_step<MODE, BJ><<<pgy, kPCThreads, pc_smem(0, BJ), c->stream>>>(                                           \
+        n, 0, nblky, 0, Minvy, (float *)B.xz, (float *)B.rz, (float *)B.pz, (const float *)B.qz, (float *)B.zz,    \
+        (float *)B.xy, (float *)B.ry, (float *)B.py, (const float *)B.qy, (float *)B.zy, rhs_y, sc, part, part_rr, \
+        pstride)
+#define GP2S_PCY(MODE)                                                                                              \
+    do {                                                                                                            \
+        if (bjy == 128) GP2S_PCY_BJ(MODE, 128);                                                                     \
+        else GP2S_PCY_BJ(MODE, 64);                                                                                 \
+    } while (0)
     // initial state: probe group then y column
     if (m > 0) {
-        if (pcz) GP2S_PC(PC_INIT, pgz, 0, m);
+        if (pcz) GP2S_PCZ(PC_INIT, m);
         else k_cg_init<T><<<nbz, ut, 0, c->stream>>>(n, m, rhs_y, (T *)B.xz, (T *)B.rz, (T *)B.pz, (T *)B.xy,
                                                       (T *)B.ry, (T *)B.py, part, pstride, nbz);
         GP2S_LAUNCH(c);
     }
-    if (pcy) GP2S_PC(PC_INIT, 0, pgy, 0);
+    if (pcy) GP2S_PCY(PC_INIT);
     else k_cg_init<T><<<nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, rhs_y, (T *)B.xz, (T *)B.rz, (T *)B.pz,
                                                   (T *)B.xy, (T *)B.ry, (T *)B.py, part, pstride, 0);
     GP2S_LAUNCH(c);
@@ -1468,7 +1539,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     for (; it < max_iter; ++it) {
         if (pc_avail && !pcz && mc > 0 && it == kmin_probe) {
             // the SLQ steps are recorded: restart the probe columns as PCG from their iterates
-            GP2S_PC(PC_RESTART, pgz, 0, mc);
+            GP2S_PCZ(PC_RESTART, mc);
             GP2S_LAUNCH(c);
             k_scal_restart<<<mc, 256, 0, c->stream>>>(part, pstride, pgz, sc, active);
             GP2S_LAUNCH(c);
@@ -1481,13 +1552,13 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         GP2S_LAUNCH(c);
         GP2S_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int) * 2, c->stream));
         if (mc > 0) {
-            if (pcz) GP2S_PC(PC_UPDATE, pgz, 0, mc);
+            if (pcz) GP2S_PCZ(PC_UPDATE, mc);
             else k_update<T><<<nbz, ut, 0, c->stream>>>(n, m, (T *)B.xz, (T *)B.rz, (const T *)B.pz, (const T *)B.qz,
                                                          (T *)B.xy, (T *)B.ry, (const T *)B.py, (const T *)B.qy, sc,
                                                          part, pstride, nbz);
             GP2S_LAUNCH(c);
         }
-        if (pcy) GP2S_PC(PC_UPDATE, 0, pgy, 0);
+        if (pcy) GP2S_PCY(PC_UPDATE);
         else k_update<T><<<nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, (T *)B.xz, (T *)B.rz, (const T *)B.pz,
                                                      (const T *)B.qz, (T *)B.xy, (T *)B.ry, (const T *)B.py,
                                                      (const T *)B.qy, sc, part, pstride, 0);
@@ -1507,7 +1578,10 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
                                                                  dgz);
             GP2S_LAUNCH(c);
         }
-#undef GP2S_PC
+#undef GP2S_PCZ
+#undef GP2S_PCZ_BJ
+#undef GP2S_PCY
+#undef GP2S_PCY_BJ
         if ((it + 1) % check_every == 0 || it + 1 == max_iter) {
             GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
             GP2S_CUDA(c, cudaStreamSynchronize(c->stream));

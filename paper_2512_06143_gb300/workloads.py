@@ -14,7 +14,7 @@ Workloads (the datasets of the paper are not available; these stand in for them)
   * ``clusters_3d``-- N = 1,000,000, d = 3, 50 Gaussian clusters (sigma 0.03, centers ~ U[0,1]^3)
                       clipped to [0,1]^3, y = sin(2 pi x1) + sin(4 pi x2 + 1) + sin(6 pi x3 + 2)
                       + N(0, 0.02^2), L = 8 bumps (radii 0.4), r tuned for ~100 entries per row,
-                      sigma^2 = 4e-4 (the generic synthetic data of App. B.7, at N = 1e6).
+                      sigma^2 = 4e-4 (the generic synthetic data of App. B.6, at N = 1e6).
   * ``batch``      -- 256 independent problems, N log-uniform in [2048, 65536], d in {1, 2, 3},
                       target entries per row log-uniform in [10, 200], X ~ U[0,1]^d, L = 4 bumps
                       (radii 0.4), y = the clusters_3d function on the first d coordinates,
