@@ -266,6 +266,8 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (bw && std::atoi(bw) > 0) c->batch_workers_max = std::atoi(bw);
     const char *lim = std::getenv("GP2S_MEM_LIMIT");
     if (lim) c->mem_limit = (size_t)std::strtoull(lim, nullptr, 10);
+    const char *gr = std::getenv("GP2S_GRAPHS");
+    if (gr && std::strcmp(gr, "0") == 0) c->use_graphs = false;
     *ctx = c;
     return GP2S_OK;
 }
@@ -287,6 +289,7 @@ void gp2s_destroy(gp2s_ctx *c)
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (gp2s_ctx *w : c->workers) gp2s_destroy(w);
     for (cudaStream_t s : c->worker_streams) cudaStreamDestroy(s);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     if (c->hbuf.p) cudaFreeHost(c->hbuf.p);
     delete c;
 }

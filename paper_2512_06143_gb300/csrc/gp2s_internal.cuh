@@ -107,6 +107,8 @@ struct gp2s_ctx {
     int bj_size_y = 64;             // rows per block of the y column (64 or 128)
     double bj_logdet = 0.0;
     bool probes_for_grad = false;   // the probe solves feed the Hutchinson gradient
+    bool use_graphs = true;         // replay runs of CG iterations as CUDA graphs (GP2S_GRAPHS=0: off)
+    cudaStream_t capture_stream = nullptr;   // private stream the graphs are captured on
     // batched form: worker contexts (own stream and workspace each), created on first use
     std::vector<gp2s_ctx *> workers;
     std::vector<cudaStream_t> worker_streams;

@@ -1436,6 +1436,74 @@ gp2s_status build_rb8(gp2s_ctx *c)
     return GP2S_OK;
 }
 
+// A captured run of CG iterations (CUDA graph) for one column set, with the work counters of
+// one replay so that the launch / SpMM accounting stays exact.
+struct GraphRun {
+    gp2s_ctx *c;
+    cudaGraphExec_t exec = nullptr;
+    int mc = -1;
+    bool pcz = false;
+    int64_t launches = 0, spmm_launches = 0;
+    double spmm_bytes = 0.0;
+    explicit GraphRun(gp2s_ctx *cc) : c(cc) {}
+    ~GraphRun() { if (exec) cudaGraphExecDestroy(exec); }
+    bool matches(int m_, bool p_) const { return exec && mc == m_ && pcz == p_; }
+    template <class F>
+    gp2s_status capture(int m_, bool p_, int iters, F &&body)
+    {
+        if (exec) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+        const int64_t l0 = c->launches, s0 = c->spmm_launches;
+        const double b0 = c->spmm_bytes;
+        // capture on the context's private stream (the caller's stream may be the legacy default
+        // stream, which cannot be captured); the graph is then launched on the caller's stream
+        if (!c->capture_stream) GP2S_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t user = c->stream;
+        c->stream = c->capture_stream;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            c->stream = user;
+            return cuda_err(c, e, "cudaStreamBeginCapture");
+        }
+        gp2s_status st = GP2S_OK;
+        for (int r = 0; r < iters && st == GP2S_OK; ++r) st = body();
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(c->stream, &g);
+        c->stream = user;
+        // nothing ran while capturing: take the counts back, and add them per replay
+        launches = c->launches - l0;
+        spmm_launches = c->spmm_launches - s0;
+        spmm_bytes = c->spmm_bytes - b0;
+        c->launches = l0;
+        c->spmm_launches = s0;
+        c->spmm_bytes = b0;
+        if (st != GP2S_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            exec = nullptr;
+            return cuda_err(c, e, "cudaGraphInstantiate");
+        }
+        mc = m_;
+        pcz = p_;
+        return GP2S_OK;
+    }
+    gp2s_status launch()
+    {
+        GP2S_CUDA(c, cudaGraphLaunch(exec, c->stream));
+        c->launches += launches;
+        c->spmm_launches += spmm_launches;
+        c->spmm_bytes += spmm_bytes;
+        return GP2S_OK;
+    }
+};
+
 // One CG run (x0 = 0) on columns [y | probes]; the probe right-hand sides must already be in rz.
 template <class T, class V>
 gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const double *rhs_y, double tol_y,
@@ -1536,15 +1604,9 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     int it = 0;
     int *hcount = reinterpret_cast<int *>(c->hbuf.p);
     int mc = m;          // probe columns still iterated; 0 once every probe column has stopped
-    for (; it < max_iter; ++it) {
-        if (pc_avail && !pcz && mc > 0 && it == kmin_probe) {
-            // the SLQ steps are recorded: restart the probe columns as PCG from their iterates
-            GP2S_PCZ(PC_RESTART, mc);
-            GP2S_LAUNCH(c);
-            k_scal_restart<<<mc, 256, 0, c->stream>>>(part, pstride, pgz, sc, active);
-            GP2S_LAUNCH(c);
-            pcz = true;
-        }
+    // one CG / PCG iteration on the active columns (every argument is fixed for given mc, pcz:
+    // the scalars live in device memory), so runs of iterations can be captured into a graph
+    auto one_iter = [&]() -> gp2s_status {
         const int kc = 1 + mc;
         int np = nb;
         GP2S_TRY((launch_spmm<T, V>(c, mc, true, val, B, part, pstride, nb, rsplit, active, &np)));
@@ -1578,18 +1640,43 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
                                                                  dgz);
             GP2S_LAUNCH(c);
         }
+        return GP2S_OK;
+    };
+    // Runs of check_every iterations between two convergence checks are captured once into a CUDA
+    // graph and replayed while the column set (mc, pcz) stays the same: one launch instead of
+    // about seven per iteration.  The first run (it allocates the per-launch scratch), the run
+    // holding the probes' PCG restart, a shortened last run and profiled calls go eagerly.
+    GraphRun gr(c);
+    while (it < max_iter) {
+        const int len = std::min(check_every, max_iter - it);
+        const bool restart_in_run = pc_avail && !pcz && mc > 0 && kmin_probe >= it && kmin_probe < it + len;
+        if (c->use_graphs && !c->profile && it > 0 && len == check_every && !restart_in_run) {
+            if (!gr.matches(mc, pcz)) GP2S_TRY(gr.capture(mc, pcz, check_every, one_iter));
+            GP2S_TRY(gr.launch());
+            it += len;
+        } else {
+            for (int r = 0; r < len; ++r, ++it) {
+                if (pc_avail && !pcz && mc > 0 && it == kmin_probe) {
+                    // the SLQ steps are recorded: restart the probe columns as PCG from their iterates
+                    GP2S_PCZ(PC_RESTART, mc);
+                    GP2S_LAUNCH(c);
+                    k_scal_restart<<<mc, 256, 0, c->stream>>>(part, pstride, pgz, sc, active);
+                    GP2S_LAUNCH(c);
+                    pcz = true;
+                }
+                GP2S_TRY(one_iter());
+            }
+        }
+        GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+        GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+        GP2S_TRY(flush_profile(c));
+        if (hcount[1] == 0) break;
+        if (mc > 0 && hcount[2] == 0) mc = 0;   // only the y column is left: y-only kernels
+    }
 #undef GP2S_PCZ
 #undef GP2S_PCZ_BJ
 #undef GP2S_PCY
 #undef GP2S_PCY_BJ
-        if ((it + 1) % check_every == 0 || it + 1 == max_iter) {
-            GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
-            GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
-            GP2S_TRY(flush_profile(c));
-            if (hcount[1] == 0) { ++it; break; }
-            if (mc > 0 && hcount[2] == 0) mc = 0;   // only the y column is left: y-only kernels
-        }
-    }
     // iteration counts per column group
     std::vector<double> hs((size_t)kScal * k);
     GP2S_CUDA(c, cudaMemcpyAsync(hs.data(), sc, sizeof(double) * kScal * k, cudaMemcpyDeviceToHost, c->stream));

@@ -263,6 +263,23 @@ def test_gradient_fp64_form_matches_oracle_hutchinson_tightly(gp, ctx):
     assert np.abs(g - gref).max() <= 1e-6 * np.abs(gref).max()
 
 
+def test_graph_replay_equals_eager_launches(gp, monkeypatch):
+    """Runs of CG iterations replayed as CUDA graphs give bit-identical results to launching every
+    kernel eagerly (the same kernels with the same arguments), and count the same launches."""
+    w = W.random_small(305, 6000, 3, L=3, sigma2=1e-3)
+    h = gp.Hyper(**w["hyper"])
+    X = torch.tensor(w["X"], device="cuda")
+    y = torch.tensor(w["y"], device="cuda")
+    opts = gp.default_opts(logdet=gp.LOGDET_SLQ, probes=64, lanczos_steps=50, seed=8)
+    monkeypatch.setenv("GP2S_GRAPHS", "1")
+    lml_g, g_g, info_g = gp.Context(0).lml_grad(X, y, h, opts)
+    monkeypatch.setenv("GP2S_GRAPHS", "0")
+    lml_e, g_e, info_e = gp.Context(0).lml_grad(X, y, h, opts)
+    assert lml_g == lml_e
+    assert np.array_equal(g_g, g_e)
+    assert info_g["iters_y"] == info_e["iters_y"] and info_g["launches"] == info_e["launches"]
+
+
 def test_autograd_function(gp, ctx):
     w = W.random_small(303, 3000, 2, L=2, sigma2=1e-3)
     h = gp.Hyper(**w["hyper"])
