@@ -102,8 +102,8 @@ typedef struct {
     int32_t max_outer;       /* refinement steps cap, default 8 */
     int32_t profile;         /* 1 = time every SpMM launch with CUDA events (gp2s_lml_info.ms_spmm); default 0 */
     int32_t bj_block;        /* rows per block-Jacobi block (precond = 2): 64, 128, or 0 =
-                                automatic (128 when A has at least 64 stored entries per row, else
-                                64); default 0 */
+                                automatic (128 when A has at least 64 stored entries per row and
+                                at least 768 rows per SM, else 64); default 0 */
     int32_t reserved;
 } gp2s_opts;
 

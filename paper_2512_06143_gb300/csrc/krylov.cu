@@ -1343,15 +1343,18 @@ size_t pc_smem(int m, int bj)
 }
 
 // Block size of the block-Jacobi preconditioner: opts.bj_block when set, else 128 rows for
-// matrices with at least 64 stored entries per row (there the larger blocks cut the iteration
-// count by about a fifth, which outweighs the dearer step), else 64 (with fewer entries per row
-// 64-row blocks already capture the neighbourhoods).  The probe columns and the y column can use
-// different sizes (two sets of factors); the automatic choice gives both the same.
+// matrices with at least 64 stored entries per row and enough rows to give every SM six blocks
+// (there the larger blocks cut the iteration count by about a fifth, which outweighs the dearer
+// step), else 64 (with fewer entries per row 64-row blocks already capture the neighbourhoods,
+// and a small problem needs the finer blocks to fill the GPU).  The probe columns and the y
+// column can use different sizes (two sets of factors); the automatic choice gives both the same.
 int bj_block_size(const gp2s_ctx *c)
 {
     const int req = c->A.opts.bj_block;
     if (req == 64 || req == 128) return req;
-    return c->A.nnz >= 64 * c->A.n ? 128 : 64;
+    const bool dense_rows = c->A.nnz >= 64 * c->A.n;
+    const bool many_rows = c->A.n >= (int64_t)128 * 6 * c->num_sms;
+    return dense_rows && many_rows ? 128 : 64;
 }
 
 // Build one set of block-Jacobi factors (FP64 blocks -> FP32 M^{-1}) with blocks of bj rows.
