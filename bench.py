@@ -53,6 +53,21 @@ def load_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def profile_traffic(workload: str, n: int):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of k_spmm_rb from the
+    committed ncu summary of this workload, if there is one: (bytes, file) or (None, None)."""
+    path = os.path.join(ROOT, "profiles", f"k_spmm_rb_{workload}_n{n // 1_000_000}m.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("| traffic per launch (read + write) |"):
+                    v = line.split("|")[2].strip().split()
+                    return float(v[0]) * {"GB": 1e9, "MB": 1e6}[v[1]], os.path.relpath(path, ROOT)
+    except OSError:
+        pass
+    return None, None
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
 
@@ -260,6 +275,7 @@ def run_gpu(args):
     peak, peak_src = load_peaks()
     achieved = (spmm_bytes / spmm_launches) / ((spmm_ms / spmm_launches) / 1000.0) / 1e9 if spmm_ms > 0 else None
     launches = int(sum(i["launches"] for i in infos))
+    traffic, traffic_src = profile_traffic(args.workload, int(n))
     if rank == 0:
         cpu_v, cores, sample, _ = oracle_sample(args.workload) if not args.no_cpu_baseline else (None, None, "skipped", 0)
         i0 = infos[-1]
@@ -274,7 +290,9 @@ def run_gpu(args):
                        "parallelism": f"replicas x{ws}"},
             "roofline": {"kernel": "k_spmm_rb (multi-RHS RB8 SpMM of the Krylov solves)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                         "traffic_source": traffic_src,
                          "peak_source": f"{peak_src} hbm_gbs",
                          "launches_per_step": spmm_launches / args.steps,
                          "bytes_per_launch": spmm_bytes / max(spmm_launches, 1),
