@@ -943,6 +943,14 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
                 }
             }
         }
+        if (seg_tiles == 1) {
+            // every tile is a segment of its own: its partial dots go straight to part
+#pragma unroll
+            for (int k = 0; k < K; ++k) part[(int64_t)(1 + lane * K + k) * pstride + (int64_t)t] = dz[k].value();
+            if (lane == 0) part[(int64_t)t] = HAS_Y ? dy.value() : 0.0;
+            t = __shfl_sync(0xffffffffu, tn, 0);
+            continue;
+        }
         // the tile's partial dots, then the segment count; the segment's last tile reduces it
         double *tp = tpart + (int64_t)t * (M + 1);
 #pragma unroll
@@ -1000,13 +1008,16 @@ size_t rb_smem()
 // Tiles of the RB8 SpMM: about 32 per warp of the grid (a warp's last tile is a small share of
 // its work, so the SMs finish together), and segments of seg_tiles tiles, at most kMaxPartBlocks
 // of them (the partial-dot stride).
+// A small matrix takes fewer CTAs (about eight row blocks per warp): the SMs it leaves free run
+// the other problems' kernels when many problems share the GPU on separate streams.
 struct RBTiles {
-    int tile_blocks, ntiles, seg_tiles, nseg;
+    int ctas, tile_blocks, ntiles, seg_tiles, nseg;
 };
 inline RBTiles rb_tiles(int64_t nblk, int nb)
 {
     RBTiles t;
-    const int64_t want = (int64_t)nb * RBCfg<1>::warps * 32;
+    t.ctas = (int)std::max<int64_t>(1, std::min<int64_t>(nb, ceil_div(nblk, (int64_t)RBCfg<1>::warps * 8)));
+    const int64_t want = (int64_t)t.ctas * RBCfg<1>::warps * 32;
     const int64_t tb = std::max<int64_t>(1, ceil_div(nblk, want));
     t.tile_blocks = (int)tb;
     t.ntiles = (int)ceil_div(nblk, tb);
@@ -1024,7 +1035,7 @@ gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride
     const RBTiles tl = rb_tiles(ceil_div(c->A.n, kRB), nb);
     GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (32 * K + 1)));
     RBWork *work = reinterpret_cast<RBWork *>(c->counters.as<char>() + kRBWorkOffset);
-    kern<<<nb, RBCfg<K>::threads, smem, c->stream>>>(c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
+    kern<<<tl.ctas, RBCfg<K>::threads, smem, c->stream>>>(c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
                                                      c->rb_val.as<float>(), c->A.n, (const float *)B.py,
                                                      (const float *)B.pz, (float *)B.qy, (float *)B.qz, part,
                                                      pstride, work, tl.tile_blocks, tl.ntiles,
