@@ -603,7 +603,22 @@ k_spmv_y(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, co
     for (int64_t i = w0; i < n; i += nw) {
         const int p1 = rowptr[i + 1];
         T s = T(0);
-        for (int p = rowptr[i] + lane; p < p1; p += kWarp) s += (T)val[p] * py[col[p]];
+        // four independent entries per lane in flight (rows of up to 128 entries in one pass)
+        for (int p = rowptr[i] + lane; p < p1; p += 4 * kWarp) {
+            V v[4];
+            int cj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = p + u * kWarp;
+                v[u] = q < p1 ? val[q] : V(0);
+                cj[u] = q < p1 ? col[q] : 0;
+            }
+            T g[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g[u] = py[cj[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s += (T)v[u] * g[u];
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
