@@ -1073,53 +1073,58 @@ gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride
 // ---------------------------------------------------------------------------------------------
 constexpr int kPCThreads = 256;
 
-// One CTA per block of BJ rows (BJ = 64 or 128): dense FP64 block from the CSR, Cholesky
-// L L^T, L^{-1} in place, then M^{-1} = L^{-T} L^{-1} (FP32, symmetric) and the block's log|M_b|.
-// Rows beyond n (last block) are padded with the identity.
+// One CTA per block of BJ rows (BJ = 64 or 128): the dense block of Ah (FP32 values) from the
+// CSR, Cholesky L L^T, L^{-1} in place, then M^{-1} = L^{-T} L^{-1} (symmetric bit for bit: both
+// triangles come from the same products in the same order) and the block's log|M_b|.  FP32 is
+// enough for a preconditioner (a block's condition number is bounded by about 1 / sigma^2 of the
+// Jacobi-scaled matrix) and runs on the full-rate FP32 pipes; rows beyond n (last block) are
+// padded with the identity.
 template <int BJ>
 __global__ void __launch_bounds__(kPCThreads)
-k_bj_build(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const double *__restrict__ val64,
+k_bj_build(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const float *__restrict__ val32,
            int64_t n, float *__restrict__ Minv32, double *__restrict__ logdet_blk,
            int *__restrict__ bad)
 {
-    extern __shared__ double bj_sh[];
-    double (*S)[BJ + 1] = reinterpret_cast<double (*)[BJ + 1]>(bj_sh);   // L, then L^{-1} (lower)
-    double *tmp = bj_sh + BJ * (BJ + 1);                                 // one column of L
+    extern __shared__ float bjf_sh[];
+    float (*S)[BJ + 1] = reinterpret_cast<float (*)[BJ + 1]>(bjf_sh);   // L, then L^{-1} (lower)
+    float *tmp = bjf_sh + BJ * (BJ + 1);                                // one column of L
     const int64_t b = blockIdx.x;
     const int64_t i0 = b * BJ;
     const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
     for (int t = threadIdx.x; t < BJ * BJ; t += blockDim.x) {
         int i = t / BJ, j = t % BJ;
-        S[i][j] = (i == j && i >= nb) ? 1.0 : 0.0;
+        S[i][j] = (i == j && i >= nb) ? 1.0f : 0.0f;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i = wid; i < nb; i += kPCThreads / kWarp) {
         for (int p = rowptr[i0 + i] + lane; p < rowptr[i0 + i + 1]; p += kWarp) {
             int64_t j = col[p] - i0;
-            if (j >= 0 && j < nb) S[i][j] = val64[p];
+            if (j >= 0 && j < nb) S[i][j] = val32[p];
         }
     }
     __syncthreads();
-    // right-looking Cholesky of the lower triangle
+    // right-looking Cholesky of the lower triangle; the trailing update visits only the
+    // (BJ - j - 1)^2 square below and right of the pivot
     for (int j = 0; j < BJ; ++j) {
         if (threadIdx.x == 0) {
-            double d = S[j][j];
-            if (!(d > 0.0)) { atomicOr(bad, 1); d = 1.0; }
-            S[j][j] = sqrt(d);
+            float d = S[j][j];
+            if (!(d > 0.0f)) { atomicOr(bad, 1); d = 1.0f; }
+            S[j][j] = sqrtf(d);
         }
         __syncthreads();
         for (int i = j + 1 + threadIdx.x; i < BJ; i += blockDim.x) S[i][j] /= S[j][j];
         __syncthreads();
-        for (int t = threadIdx.x; t < BJ * BJ; t += blockDim.x) {
-            int i = t / BJ, k = t % BJ;
-            if (i > j && k > j && k <= i) S[i][k] -= S[i][j] * S[k][j];
+        const int w = BJ - j - 1;
+        for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+            const int i = j + 1 + t / w, k = j + 1 + t % w;
+            if (k <= i) S[i][k] -= S[i][j] * S[k][j];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         double ld = 0.0;
-        for (int i = 0; i < nb; ++i) ld += log(S[i][i]);
+        for (int i = 0; i < nb; ++i) ld += log((double)S[i][i]);
         logdet_blk[b] = 2.0 * ld;
     }
     // V = L^{-1} in place, columns from the last to the first: V L = I gives V_jj = 1 / L_jj and
@@ -1128,22 +1133,22 @@ k_bj_build(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, 
     for (int j = BJ - 1; j >= 0; --j) {
         for (int k = j + threadIdx.x; k < BJ; k += blockDim.x) tmp[k] = S[k][j];
         __syncthreads();
-        const double ljj = tmp[j];
+        const float ljj = tmp[j];
         for (int i = j + 1 + threadIdx.x; i < BJ; i += blockDim.x) {
-            double s = 0.0;
-            for (int k = j + 1; k <= i; ++k) s += S[i][k] * tmp[k];
+            float s = 0.0f;
+            for (int k = j + 1; k <= i; ++k) s = fmaf(S[i][k], tmp[k], s);
             S[i][j] = -s / ljj;
         }
-        if (threadIdx.x == 0) S[j][j] = 1.0 / ljj;
+        if (threadIdx.x == 0) S[j][j] = 1.0f / ljj;
         __syncthreads();
     }
     float *Mb = Minv32 + b * BJ * BJ;
     for (int t = threadIdx.x; t < BJ * BJ; t += blockDim.x) {
         int i = t / BJ, j = t % BJ;
         // (L^{-T} L^{-1})_ij = sum_k V[k][i] V[k][j], k >= max(i, j)
-        double s = 0.0;
-        for (int k = i > j ? i : j; k < BJ; ++k) s += S[k][i] * S[k][j];
-        Mb[t] = (float)s;
+        float s = 0.0f;
+        for (int k = i > j ? i : j; k < BJ; ++k) s = fmaf(S[k][i], S[k][j], s);
+        Mb[t] = s;
     }
 }
 
@@ -1383,7 +1388,7 @@ int bj_block_size(const gp2s_ctx *c)
     return dense_rows && many_rows ? 128 : 64;
 }
 
-// Build one set of block-Jacobi factors (FP64 blocks -> FP32 M^{-1}) with blocks of bj rows.
+// Build one set of block-Jacobi factors (FP32 M^{-1}) with blocks of bj rows.
 static gp2s_status build_bj_set(gp2s_ctx *c, int bj, DevBuf &minv, double *logdet)
 {
     const int64_t n = c->A.n;
@@ -1393,16 +1398,16 @@ static gp2s_status build_bj_set(gp2s_ctx *c, int bj, DevBuf &minv, double *logde
     GP2S_TRY(ensure(c, c->counters, 256));
     int *bad = reinterpret_cast<int *>(c->counters.as<char>() + 208);
     GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-    const size_t smem = sizeof(double) * ((size_t)bj * (bj + 1) + bj);
+    const size_t smem = sizeof(float) * ((size_t)bj * (bj + 1) + bj);
     if (bj == 128) {
         GP2S_TRY(smem_attr(c, (const void *)k_bj_build<128>, smem));
         k_bj_build<128><<<(unsigned)nblk, kPCThreads, smem, c->stream>>>(
-            c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val64.as<double>(), n, minv.as<float>(),
+            c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val32.as<float>(), n, minv.as<float>(),
             c->bj_ld.as<double>(), bad);
     } else {
         GP2S_TRY(smem_attr(c, (const void *)k_bj_build<64>, smem));
         k_bj_build<64><<<(unsigned)nblk, kPCThreads, smem, c->stream>>>(
-            c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val64.as<double>(), n, minv.as<float>(),
+            c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val32.as<float>(), n, minv.as<float>(),
             c->bj_ld.as<double>(), bad);
     }
     GP2S_LAUNCH(c);
