@@ -178,6 +178,14 @@ def oracle_sample(workload: str, budget_s: float = 20.0):
 
 
 # ----------------------------------------------------------------------------------------------
+def reference_config(workload: str) -> dict:
+    """The GPU arm's workload description (same generator, sizes, probes and steps)."""
+    full = {"clusters_3d": dict(n=1_000_000, d=3, L=8, probes=64, lanczos_steps=100),
+            "sphere_4d": dict(n=10_000_000, d=4, L=8, probes=32, lanczos_steps=100),
+            "small_2d": dict(n=4096, d=2, L=4, probes=64, lanczos_steps=100)}.get(workload, {})
+    return {"workload": workload, **full, "precision": "fp64 oracle", "parallelism": "host cores"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -195,7 +203,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value if value > 0 else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload},
+            "config": reference_config(workload),
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
