@@ -1033,7 +1033,11 @@ inline RBTiles rb_tiles(int64_t nblk, int nb)
     RBTiles t;
     t.ctas = (int)std::max<int64_t>(1, std::min<int64_t>(nb, ceil_div(nblk, (int64_t)RBCfg<1>::warps * 8)));
     const int64_t want = (int64_t)t.ctas * RBCfg<1>::warps * 32;
-    const int64_t tb = std::max<int64_t>(1, ceil_div(nblk, want));
+    int64_t tb = std::max<int64_t>(1, ceil_div(nblk, want));
+    // a small matrix takes tiles large enough that every tile is its own segment (no segment
+    // counters, fences or second reduction pass), as long as every warp still gets a tile
+    const int64_t tb_one = ceil_div(nblk, kMaxPartBlocks);
+    if (ceil_div(nblk, tb_one) >= (int64_t)t.ctas * RBCfg<1>::warps) tb = std::max<int64_t>(tb, tb_one);
     t.tile_blocks = (int)tb;
     t.ntiles = (int)ceil_div(nblk, tb);
     t.seg_tiles = (int)ceil_div(t.ntiles, kMaxPartBlocks);
