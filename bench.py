@@ -132,6 +132,18 @@ def make_workload(name: str, seed: int, n: int | None = None):
     raise ValueError(name)
 
 
+def replica_throughput(ws: int, steps: int, total_ms: float, e2e_ms: float, device: str):
+    """Whole-job throughput of ws independent replicas: every rank evaluated `steps` problems; the
+    job's time is the slowest rank's (MAX all-reduce of the device-timed and end-to-end totals).
+    Returns (evals/s, e2e evals/s, max total ms, max e2e ms)."""
+    if ws > 1:
+        import torch
+        t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_ms = float(t[0]), float(t[1])
+    return ws * steps / (total_ms / 1000.0), ws * steps / (e2e_ms / 1000.0), total_ms, e2e_ms
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -270,12 +282,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     e2e_total = sum(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms, e2e_total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_total = float(t[0]), float(t[1])
-    value = ws * args.steps / (total_ms / 1000.0)
-    e2e_value = ws * args.steps / (e2e_total / 1000.0)
+    value, e2e_value, total_ms, e2e_total = replica_throughput(ws, args.steps, total_ms, e2e_total, "cuda")
     # roofline of the dominant kernel (SpMM of the Krylov solves)
     spmm_ms = sum(i["ms_spmm"] for i in infos)
     spmm_launches = sum(i["spmm_launches"] for i in infos)
