@@ -132,6 +132,25 @@ def make_workload(name: str, seed: int, n: int | None = None):
     raise ValueError(name)
 
 
+FP32_INSTR_PEAK = 152 * 128 * 2.07e9   # FP32 lanes x SMs x maximum SM clock (instructions/s)
+
+
+def assembly_roofline(n: int, d: int, L: int, nnz: int, ms: float, hbm_gbs: float) -> dict:
+    """Whole assembly (sort, cell list, count, scan, fill, FP64 values) against its algorithmic
+    roofline: memory leg = the CSR written once (8 B per stored entry + 4 B per row pointer);
+    compute leg = one support test (2d FP32 instructions) and one value (2d + 8 + L instructions,
+    a fused multiply-add counted once) per unique pair, (nnz + n) / 2 pairs, at the FP32 issue
+    rate of 152 SMs x 128 lanes x 2.07 GHz."""
+    mem = 8.0 * nnz + 4.0 * (n + 1)
+    instr = 0.5 * (nnz + n) * (2 * d + 2 * d + 8 + L)
+    t_mem, t_alu = mem / (hbm_gbs * 1e9), instr / FP32_INSTR_PEAK
+    roof_ms = 1000.0 * max(t_mem, t_alu)
+    return {"ms": ms, "gnnz_per_s": nnz / (ms * 1e6) if ms > 0 else None,
+            "roofline": {"bound": "hbm" if t_mem >= t_alu else "alu", "bytes": mem, "fp32_instr": instr,
+                         "roof_ms": roof_ms, "frac": roof_ms / ms if ms > 0 else None,
+                         "alu_peak_instr_per_s": FP32_INSTR_PEAK}}
+
+
 def replica_throughput(ws: int, steps: int, total_ms: float, e2e_ms: float, device: str):
     """Whole-job throughput of ws independent replicas: every rank evaluated `steps` problems; the
     job's time is the slowest rank's (MAX all-reduce of the device-timed and end-to-end totals).
@@ -315,8 +334,7 @@ def run_gpu(args):
                          "share_of_step": spmm_ms / total_ms if total_ms > 0 else None,
                          "bytes_definition": "8 B per stored entry (FP32 value + int32 column) + 4 B per row "
                                              "pointer + 4 B per input and per output vector element"},
-            "assembly": {"ms": i0["ms_assemble"], "gnnz_per_s": i0["nnz"] / (i0["ms_assemble"] * 1e6)
-                         if i0["ms_assemble"] > 0 else None},
+            "assembly": assembly_roofline(int(n), int(hyper.d), int(hyper.L), int(i0["nnz"]), i0["ms_assemble"], peak),
             "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": int(Xh.numel() * 8 + yh.numel() * 8),
                     "d2h_bytes_per_step": int(8 + 8 * hyper.nparams)},
