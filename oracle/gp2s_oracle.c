@@ -18,7 +18,7 @@
  * Krylov pieces (conjugate gradients, Lanczos) follow their textbook definitions; they are
  * used only where the paper leaves the log-determinant method open (Sec. 4.6, App. B.7).
  *
- * Readings taken where the paper is silent or garbled (each is listed in the design doc):
+ * Readings taken where the paper is silent or garbled:
  *   - "Wendland C2" = phi(t) = (1-t)^4 (4t+1) for d <= 3 and (1-t)^5 (5t+1) for d = 4;
  *     Eq. 3's own C6 form (1-t)^8 (32t^3+25t^2+8t+1) is kind 1.
  *   - bump support is s = |x-c|^2 / rho^2 < 1 (Eq. 7 prints "|x-c|^2 < r").

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI (gp2s_* in libgp2s.so).
 
-Tolerances (written here, derived in the design doc):
+Tolerances:
   * pattern: identical sets of (row, column) pairs (bit-exact, FP64 support test on both sides);
   * FP64 values: max |dA| <= 1e-12 max |A|;
   * FP32 values (MIXED): max |dA| <= 1e-6 max |A| and |dA|_F <= 1e-6 |A|_F;
