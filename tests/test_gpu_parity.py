@@ -184,6 +184,58 @@ def test_assembly_clusters_3d_full_size_sampled_rows(gp, ctx):
         assert np.abs(a32 - ov).max() <= 1e-6 * scale
 
 
+def test_assembly_sphere_4d_full_size_sampled_rows(gp, ctx):
+    """10M-point 4-D workload (599 M stored entries, the benchmark's largest configuration): GPU
+    rows vs oracle brute force over all 10M points on sampled rows; pattern bit-exact, values
+    within tolerance."""
+    import oracle
+    w = W.sphere_4d(0)
+    h = gp.Hyper(**w["hyper"])
+    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
+    info = ctx.assemble(X, h, gp.default_opts())
+    assert 55 < info["nnz"] / info["n"] < 65
+    c = ctx.csr()
+    rng = np.random.default_rng(2)
+    rows = rng.choice(info["n"], 24, replace=False)
+    perm = c["perm"].cpu().numpy().astype(np.int64)
+    iperm = np.empty_like(perm)
+    iperm[perm] = np.arange(len(perm))
+    sorted_rows = torch.tensor(iperm[rows], device="cuda")
+    rp = c["rowptr"]
+    ref = oracle.rows_brute(w["X"], oracle.Hyper(**w["hyper"]), rows)
+    s = c["dscale"]
+    for k, (oc, ov) in enumerate(ref):
+        i = int(sorted_rows[k])
+        b, e = int(rp[i]), int(rp[i + 1])
+        cs = c["col"][b:e].long()
+        pc = perm[cs.cpu().numpy()]
+        order = np.argsort(pc)
+        assert np.array_equal(pc[order], oc)
+        den = (s[i] * s[cs]).cpu().numpy()[order]
+        a64 = c["val64"][b:e].cpu().numpy()[order] / den
+        a32 = c["val32"][b:e].cpu().numpy().astype(np.float64)[order] / den
+        scale = max(np.abs(ov).max(), 1e-300)
+        assert np.abs(a64 - ov).max() <= 1e-12 * scale
+        assert np.abs(a32 - ov).max() <= 1e-6 * scale
+
+
+def test_solve_clusters_3d_full_size_sampled_residual_rows(gp, ctx):
+    """1M-point benchmark configuration, mixed precision with FP64 refinement: the residual
+    y - A a on sampled rows, with the rows of A from oracle brute force over all points, stays
+    within the 1e-8 relative bound of the whole residual (each |r_i| <= |r|)."""
+    import oracle
+    w = W.clusters_3d(0)
+    h = gp.Hyper(**w["hyper"])
+    ctx.assemble(torch.tensor(w["X"], device="cuda"), h, gp.default_opts())
+    a, info = ctx.solve(torch.tensor(w["y"], device="cuda"))
+    assert info["relres"] <= 1e-8
+    a = a.cpu().numpy()
+    rows = np.random.default_rng(3).choice(len(a), 64, replace=False)
+    ynorm = np.linalg.norm(w["y"])
+    for r, (oc, ov) in zip(rows, oracle.rows_brute(w["X"], oracle.Hyper(**w["hyper"]), rows)):
+        assert abs(w["y"][r] - float(ov @ a[oc])) <= 1e-8 * ynorm
+
+
 # ------------------------------------------------------------------------------------------------
 # Solve, log-determinant, LML, gradient
 # ------------------------------------------------------------------------------------------------
