@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
 // points per block step); blockDim.x is a multiple of L.
 template <int D>
 __global__ void __launch_bounds__(256)
-k_bump_grad(const double4 *__restrict__ X64, const float *__restrict__ H, int64_t n, KernelParams kp,
+k_bump_grad(const double4_16a *__restrict__ X64, const float *__restrict__ H, int64_t n, KernelParams kp,
             double *__restrict__ part)
 {
     const int L = kp.L;
@@ -198,7 +198,7 @@ k_bump_grad(const double4 *__restrict__ X64, const float *__restrict__ H, int64_
     for (int64_t i = (int64_t)blockIdx.x * R + threadIdx.x / L; i < n; i += (int64_t)gridDim.x * R) {
         const double h = (double)H[i * L + l];
         if (h == 0.0) continue;
-        const double4 xv = X64[i];
+        const double4_16a xv = X64[i];
         const double x[4] = {xv.x, xv.y, xv.z, xv.w};
         double q = 0.0;
 #pragma unroll
@@ -311,10 +311,10 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
         const int thr = L * (256 / L);
         size_t smem = sizeof(double) * (size_t)thr * (d + 2);
         switch (d) {
-        case 1: k_bump_grad<1><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4>(), c->H.as<float>(), n, A.kp, bpart); break;
-        case 2: k_bump_grad<2><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4>(), c->H.as<float>(), n, A.kp, bpart); break;
-        case 3: k_bump_grad<3><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4>(), c->H.as<float>(), n, A.kp, bpart); break;
-        default: k_bump_grad<4><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4>(), c->H.as<float>(), n, A.kp, bpart); break;
+        case 1: k_bump_grad<1><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4_16a>(), c->H.as<float>(), n, A.kp, bpart); break;
+        case 2: k_bump_grad<2><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4_16a>(), c->H.as<float>(), n, A.kp, bpart); break;
+        case 3: k_bump_grad<3><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4_16a>(), c->H.as<float>(), n, A.kp, bpart); break;
+        default: k_bump_grad<4><<<nbf, thr, smem, c->stream>>>(c->Xs64.as<double4_16a>(), c->H.as<float>(), n, A.kp, bpart); break;
         }
         GP2S_LAUNCH(c);
     }

@@ -27,7 +27,7 @@ constexpr int kChunk = 256;
 
 struct AsmArgs {
     const float4 *Xhi, *Xlo;
-    const double4 *X64;
+    const double4_16a *X64;
     const int4 *items;
     const int32_t *cell_start;
     const uint64_t *cell_key;
@@ -79,7 +79,7 @@ __device__ __forceinline__ float d2_f32(const float4 &hi_i, const float4 &lo_i, 
 
 // The exact pattern test: ((D0*D0 + D1*D1) + D2*D2) + ... < r*r, FP64, no fused multiply-add.
 template <int D>
-__device__ __forceinline__ bool exact_in(const double4 &a, const double4 &b, double r2)
+__device__ __forceinline__ bool exact_in(const double4_16a &a, const double4_16a &b, double r2)
 {
     const double xa[4] = {a.x, a.y, a.z, a.w}, xb[4] = {b.x, b.y, b.z, b.w};
     double q = 0.0;
@@ -271,13 +271,13 @@ size_t asm_smem_bytes(int D, bool fill, int L)
 // Bump tables (Eq. 7) in FP64 (+ an FP32 copy), the diagonal D_i = A_ii = (sum_l b_l^2 + w0)
 // + sigma^2 and the Jacobi scales s_i = D_i^{-1/2}.
 template <int D>
-__global__ void k_bumps(const double4 *__restrict__ X64, int64_t n, KernelParams kp,
+__global__ void k_bumps(const double4_16a *__restrict__ X64, int64_t n, KernelParams kp,
                         double *__restrict__ B64, float *__restrict__ B32, double *__restrict__ D64,
                         double *__restrict__ s64, float *__restrict__ s32, int *__restrict__ bad)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double4 xv = X64[i];
+        double4_16a xv = X64[i];
         const double x[4] = {xv.x, xv.y, xv.z, xv.w};
         double S = 0.0;
         for (int l = 0; l < kp.L; ++l) {
@@ -313,7 +313,7 @@ __global__ void k_bumps(const double4 *__restrict__ X64, int64_t n, KernelParams
 // FP64 values of Ah on the assembled pattern: one warp per row, lanes over the row's entries.
 template <int D>
 __global__ void __launch_bounds__(256)
-k_values64(const double4 *__restrict__ X64, const int32_t *__restrict__ rowptr,
+k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowptr,
            const int32_t *__restrict__ col, int64_t n, KernelParams kp, const double *__restrict__ B64,
            const double *__restrict__ s64, double *__restrict__ val64)
 {
@@ -322,7 +322,7 @@ k_values64(const double4 *__restrict__ X64, const int32_t *__restrict__ rowptr,
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int L = kp.L;
     for (int64_t i = warp0; i < n; i += nwarps) {
-        const double4 xi = X64[i];
+        const double4_16a xi = X64[i];
         const double si = s64[i];
         const int p0 = rowptr[i], p1 = rowptr[i + 1];
         for (int p = p0 + lane; p < p1; p += kWarp) {
@@ -331,7 +331,7 @@ k_values64(const double4 *__restrict__ X64, const int32_t *__restrict__ rowptr,
             if (j == i) {
                 v = 1.0;
             } else {
-                const double4 xj = X64[j];
+                const double4_16a xj = X64[j];
                 const double a[4] = {xi.x, xi.y, xi.z, xi.w}, b[4] = {xj.x, xj.y, xj.z, xj.w};
                 double q = 0.0;
 #pragma unroll
@@ -534,7 +534,7 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     GP2S_CUDA(c, cudaMemsetAsync(c->counters.p, 0, 256, c->stream));
     {
         unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
-        const double4 *x64 = c->Xs64.as<double4>();
+        const double4_16a *x64 = c->Xs64.as<double4_16a>();
         double *B64 = c->B64.as<double>();
         switch (d) {
         case 1: k_bumps<1><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
@@ -553,7 +553,7 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     std::memset(&a, 0, sizeof(a));
     a.Xhi = c->Xhi.as<float4>();
     a.Xlo = c->Xlo.as<float4>();
-    a.X64 = c->Xs64.as<double4>();
+    a.X64 = c->Xs64.as<double4_16a>();
     a.items = c->items.as<int4>();
     a.cell_start = c->cell_start.as<int32_t>();
     a.cell_key = cell_keys_ptr(c, ncells);
@@ -585,7 +585,7 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     // ---- FP64 values ----
     {
         unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 32);
-        const double4 *x64 = c->Xs64.as<double4>();
+        const double4_16a *x64 = c->Xs64.as<double4_16a>();
         const int32_t *rp = c->rowptr.as<int32_t>(), *cl = c->col.as<int32_t>();
         const double *B64 = c->B64.as<double>(), *s64 = c->s64.as<double>();
         double *v64 = c->val64.as<double>();

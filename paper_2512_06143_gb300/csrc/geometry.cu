@@ -99,7 +99,7 @@ __global__ void k_morton(const double *__restrict__ X, int64_t n, GridParams g,
 
 template <int D>
 __global__ void k_permute(const double *__restrict__ X, const int32_t *__restrict__ perm, int64_t n,
-                          double4 *__restrict__ Xs64, float4 *__restrict__ Xhi, float4 *__restrict__ Xlo,
+                          double4_16a *__restrict__ Xs64, float4 *__restrict__ Xhi, float4 *__restrict__ Xlo,
                           int32_t *__restrict__ iperm)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -114,7 +114,7 @@ __global__ void k_permute(const double *__restrict__ X, const int32_t *__restric
             h[k] = __double2float_rn(v[k]);
             l[k] = __double2float_rn(__dsub_rn(v[k], (double)h[k]));   // v - hi is exact in FP64
         }
-        Xs64[i] = make_double4(v[0], v[1], v[2], v[3]);
+        Xs64[i] = make_double4_16a(v[0], v[1], v[2], v[3]);
         Xhi[i] = make_float4(h[0], h[1], h[2], h[3]);
         Xlo[i] = make_float4(l[0], l[1], l[2], l[3]);
         iperm[o] = (int32_t)i;
@@ -215,7 +215,7 @@ gp2s_status geom_sort(gp2s_ctx *c, const double *X, int64_t n, const GridParams 
 
 gp2s_status geom_permute(gp2s_ctx *c, const double *X, int64_t n, int d)
 {
-    GP2S_TRY(ensure(c, c->Xs64, sizeof(double4) * n));
+    GP2S_TRY(ensure(c, c->Xs64, sizeof(double4_16a) * n));
     GP2S_TRY(ensure(c, c->Xhi, sizeof(float4) * n));
     GP2S_TRY(ensure(c, c->Xlo, sizeof(float4) * n));
     GP2S_TRY(ensure(c, c->iperm, sizeof(int32_t) * n));
@@ -223,7 +223,7 @@ gp2s_status geom_permute(gp2s_ctx *c, const double *X, int64_t n, int d)
     GP2S_CUDA(c, cudaMemcpyAsync(c->perm.p, c->idx.p, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
     unsigned gb = grid_for(n, 256);
     const int32_t *perm = c->perm.as<int32_t>();
-    double4 *x64 = c->Xs64.as<double4>();
+    double4_16a *x64 = c->Xs64.as<double4_16a>();
     float4 *hi = c->Xhi.as<float4>(), *lo = c->Xlo.as<float4>();
     int32_t *ip = c->iperm.as<int32_t>();
     switch (d) {
