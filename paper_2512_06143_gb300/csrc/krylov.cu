@@ -297,14 +297,18 @@ __global__ void k_scal_init(const double *__restrict__ part, const double *__res
         q[S_ALPHA] = 0.0;
         q[S_BETA] = 0.0;
         q[S_STEPS] = 0.0;
+        q[S_RR] = s2;
         active[c] = s > 0.0 ? 1 : 0;
     }
 }
 
-// alpha_c = rho_c / (p_c^T q_c); breakdown if p^T q <= 0 or NaN.
+// alpha_c = rho_c / (p_c^T q_c).  p^T q <= 0 (or NaN) is a breakdown, except when the column's
+// residual has already fallen to the rounding level of the vector precision (|r|^2 <= lucky
+// |b|^2): then the Krylov space is exhausted and the column simply stops, with the steps it has
+// recorded (a small problem, or an operator with few distinct eigenvalues).
 __global__ void k_scal_alpha(const double *__restrict__ part, int pstride, int nparts, double *__restrict__ sc,
                              int *__restrict__ active, int *__restrict__ flags, double *__restrict__ rec,
-                             int ksteps)
+                             int ksteps, double lucky)
 {
     const int c = blockIdx.x;
     double s = block_sum(part + (int64_t)c * pstride, nparts);
@@ -318,7 +322,7 @@ __global__ void k_scal_alpha(const double *__restrict__ part, int pstride, int n
         if (!(s > 0.0)) {
             active[c] = 0;
             q[S_ALPHA] = 0.0;
-            atomicOr(&flags[0], 1);   // breakdown
+            if (!(q[S_RR] <= lucky * q[S_B2])) atomicOr(&flags[0], 1);   // breakdown
             return;
         }
         double a = q[S_RHO] / s;
@@ -333,7 +337,7 @@ __global__ void k_scal_alpha(const double *__restrict__ part, int pstride, int n
 __global__ void k_scal_beta(const double *__restrict__ part, const double *__restrict__ part_rr, int pstride,
                             int nparts_y, int nparts_z, double *__restrict__ sc, int *__restrict__ active,
                             int *__restrict__ count, double *__restrict__ rec, int ksteps, int kmin_probe, int pc_y,
-                            int pc_z)
+                            int pc_z, double lucky)
 {
     const int c = blockIdx.x;
     const int np = c == 0 ? nparts_y : nparts_z;
@@ -356,7 +360,10 @@ __global__ void k_scal_beta(const double *__restrict__ part, const double *__res
         q[S_STEPS] = (double)(st + 1);
         bool conv = s2 <= q[S_TOL];
         int kmin = c == 0 ? 0 : kmin_probe;
-        if ((conv && st + 1 >= kmin) || !(s == s)) {
+        // a residual at the rounding level ends the column even before kmin steps: the steps after
+        // it would only record rounding noise as Lanczos coefficients
+        const bool exhausted = s2 <= lucky * q[S_B2];
+        if ((conv && st + 1 >= kmin) || exhausted || !(s == s)) {
             active[c] = 0;
             // p is not updated for inactive columns (beta unused)
         } else {
@@ -1638,6 +1645,8 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
                                           tol_z, pcy, pcz);
     GP2S_LAUNCH(c);
 
+    // squared relative residual at the rounding level of the vector precision
+    const double lucky = std::is_same<T, float>::value ? 1e-12 : 1e-26;
     const int check_every = 8;
     int it = 0;
     int *hcount = reinterpret_cast<int *>(c->hbuf.p);
@@ -1648,7 +1657,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         const int kc = 1 + mc;
         int np = nb;
         GP2S_TRY((launch_spmm<T, V>(c, mc, true, val, B, part, pstride, nb, rsplit, active, &np)));
-        k_scal_alpha<<<kc, 256, 0, c->stream>>>(part, pstride, np, sc, active, flags, rec, ksteps);
+        k_scal_alpha<<<kc, 256, 0, c->stream>>>(part, pstride, np, sc, active, flags, rec, ksteps, lucky);
         GP2S_LAUNCH(c);
         GP2S_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int) * 2, c->stream));
         if (mc > 0) {
@@ -1664,7 +1673,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
                                                      (const T *)B.qy, sc, part, pstride, 0);
         GP2S_LAUNCH(c);
         k_scal_beta<<<kc, 256, 0, c->stream>>>(part, part_rr, pstride, pcy ? pgy : nby, pcz ? pgz : nbz, sc, active,
-                                               flags + 1, rec, ksteps, kmin_probe, pcy, pcz);
+                                               flags + 1, rec, ksteps, kmin_probe, pcy, pcz, lucky);
         GP2S_LAUNCH(c);
         {
             // direction: p = z + beta p (z = M^{-1} r for a preconditioned group, z = r otherwise)

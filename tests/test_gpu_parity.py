@@ -317,6 +317,32 @@ def test_gradient_fp64_form_matches_oracle_hutchinson_tightly(gp, ctx):
     assert np.abs(g - gref).max() <= 1e-6 * np.abs(gref).max()
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_slq_when_the_krylov_space_is_exhausted(gp, ctx, precision):
+    """Degenerate SLQ cases: n = 40 points (fewer than the 100 Lanczos steps) and isolated points
+    (A diagonal, Ah = I).  The probe columns stop when their residual reaches the rounding level
+    instead of reporting a breakdown; the log-determinant matches the oracle with identical probes,
+    and for the diagonal case equals sum log A_ii exactly."""
+    import oracle
+    prec = gp.PREC_MIXED if precision == "mixed" else gp.PREC_FP64
+    opts = gp.default_opts(logdet=gp.LOGDET_SLQ, probes=32, lanczos_steps=100, seed=3, precision=prec)
+    w = W.random_small(440, 40, 2, L=2, sigma2=1e-2)
+    lml, g, info = ctx.lml_grad(w["X"], w["y"], gp.Hyper(**w["hyper"]), opts)
+    s = oracle.lml_slq(w["X"], w["y"], oracle.Hyper(**w["hyper"]), m=32, k=100, seed=3)
+    assert info["logdet"] == pytest.approx(s["logdet"], rel=1e-3)
+    assert np.abs(g - s["grad"]).max() <= 1e-6 * np.abs(s["grad"]).max()
+    rng = np.random.default_rng(7)
+    X = rng.random((500, 2))
+    y = np.sin(6 * X[:, 0])
+    hyper = dict(d=2, r=1e-6, sigma2=1e-2, centers=np.array([[0.5, 0.5]]), radii=np.array([2.0]),
+                 amps=np.array([1.0]), beta=1.0, w0=0.0, kind=0)
+    lml, g, info = ctx.lml_grad(X, y, gp.Hyper(**hyper), opts)
+    e = oracle.lml_exact(X, y, oracle.Hyper(**hyper))
+    assert info["nnz"] == 500
+    assert info["logdet"] == pytest.approx(e["logdet"], rel=1e-12)
+    assert lml == pytest.approx(e["lml"], rel=1e-10)
+
+
 def test_graph_replay_equals_eager_launches(gp, monkeypatch):
     """Runs of CG iterations replayed as CUDA graphs give bit-identical results to launching every
     kernel eagerly (the same kernels with the same arguments), and count the same launches."""
