@@ -42,7 +42,9 @@ typedef enum {
     GP2S_ENOMEM = 2,      /* device allocation failed (or exceeded GP2S_MEM_LIMIT bytes) */
     GP2S_ECUDA = 3,       /* a CUDA runtime call failed */
     GP2S_ENOCONV = 4,     /* a Krylov solve hit max_iter before its tolerance */
-    GP2S_EBREAKDOWN = 5,  /* CG breakdown: p^T A p <= 0 or NaN */
+    GP2S_EBREAKDOWN = 5,  /* CG breakdown: p^T A p <= 0 or NaN while the column's residual is still
+                             above the rounding level of its precision (a column whose residual has
+                             reached it just stops: its Krylov space is exhausted) */
     GP2S_ETIMEOUT = 6,    /* reserved: a bounded device-side wait gave up */
     GP2S_EOVERFLOW = 7,   /* nnz would exceed 2^31 - 1 (int32 column / row-pointer limit) */
     GP2S_ENOTPD = 8,      /* A not positive definite (zero diagonal, Cholesky pivot <= 0) */
