@@ -187,7 +187,7 @@ def oracle_sample(workload: str, budget_s: float = 20.0):
         gen = lambda n: W.clusters_3d(0, n=n, target_nnz=target)  # noqa: E731
     elif workload == "sphere_4d":
         full_n, target, m = 10_000_000, 60.0, 32
-        ns = 40000
+        ns = 70000
         gen = lambda n: W.sphere_4d(0, n=n, target_nnz=target)  # noqa: E731
     else:
         full_n, m = 4096, 64
