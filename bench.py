@@ -187,7 +187,7 @@ def oracle_sample(workload: str, budget_s: float = 20.0):
         gen = lambda n: W.clusters_3d(0, n=n, target_nnz=target)  # noqa: E731
     elif workload == "sphere_4d":
         full_n, target, m = 10_000_000, 60.0, 32
-        ns = 70000
+        ns = 150000
         gen = lambda n: W.sphere_4d(0, n=n, target_nnz=target)  # noqa: E731
     else:
         full_n, m = 4096, 64
@@ -203,7 +203,8 @@ def oracle_sample(workload: str, budget_s: float = 20.0):
         oracle.lml_slq(w["X"], w["y"], h, m=m, k=100, seed=0, tol=1e-8)
     t = time.perf_counter() - t0
     evals = (ns / full_n) / t
-    sample = (f"oracle LML+grad (brute-force assembly, FP64 CG to 1e-8, SLQ {m}x100, Hutchinson gradient) "
+    asm = "brute-force assembly" if ns <= 20000 else "k-d tree candidates + exact FP64 test"
+    sample = (f"oracle LML+grad ({asm}, FP64 CG to 1e-8, SLQ {m}x100, Hutchinson gradient) "
               f"on N={ns} points of the same generator, {t:.2f} s, scaled by N/{full_n}")
     return evals, oracle.num_threads(), sample, t
 
