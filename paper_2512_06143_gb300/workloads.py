@@ -191,3 +191,32 @@ def random_small(seed: int, n: int, d: int, L: int = 3, r: float | None = None, 
     hyp = _hyper(d, r, sigma2, rng.random((L, d)), rng.uniform(0.3, 0.6, L), rng.uniform(0.5, 1.5, L),
                  w0=w0, kind=kind)
     return dict(name=f"random_small[{seed}]", X=X, y=y, hyper=hyp)
+
+
+def perturbed_hypers(hyper: dict, count: int, seed: int) -> list:
+    """`count` hyperparameter sets drawn around `hyper` (inputs for gradient checks at random
+    theta): centers shifted by U(-0.1, 0.1) per coordinate, bump radii and amplitudes scaled by
+    log-uniform factors in [0.8, 1.25] and [0.5, 2], r by [0.9, 1.1] and sigma^2 by [0.5, 2]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    L, d = np.asarray(hyper["radii"]).shape[0], hyper["d"]
+
+    def lu(lo, hi, size=None):
+        return np.exp(rng.uniform(math.log(lo), math.log(hi), size))
+
+    for _ in range(count):
+        out.append(_hyper(d, hyper["r"] * lu(0.9, 1.1), hyper["sigma2"] * lu(0.5, 2.0),
+                          np.asarray(hyper["centers"]) + rng.uniform(-0.1, 0.1, (L, d)),
+                          np.asarray(hyper["radii"]) * lu(0.8, 1.25, L),
+                          np.asarray(hyper["amps"]) * lu(0.5, 2.0, L),
+                          beta=hyper["beta"], w0=hyper["w0"], kind=hyper["kind"]))
+    return out
+
+
+def checksums(X: np.ndarray, y: np.ndarray) -> list:
+    """Order-sensitive sums of the inputs, to confirm that another machine's generator produced
+    the same X and y (up to the last-bit differences of its math library)."""
+    X = np.asarray(X, np.float64)
+    y = np.asarray(y, np.float64)
+    wgt = np.linspace(1.0, 2.0, X.shape[0])
+    return [float(v) for v in np.concatenate([X.sum(0), (X * wgt[:, None]).sum(0), [y.sum(), (y * wgt).sum()]])]
