@@ -236,10 +236,164 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value if value > 0 else None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": reference_config(workload),
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "extrapolated": workload != "small_2d"},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": ("value and ms_per_step are extrapolated from the timed sample by N (the oracle never runs "
+                     "the full workload here), so ms_per_step exceeds the run's own wall time"
+                     if workload != "small_2d" else "the full workload, timed")}
     print(json.dumps(line), flush=True)
     return 0
+
+
+GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
+SAMPLE_CASES = {"clusters_3d": ("clusters_3d_150k_t0", 100.0), "sphere_4d": ("sphere_4d_150k", 60.0)}
+
+
+def timed_evals(ctx, X, y, hyper, opts, steps, warmup, flush, stream, barrier):
+    """warmup untimed evaluations, then `steps` evaluations bracketed by CUDA events on the
+    launching stream (L2 flushed before each).  Returns (per-step ms, infos)."""
+    for _ in range(warmup):
+        ctx.lml_grad(X, y, hyper, opts)
+    import torch
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos = []
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        _, _, info = ctx.lml_grad(X, y, hyper, opts)
+        ev[k][1].record(stream)
+        infos.append(info)
+    barrier()
+    return [a.elapsed_time(b) for a, b in ev], infos
+
+
+def e2e_evals(ctx, Xh, yh, hyper, opts, steps, flush):
+    """The same evaluation from pinned HOST buffers: the call copies X and y to the device and
+    returns the LML and gradient to the host; wall clock around each call."""
+    import torch
+    out = []
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.lml_grad(Xh, yh, hyper, opts)
+        torch.cuda.synchronize()
+        out.append(1000.0 * (time.perf_counter() - t0))
+    return out
+
+
+def spmm_roofline(gp, ctx, X, y, hyper, wopts, precision, flush, workload, n, peak, peak_src):
+    """One extra evaluation with opts.profile = 1 after the timed region: CUDA events around every
+    multi-RHS SpMM launch on the context's stream (graphs off for this pass only).  Gives the
+    dominant kernel's per-launch time, its algorithmic bytes and its share of the evaluation."""
+    flush.fill_(7)
+    _, _, info = ctx.lml_grad(X, y, hyper, gp.default_opts(precision=precision, profile=1, **wopts))
+    launches = max(int(info["spmm_launches"]), 1)
+    ms = info["ms_spmm"] / launches
+    nbytes = info["spmm_bytes"] / launches
+    achieved = nbytes / (ms / 1000.0) / 1e9 if ms > 0 else None
+    traffic, traffic_src = profile_traffic(workload, int(n))
+    return {"kernel": "k_spmm_rb (multi-RHS RB8 SpMM of the Krylov solves)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "traffic_source": traffic_src, "peak_source": f"{peak_src} hbm_gbs",
+            "launches_per_step": int(info["spmm_launches"]), "bytes_per_launch": nbytes, "ms_per_launch": ms,
+            "share_of_step": info["ms_spmm"] / info["ms_total"] if info["ms_total"] > 0 else None,
+            "timing": "CUDA events around each SpMM launch in one profiled evaluation after the timed region",
+            "bytes_definition": "8 B per stored entry (FP32 value + int32 column) + 4 B per row pointer + 4 B per "
+                                "input and per output vector element"}
+
+
+def measure_workload(gp, ctx, workload, seed, n, steps, warmup, flush, stream, barrier, peak, peak_src,
+                     sampler=None):
+    """Device-timed evaluations (production options), the end-to-end form from host buffers, and
+    the dominant kernel's roofline, for one workload."""
+    import torch
+    w, wopts = make_workload(workload, seed=seed, n=n)
+    hyper = gp.Hyper(**w["hyper"])
+    nn = w["X"].shape[0]
+    precision = gp.PREC_MIXED if workload != "small_2d" else gp.PREC_FP64
+    opts = gp.default_opts(precision=precision, **wopts)
+    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
+    y = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
+    Xh = torch.tensor(w["X"], dtype=torch.float64).pin_memory()
+    yh = torch.tensor(w["y"], dtype=torch.float64).pin_memory()
+    for _ in range(warmup):
+        ctx.lml_grad(X, y, hyper, opts)
+    if sampler is not None:
+        sampler.start()
+    step_ms, infos = timed_evals(ctx, X, y, hyper, opts, steps, 0, flush, stream, barrier)
+    clocks = sampler.stop() if sampler is not None else None
+    e2e_ms = e2e_evals(ctx, Xh, yh, hyper, opts, steps, flush)
+    roof = spmm_roofline(gp, ctx, X, y, hyper, wopts, precision, flush, workload, nn, peak, peak_src)
+    i0 = infos[-1]
+    return dict(w=w, hyper=hyper, opts=opts, wopts=wopts, precision=precision, X=X, y=y, n=int(nn),
+                step_ms=step_ms, infos=infos, e2e_ms=e2e_ms, roofline=roof, clocks=clocks,
+                h2d=int(Xh.numel() * 8 + yh.numel() * 8), d2h=int(8 + 8 * hyper.nparams),
+                config={"workload": workload, "n": int(nn), "d": int(hyper.d), "L": hyper.L, "nnz": int(i0["nnz"]),
+                        "probes": int(opts.probes), "lanczos_steps": int(opts.lanczos_steps),
+                        "precision": "mixed" if precision == gp.PREC_MIXED else "fp64",
+                        "l2": "flushed (256 MB write) between steps"},
+                detail={"ms_assemble": i0["ms_assemble"], "ms_solve": i0["ms_solve"], "ms_logdet": i0["ms_logdet"],
+                        "ms_grad": i0["ms_grad"], "iters_y": i0["iters_y"], "iters_probes": i0["iters_probes"],
+                        "outer": i0["outer"], "relres": i0["relres"], "lml": i0["lml"],
+                        "logdet_stderr": i0["logdet_stderr"], "bj_block": i0["bj_block"],
+                        "spmm_seg_tiles": i0["spmm_seg_tiles"], "step_ms": step_ms})
+
+
+def oracle_errors(gp, ctx, m: dict) -> dict:
+    """Part of the oracle leg (after every timed region): each result's error against the FP64
+    oracle.  (1) The full-size y solve: |y_i - A_i a| on sampled rows, the rows of A from the
+    oracle's brute force over all points, against |y|.  (2) The log-determinant, quadratic term,
+    LML and gradient on a 150,000-point sample of the same generator against the oracle's results
+    stored in tests/golden (written by tests/golden/make_oracle_large.py, which calls only the
+    oracle), with the bench's own default options."""
+    import oracle
+    from paper_2512_06143_gb300 import workloads as W
+    out = {}
+    w, hyper = m["w"], m["hyper"]
+    ctx.assemble(m["X"], hyper, m["opts"])
+    a, sinfo = ctx.solve(m["y"])
+    a = a.cpu().numpy()
+    rows = np.random.default_rng(3).choice(m["n"], 16, replace=False)
+    ynorm = float(np.linalg.norm(w["y"]))
+    worst = 0.0
+    for r, (oc, ov) in zip(rows, oracle.rows_brute(w["X"], oracle.Hyper(**w["hyper"]), rows)):
+        worst = max(worst, abs(w["y"][r] - float(ov @ a[oc])) / ynorm)
+    out["y_residual"] = {"relres_fp64": sinfo["relres"], "max_sampled_row_residual_over_ynorm": worst,
+                         "rows": len(rows), "bound": 1e-8}
+    case = SAMPLE_CASES.get(m["config"]["workload"])
+    if case is None:
+        return out
+    path = os.path.join(GOLDEN_DIR, f"oracle_{case[0]}.json")
+    try:
+        with open(path) as f:
+            ref = json.load(f)
+    except OSError:
+        out["sample"] = {"skipped": f"{os.path.relpath(path, ROOT)} missing"}
+        return out
+    gen = {"clusters_3d": W.clusters_3d, "sphere_4d": W.sphere_4d}[ref["workload"]]
+    ws = gen(0, n=ref["n"], target_nnz=ref["target"])
+    if not np.allclose(W.checksums(ws["X"], ws["y"]), ref["checksums"], rtol=1e-10, atol=0.0):
+        out["sample"] = {"skipped": "this machine's generator gave other inputs than the stored case"}
+        return out
+    hs = gp.Hyper(**ref["hyper"])
+    opts = gp.default_opts(precision=gp.PREC_MIXED, probes=ref["probes"], lanczos_steps=ref["steps"],
+                           seed=ref["seed"])
+    lml, g, info = ctx.lml_grad(ws["X"], ws["y"], hs, opts)
+    gref = np.asarray(ref["grad"])
+    out["sample"] = {"case": ref["case"], "n": ref["n"], "nnz": int(info["nnz"]), "oracle_nnz": ref["nnz"],
+                     "logdet_rel_err": abs(info["logdet"] - ref["logdet"]) / abs(ref["logdet"]),
+                     "quad_rel_err": abs(info["quad"] - ref["quad"]) / abs(ref["quad"]),
+                     "lml_abs_err": abs(lml - ref["lml"]),
+                     "lml_bar": 0.5e-3 * abs(ref["logdet"]) + 0.5e-7 * abs(ref["quad"]),
+                     "grad_max_err_over_max_abs": float(np.abs(g - gref).max() / np.abs(gref).max()),
+                     "bj_block": info["bj_block"], "spmm_seg_tiles": info["spmm_seg_tiles"],
+                     "bars": {"logdet": 1e-3, "quad": 1e-7, "grad": 1e-4},
+                     "probes": "identical Rademacher probes on both sides"}
+    return out
 
 
 def run_gpu(args):
@@ -255,95 +409,68 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     build.build()
     gp.load()
-    w, wopts = make_workload(args.workload, seed=rank, n=args.n)
-    hyper = gp.Hyper(**w["hyper"])
-    n = w["X"].shape[0]
-    precision = gp.PREC_MIXED if args.workload != "small_2d" else gp.PREC_FP64
-    opts = gp.default_opts(precision=precision, **wopts)
-    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
-    y = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
-    Xh = torch.tensor(w["X"], dtype=torch.float64).pin_memory()
-    yh = torch.tensor(w["y"], dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream()
     ctx = gp.Context(local, stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # 256 MB > 129 MB L2
+    peak, peak_src = load_peaks()
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        ctx.lml_grad(X, y, hyper, opts)
-    # --- timed region: device-resident inputs -------------------------------------------------
-    prof_opts = gp.default_opts(precision=precision, profile=1, **wopts)
-    sampler = ClockSampler(local)
-    sampler.start()
-    barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    infos = []
-    for k in range(args.steps):
-        flush.fill_(k & 0xff)
-        ev[k][0].record(stream)
-        lml, g, info = ctx.lml_grad(X, y, hyper, prof_opts)
-        ev[k][1].record(stream)
-        infos.append(info)
-    barrier()
-    clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    # --- e2e: host buffers, H2D of X and y and D2H of the LML and gradient inside the call ------
-    e2e_ms = []
-    for k in range(args.steps):
-        flush.fill_(k & 0xff)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.lml_grad(Xh, yh, hyper, opts)
-        torch.cuda.synchronize()
-        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    e2e_total = sum(e2e_ms)
+    main_m = measure_workload(gp, ctx, args.workload, rank, args.n, args.steps, args.warmup, flush, stream, barrier,
+                              peak, peak_src, sampler=ClockSampler(local))
+    total_ms = sum(main_m["step_ms"])
+    e2e_total = sum(main_m["e2e_ms"])
     value, e2e_value, total_ms, e2e_total = replica_throughput(ws, args.steps, total_ms, e2e_total, "cuda")
-    # roofline of the dominant kernel (SpMM of the Krylov solves)
-    spmm_ms = sum(i["ms_spmm"] for i in infos)
-    spmm_launches = sum(i["spmm_launches"] for i in infos)
-    spmm_bytes = sum(i["spmm_bytes"] for i in infos)
-    peak, peak_src = load_peaks()
-    achieved = (spmm_bytes / spmm_launches) / ((spmm_ms / spmm_launches) / 1000.0) / 1e9 if spmm_ms > 0 else None
+    infos = main_m["infos"]
     launches = int(sum(i["launches"] for i in infos))
-    traffic, traffic_src = profile_traffic(args.workload, int(n))
+    secondary = {}
+    if ws == 1 and args.workload == "clusters_3d" and args.n is None and not args.no_secondary:
+        # the metric's second size (N = 10M, d = 4) and the batched form, each measured the same way
+        ctx2 = gp.Context(local, stream.cuda_stream)
+        m2 = measure_workload(gp, ctx2, "sphere_4d", 0, None, 2, 1, flush, stream, barrier, peak, peak_src,
+                              sampler=ClockSampler(local))
+        t2 = sum(m2["step_ms"])
+        secondary["sphere_4d"] = {
+            "metric": METRIC, "value": 2 / (t2 / 1000.0), "unit": "evals/s", "steps": 2, "warmup": 1,
+            "ms_per_step": t2 / 2, "config": m2["config"], "roofline": m2["roofline"], "clocks": m2["clocks"],
+            "e2e": {"value": 2 / (sum(m2["e2e_ms"]) / 1000.0), "unit": "evals/s", "h2d_bytes_per_step": m2["h2d"],
+                    "d2h_bytes_per_step": m2["d2h"]},
+            "assembly": assembly_roofline(m2["n"], int(m2["hyper"].d), int(m2["hyper"].L),
+                                          int(m2["infos"][-1]["nnz"]), m2["infos"][-1]["ms_assemble"], peak),
+            "gpu_launches": int(sum(i["launches"] for i in m2["infos"])), "detail": m2["detail"]}
+        secondary["batch"] = batch_record(gp, torch, local, steps=1, warmup=1)
     if rank == 0:
-        cpu_v, cores, sample, _ = oracle_sample(args.workload) if not args.no_cpu_baseline else (None, None, "skipped", 0)
         i0 = infos[-1]
+        errors = None
+        if not args.no_cpu_baseline:
+            cpu_v, cores, sample, _ = oracle_sample(args.workload)
+            errors = {args.workload: oracle_errors(gp, ctx, main_m)}
+            if "sphere_4d" in secondary:
+                m2["config"]["workload"] = "sphere_4d"
+                errors["sphere_4d"] = oracle_errors(gp, ctx2, m2)
+        else:
+            cpu_v, cores, sample = None, None, "skipped"
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if precision == gp.PREC_MIXED else "f64",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "n": int(n), "d": int(hyper.d), "L": hyper.L,
-                       "nnz": int(i0["nnz"]), "probes": int(opts.probes), "lanczos_steps": int(opts.lanczos_steps),
-                       "precision": "mixed" if precision == gp.PREC_MIXED else "fp64", "l2": "flushed (256 MB write) between steps",
-                       "parallelism": f"replicas x{ws}"},
-            "roofline": {"kernel": "k_spmm_rb (multi-RHS RB8 SpMM of the Krylov solves)", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                         "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                         "traffic_source": traffic_src,
-                         "peak_source": f"{peak_src} hbm_gbs",
-                         "launches_per_step": spmm_launches / args.steps,
-                         "bytes_per_launch": spmm_bytes / max(spmm_launches, 1),
-                         "ms_per_launch": spmm_ms / max(spmm_launches, 1),
-                         "share_of_step": spmm_ms / total_ms if total_ms > 0 else None,
-                         "bytes_definition": "8 B per stored entry (FP32 value + int32 column) + 4 B per row "
-                                             "pointer + 4 B per input and per output vector element"},
-            "assembly": assembly_roofline(int(n), int(hyper.d), int(hyper.L), int(i0["nnz"]), i0["ms_assemble"], peak),
-            "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": int(Xh.numel() * 8 + yh.numel() * 8),
-                    "d2h_bytes_per_step": int(8 + 8 * hyper.nparams)},
-            "clocks": clocks, "gpu_launches": launches,
-            "detail": {"ms_assemble": i0["ms_assemble"], "ms_solve": i0["ms_solve"], "ms_logdet": i0["ms_logdet"],
-                       "ms_grad": i0["ms_grad"], "iters_y": i0["iters_y"], "iters_probes": i0["iters_probes"],
-                       "outer": i0["outer"], "relres": i0["relres"], "lml": i0["lml"],
-                       "logdet_stderr": i0["logdet_stderr"], "step_ms": step_ms},
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if main_m["precision"] == gp.PREC_MIXED else "f64", "data": "synthetic",
+            "config": {**main_m["config"], "parallelism": f"replicas x{ws}",
+                       "options": "production defaults (CUDA graphs on, no per-launch events)"},
+            "roofline": main_m["roofline"],
+            "assembly": assembly_roofline(main_m["n"], int(main_m["hyper"].d), int(main_m["hyper"].L),
+                                          int(i0["nnz"]), i0["ms_assemble"], peak),
+            "cpu_baseline": {"value": cpu_v, "unit": "evals/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "extrapolated": True},
+            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": main_m["h2d"],
+                    "d2h_bytes_per_step": main_m["d2h"]},
+            "clocks": main_m["clocks"], "gpu_launches": launches,
+            "errors": errors,
+            "secondary": secondary or None,
+            "detail": main_m["detail"],
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -359,6 +486,8 @@ def main():
     ap.add_argument("--impl", default="gp2s", choices=["gp2s", "reference"])
     ap.add_argument("--workload", default="clusters_3d", choices=["clusters_3d", "sphere_4d", "small_2d", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the N = 10M sphere_4d and batched records of the default run")
     ap.add_argument("--n", type=int, default=None,
                     help="points per problem (default: the workload's full size); smaller n = profiling case")
     args = ap.parse_args()
@@ -369,62 +498,77 @@ def main():
     return run_gpu(args)
 
 
-def run_batch(args):
+def batch_record(gp, torch, local, steps=1, warmup=1, seed=0) -> dict:
     """256 independent problems (N log-uniform in [2048, 65536], d in {1,2,3}, 10-200 entries per
-    row), one gp2s_lml_batched call per step (SLQ, 32 probes x 100 steps): mixed precision timed,
-    and the plain FP64 GPU form timed once beside it with the accuracy of both against each other."""
-    import torch
-
-    import paper_2512_06143_gb300 as gp
-    from paper_2512_06143_gb300 import build
+    row), one gp2s_lml_batched call per step (SLQ, 32 probes x 100 steps): the mixed-precision form
+    timed with inputs on the device and from host buffers, and the plain FP64 GPU form timed once
+    beside it, with the accuracy of the two against each other."""
     from paper_2512_06143_gb300 import workloads as W
-
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    build.build()
-    gp.load()
-    probs = []
-    for w in W.batch(rank):
-        probs.append((torch.tensor(w["X"], device="cuda"), torch.tensor(w["y"], device="cuda"),
-                      gp.Hyper(**w["hyper"])))
+    ws_ = W.batch(seed)
+    probs = [(torch.tensor(w["X"], device="cuda"), torch.tensor(w["y"], device="cuda"), gp.Hyper(**w["hyper"]))
+             for w in ws_]
+    host = [(w["X"], w["y"], gp.Hyper(**w["hyper"])) for w in ws_]
     ctx = gp.Context(local, torch.cuda.current_stream().cuda_stream)
     mixed = gp.default_opts(precision=gp.PREC_MIXED, logdet=gp.LOGDET_SLQ, probes=32, lanczos_steps=100)
     fp64 = gp.default_opts(precision=gp.PREC_FP64, logdet=gp.LOGDET_SLQ, probes=32, lanczos_steps=100, precond=1)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.lml_batched(probs, mixed)
+    stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
         lm, infos = ctx.lml_batched(probs, mixed)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_mixed = (time.perf_counter() - t0) / args.steps
+    t_mixed = e0.elapsed_time(e1) / 1000.0 / steps
+    t0 = time.perf_counter()
+    ctx.lml_batched(host, mixed)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
     ctx.lml_batched(probs, fp64)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e0.record(stream)
     l64, i64 = ctx.lml_batched(probs, fp64)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t_fp64 = time.perf_counter() - t0
+    t_fp64 = e0.elapsed_time(e1) / 1000.0
     lm, l64 = np.asarray(lm), np.asarray(l64)
-    rel = float(np.max(np.abs(lm - l64) / np.abs(l64)))
     ld_m = np.array([i["logdet"] for i in infos])
     ld_64 = np.array([i["logdet"] for i in i64])
     q_m = np.array([i["quad"] for i in infos])
     q_64 = np.array([i["quad"] for i in i64])
     se = np.array([i["logdet_stderr"] for i in i64])
-    ld_se = float(np.median(se / np.abs(ld_64)))
-    line = {"metric": "batched LML evals/s", "value": len(probs) / t_mixed, "unit": "evals/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_mixed, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "batch", "problems": len(probs), "n_total": int(sum(p[0].shape[0] for p in probs)),
-                       "probes": 32, "lanczos_steps": 100},
+    return {"metric": "batched LML evals/s", "value": len(probs) / t_mixed, "unit": "evals/s", "steps": steps,
+            "warmup": warmup, "ms_per_step": 1000.0 * t_mixed, "higher_is_better": True,
+            "config": {"workload": "batch", "problems": len(probs),
+                       "n_total": int(sum(p[0].shape[0] for p in probs)), "probes": 32, "lanczos_steps": 100},
+            "e2e": {"value": len(probs) / t_e2e, "unit": "evals/s",
+                    "h2d_bytes_per_step": int(sum(w["X"].nbytes + w["y"].nbytes for w in ws_)),
+                    "d2h_bytes_per_step": 8 * len(probs)},
             "fp64_form": {"evals_per_s": len(probs) / t_fp64, "s_per_batch": t_fp64,
                           "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
-                          "max_rel_lml_diff_mixed_vs_fp64": rel,
+                          "max_rel_lml_diff_mixed_vs_fp64": float(np.max(np.abs(lm - l64) / np.abs(l64))),
                           "max_rel_logdet_diff_mixed_vs_fp64": float(np.max(np.abs(ld_m - ld_64) / np.abs(ld_64))),
                           "max_rel_quad_diff_mixed_vs_fp64": float(np.max(np.abs(q_m - q_64) / np.abs(q_64))),
                           "max_logdet_diff_in_fp64_stderr": float(np.max(np.abs(ld_m - ld_64) / se)),
-                          "median_rel_logdet_stderr": ld_se},
-            "timing": "host wall clock around each batched call (includes its stream synchronisation)"}
+                          "median_rel_logdet_stderr": float(np.median(se / np.abs(ld_64)))},
+            "timing": "CUDA events on the calling stream around the batched calls (each call ends with its "
+                      "stream synchronisation); e2e: host wall clock, inputs in host memory"}
+
+
+def run_batch(args):
+    import torch
+
+    import paper_2512_06143_gb300 as gp
+    from paper_2512_06143_gb300 import build
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    gp.load()
+    rec = batch_record(gp, torch, local, steps=args.steps, warmup=args.warmup, seed=rank)
+    line = {**rec, "n_gpus": 1, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
 

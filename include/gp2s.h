@@ -149,6 +149,9 @@ typedef struct {
                                 pointers + each input and output vector element once */
     float ms_spmm;           /* summed CUDA-event time of those launches (opts.profile = 1) */
     float reserved_f;
+    int32_t bj_block;        /* rows per block-Jacobi block of the probe columns (0: no block-Jacobi) */
+    int32_t spmm_seg_tiles;  /* largest number of row-block tiles per reduction segment in the
+                                multi-RHS SpMM launches (1: every tile is its own segment) */
 } gp2s_lml_info;
 
 typedef struct gp2s_ctx gp2s_ctx;
@@ -268,7 +271,8 @@ gp2s_status gp2s_lml_batched(gp2s_ctx *ctx, int32_t B, const int64_t *n, const d
  *   hyper: host, as for gp2s_lml.
  *   out_dev: DEVICE pointer to 3 doubles receiving {LML, y^T A^{-1} y, log|A|}; NaN if a Cholesky
  *   pivot is not positive.
- *   cuda_stream: the stream all work is issued on (NULL = legacy default stream).
+ *   cuda_stream: the stream all work is issued on (NULL = legacy default stream).  It must belong
+ *   to the calling thread's current device: a stream of another device returns GP2S_EINVAL.
  * The call is asynchronous: it returns after queueing the work on cuda_stream.  The first call on
  * each device looks up the scratch array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture begins.  Every call on a device shares

@@ -75,7 +75,8 @@ class LmlInfo(ctypes.Structure):
                 ("outer", ctypes.c_int32), ("logdet_method", ctypes.c_int32), ("ms_assemble", ctypes.c_float),
                 ("ms_solve", ctypes.c_float), ("ms_logdet", ctypes.c_float), ("ms_grad", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("launches", ctypes.c_int64), ("spmm_launches", ctypes.c_int64),
-                ("spmm_bytes", ctypes.c_double), ("ms_spmm", ctypes.c_float), ("reserved_f", ctypes.c_float)]
+                ("spmm_bytes", ctypes.c_double), ("ms_spmm", ctypes.c_float), ("reserved_f", ctypes.c_float),
+                ("bj_block", ctypes.c_int32), ("spmm_seg_tiles", ctypes.c_int32)]
 
 
 class CsrView(ctypes.Structure):

@@ -416,6 +416,7 @@ static gp2s_status lml_impl(gp2s_ctx *c, int64_t n, const double *X, const doubl
     c->launches = 0;
     c->spmm_launches = 0;
     c->spmm_bytes = 0.0;
+    c->spmm_seg_tiles = 0;
     c->prof_ms = 0.0;
     c->prof_used = 0;
     c->profile = o->profile != 0;
@@ -473,6 +474,8 @@ static gp2s_status lml_impl(gp2s_ctx *c, int64_t n, const double *X, const doubl
         info->spmm_launches = c->spmm_launches;
         info->spmm_bytes = c->spmm_bytes;
         info->ms_spmm = (float)c->prof_ms;
+        info->bj_block = (A.precision == GP2S_PREC_MIXED && A.opts.precond == 2 && c->bj_valid) ? c->bj_size : 0;
+        info->spmm_seg_tiles = c->spmm_seg_tiles;
     }
     c->profile = false;
     return GP2S_OK;

@@ -133,6 +133,7 @@ struct gp2s_ctx {
     int64_t launches = 0;
     int64_t spmm_launches = 0;
     double spmm_bytes = 0.0;
+    int spmm_seg_tiles = 0;   // largest tiles-per-segment of this call's multi-RHS SpMM launches
     bool profile = false;
     std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop) per profiled SpMM launch
     size_t prof_used = 0;

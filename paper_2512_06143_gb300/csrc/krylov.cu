@@ -103,6 +103,18 @@ __device__ __forceinline__ void load_k(const T *__restrict__ p, T (&v)[K])
     } else if constexpr (sizeof(T) == 8 && K == 4) {
         double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
         v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+    } else if constexpr (sizeof(T) == 4 && K % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k += 4) {
+            float4 t = reinterpret_cast<const float4 *>(p)[k / 4];
+            v[k] = t.x; v[k + 1] = t.y; v[k + 2] = t.z; v[k + 3] = t.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k += 2) {
+            float2 t = reinterpret_cast<const float2 *>(p)[k / 2];
+            v[k] = t.x; v[k + 1] = t.y;
+        }
     } else {
 #pragma unroll
         for (int k = 0; k < K; ++k) v[k] = p[k];
@@ -120,6 +132,13 @@ __device__ __forceinline__ void store_k(T *__restrict__ p, const T (&v)[K])
     } else if constexpr (sizeof(T) == 8 && K == 4) {
         reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
         reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    } else if constexpr (sizeof(T) == 4 && K % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k += 4)
+            reinterpret_cast<float4 *>(p)[k / 4] = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+    } else if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k += 2) reinterpret_cast<float2 *>(p)[k / 2] = make_float2(v[k], v[k + 1]);
     } else {
 #pragma unroll
         for (int k = 0; k < K; ++k) p[k] = v[k];
@@ -840,11 +859,18 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
           int tile_blocks, int ntiles, double *__restrict__ tpart, int *__restrict__ seg_cnt, int seg_tiles)
 {
     constexpr int M = 32 * K;
+    // Each half-warp covers all M probe columns (KH = M / 16 per lane) and the two halves take
+    // alternate union entries of the same row block: one shared-memory broadcast of an entry's
+    // column and 8 values then feeds 8 x KH products per lane (twice the products per staged entry
+    // of a lane-per-column layout), and every lane keeps D independent 4 KH-byte gathers in flight.
+    constexpr int KH = 2 * K;
+    constexpr int D = K >= 3 ? 4 : 8;
     constexpr int W = RBCfg<K>::warps;
     extern __shared__ __align__(16) unsigned char rb_sh[];
     int *s_col = reinterpret_cast<int *>(rb_sh);                                    // W x 32
     float4 *s_val = reinterpret_cast<float4 *>(rb_sh + sizeof(int) * W * kWarp);  // W x 32 x 2
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int half = lane >> 4, hl = lane & 15;
     const int64_t nblk = (n + kRB - 1) / kRB;
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(&work->next, 1ull);
@@ -854,10 +880,11 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
         if (lane == 0) tn = atomicAdd(&work->next, 1ull);
         const int64_t bb = (int64_t)t * tile_blocks;
         const int64_t be = bb + tile_blocks < nblk ? bb + tile_blocks : nblk;
-        Acc32 dz[K];
+        Acc32 dz[KH];
         Acc32 dy;
         // the tile's entries are contiguous: stream them in 32-entry batches that never straddle
-        // a block, the next batch's column and values loaded while the current one is consumed
+        // a block, the next batch's column and values loaded while the current one is consumed;
+        // lanes past the block's last entry stage a zero entry on the block's first row
         int64_t b = bb;
         int e1 = bptr[b + 1];
         int eb = bptr[b];
@@ -868,16 +895,16 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             v0_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2];
             v1_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2 + 1];
         }
-        // accumulators of row pairs (2p, 2p + 1) for each column: one packed FP32x2 FMA per pair
-        // (each half rounds exactly like a scalar fmaf)
-        float2 acc[kRB / 2][K];
+        // accumulators of row pairs (2p, 2p + 1) for each of the lane's columns: one packed FP32x2
+        // FMA per pair (each half rounds exactly like a scalar fmaf)
+        float2 acc[kRB / 2][KH];
         float ay[kRB];
 #pragma unroll
         for (int r = 0; r < kRB; ++r) ay[r] = 0.0f;
 #pragma unroll
         for (int rp = 0; rp < kRB / 2; ++rp)
 #pragma unroll
-            for (int k = 0; k < K; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
+            for (int k = 0; k < KH; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
         while (b < be) {
             const int cj = cj_n;
             const float4 v0 = v0_n, v1 = v1_n;
@@ -912,44 +939,69 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             s_val[(wid * kWarp + lane) * 2] = v0;
             s_val[(wid * kWarp + lane) * 2 + 1] = v1;
             __syncwarp();
-#pragma unroll (K > 2 ? 4 : 8)
-            for (int u = 0; u < cnt; ++u) {
-                const int j = s_col[wid * kWarp + u];
-                const float4 a0 = s_val[(wid * kWarp + u) * 2], a1 = s_val[(wid * kWarp + u) * 2 + 1];
-                float pv[K];
-                load_k<float, K>(pz + (int64_t)j * M + lane * K, pv);
-                const float2 vp[kRB / 2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
-                                            make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
+            // half h takes entries 2u + h, u < ceil(cnt / 2), in groups of D (the staged entries
+            // past cnt are zeros, so a group may run past cnt)
+            const int npair = (cnt + 1) >> 1;
+            const int *scol = s_col + wid * kWarp + half;
+            const float4 *sval = s_val + (wid * kWarp + half) * 2;
+#pragma unroll 1
+            for (int u0 = 0; u0 < npair; u0 += D) {
+                int jj[D];
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const float2 pk = make_float2(pv[k], pv[k]);
+                for (int d = 0; d < D; ++d) jj[d] = scol[2 * (u0 + d)];
+                float pv[D][KH];
 #pragma unroll
-                    for (int rp = 0; rp < kRB / 2; ++rp) acc[rp][k] = __ffma2_rn(vp[rp], pk, acc[rp][k]);
+                for (int d = 0; d < D; ++d) load_k<float, KH>(pz + (int64_t)jj[d] * M + hl * KH, pv[d]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) {
+                    const float4 a0 = sval[4 * (u0 + d)], a1 = sval[4 * (u0 + d) + 1];
+                    const float2 vp[kRB / 2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
+                                                make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
+#pragma unroll
+                    for (int k = 0; k < KH; ++k) {
+                        const float2 pk = make_float2(pv[d][k], pv[d][k]);
+#pragma unroll
+                        for (int rp = 0; rp < kRB / 2; ++rp) acc[rp][k] = __ffma2_rn(vp[rp], pk, acc[rp][k]);
+                    }
                 }
             }
             __syncwarp();
             if (block_end) {
-                // row block bcur is complete: store its rows and fold them into the tile's dots
+                // row block bcur is complete: half h adds its partner's sums of rows 4h .. 4h + 3
+                // to its own, stores those rows and folds them into the tile's dots
                 const int64_t r0 = bcur * kRB;
                 const int nrows = (int)(n - r0 < kRB ? n - r0 : kRB);
+                float2 mine[2][KH];
 #pragma unroll
-                for (int r = 0; r < kRB; ++r) {
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int k = 0; k < KH; ++k) {
+                        const float2 keep = half ? acc[2 + q][k] : acc[q][k];
+                        const float2 send = half ? acc[q][k] : acc[2 + q][k];
+                        float2 got;
+                        got.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+                        got.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+                        mine[q][k] = make_float2(keep.x + got.x, keep.y + got.y);
+                    }
+#pragma unroll
+                for (int rr = 0; rr < kRB / 2; ++rr) {
+                    const int r = 4 * half + rr;
                     if (r < nrows) {
                         const int64_t i = r0 + r;
-                        float qr[K];
+                        float qr[KH];
 #pragma unroll
-                        for (int k = 0; k < K; ++k) qr[k] = (r & 1) ? acc[r / 2][k].y : acc[r / 2][k].x;
-                        store_k<float, K>(qz + i * M + lane * K, qr);
-                        float pi[K];
-                        load_k<float, K>(pz + i * M + lane * K, pi);
+                        for (int k = 0; k < KH; ++k) qr[k] = (rr & 1) ? mine[rr / 2][k].y : mine[rr / 2][k].x;
+                        store_k<float, KH>(qz + i * M + hl * KH, qr);
+                        float pi[KH];
+                        load_k<float, KH>(pz + i * M + hl * KH, pi);
 #pragma unroll
-                        for (int k = 0; k < K; ++k) dz[k].fma2(pi[k], qr[k]);
+                        for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
                     }
                 }
 #pragma unroll
                 for (int rp = 0; rp < kRB / 2; ++rp)
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
+                    for (int k = 0; k < KH; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
                 if (HAS_Y) {
 #pragma unroll
                     for (int r = 0; r < kRB; ++r) {
@@ -965,18 +1017,31 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
                 }
             }
         }
+        // the tile's dot of each probe column: rows 0-3 of every block (half 0) plus rows 4-7
+        // (half 1), in that order
+        double dzt[KH];
+#pragma unroll
+        for (int k = 0; k < KH; ++k) {
+            const double v = dz[k].value();
+            const double o = __shfl_xor_sync(0xffffffffu, v, 16);
+            dzt[k] = half ? o + v : v + o;
+        }
         if (seg_tiles == 1) {
             // every tile is a segment of its own: its partial dots go straight to part
+            if (half == 0) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) part[(int64_t)(1 + lane * K + k) * pstride + (int64_t)t] = dz[k].value();
+                for (int k = 0; k < KH; ++k) part[(int64_t)(1 + hl * KH + k) * pstride + (int64_t)t] = dzt[k];
+            }
             if (lane == 0) part[(int64_t)t] = HAS_Y ? dy.value() : 0.0;
             t = __shfl_sync(0xffffffffu, tn, 0);
             continue;
         }
         // the tile's partial dots, then the segment count; the segment's last tile reduces it
         double *tp = tpart + (int64_t)t * (M + 1);
+        if (half == 0) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) tp[1 + lane * K + k] = dz[k].value();
+            for (int k = 0; k < KH; ++k) tp[1 + hl * KH + k] = dzt[k];
+        }
         if (lane == 0) tp[0] = HAS_Y ? dy.value() : 0.0;
         __threadfence();
         __syncwarp();
@@ -1068,6 +1133,7 @@ gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride
                                                      c->rb_tpart.as<double>(), c->rb_seg.as<int>(), tl.seg_tiles);
     GP2S_LAUNCH(c);
     *nparts = tl.nseg;
+    c->spmm_seg_tiles = std::max(c->spmm_seg_tiles, tl.seg_tiles);
     return GP2S_OK;
 }
 

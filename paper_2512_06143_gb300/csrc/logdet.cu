@@ -605,6 +605,17 @@ extern "C" gp2s_status gp2s_lml_exact_noalloc(int64_t n, const double *X_dev, co
     if (!X_dev || !y_dev || !out_dev) return GP2S_EINVAL;
     if (validate_hyper(nullptr, hyper) != GP2S_OK) return GP2S_EINVAL;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    // the scratch address is per device: a stream of another device would get this device's
+    // address, so such a stream is refused (the legacy and per-thread default streams follow the
+    // current device)
+    if (s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
+        int cur = 0, sdev = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return GP2S_ECUDA;
+        }
+        if (sdev != cur) return GP2S_EINVAL;
+    }
     double *base = nullptr;
     gp2s_status st = noalloc_scratch(&base);
     if (st != GP2S_OK) return st;

@@ -59,6 +59,25 @@ def test_noalloc_matches_gp2s_lml_two_calls(gp):
         assert out[2] == pytest.approx(info["logdet"], rel=1e-10)
 
 
+@pytest.mark.parametrize("d,kind,w0", [(1, 0, 0.0), (2, 0, 0.0), (3, 0, 0.0), (4, 0, 0.0), (1, 1, 0.0),
+                                        (2, 1, 0.0), (3, 1, 0.0), (2, 0, 0.7), (3, 1, 0.5), (4, 0, 1.0)])
+def test_noalloc_matches_the_oracle(gp, d, kind, w0):
+    """Directly against the FP64 oracle's dense LML (brute-force A, library Cholesky), independent of
+    the CSR path: both Wendland kinds, with and without the constant w0 under the bump sum."""
+    import oracle
+    w = W.random_small(410 + d + 10 * kind, 500, d, L=3, sigma2=1e-3, kind=kind, w0=w0,
+                       r={1: 0.02, 2: 0.15, 3: 0.25, 4: 0.4}[d])
+    h = gp.Hyper(**w["hyper"])
+    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
+    y = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
+    st, out = _noalloc(gp, X, y, h)
+    assert st == gp.OK
+    e = oracle.lml_exact(w["X"], w["y"], oracle.Hyper(**w["hyper"]))
+    assert out[2] == pytest.approx(e["logdet"], rel=1e-10)
+    assert out[1] == pytest.approx(e["quad"], rel=1e-8)
+    assert out[0] == pytest.approx(e["lml"], rel=1e-8)
+
+
 def test_noalloc_rejects_sizes_beyond_the_limit(gp):
     w = W.random_small(403, 513, 2)
     h = gp.Hyper(**w["hyper"])
