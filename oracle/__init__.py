@@ -13,6 +13,9 @@ What each function follows:
                            Cholesky factorisation (solve and log-determinant exactly).
   * ``grad_exact``      -- the standard LML derivative 1/2 a^T dA a - 1/2 tr(A^{-1} dA) with the
                            dense inverse (exact trace).
+  * ``posterior``       -- Eq. 2 (Sec. 3): posterior mean k(X,x*)^T A^{-1} y and latent variance
+                           k(x*,x*) - k(X,x*)^T A^{-1} k(X,x*), A = K + sigma^2 I, by a dense
+                           Cholesky factorisation of the brute-force A and cross-covariance.
   * ``lml_slq``         -- where the paper leaves the log-determinant method open (Sec. 4.6,
                            App. B.7): Jacobi-scaled conjugate gradients for a = A^{-1} y,
                            stochastic Lanczos quadrature (Ubaru, Chen & Saad 2017) with
@@ -79,6 +82,7 @@ def lib():
             "orc_rows_brute": (None, [i64, vp, hp, i64, vp, vp, vp, vp]),
             "orc_assemble_candidates": (i64, [i64, vp, hp, i64, vp, vp, vp, vp, vp]),
             "orc_dense_A": (None, [i64, vp, hp, vp]),
+            "orc_cross_K": (None, [i64, vp, i64, vp, hp, vp]),
             "orc_spmm": (None, [i64, vp, vp, vp, i32, vp, vp]),
             "orc_cg": (i32, [i64, vp, vp, vp, i32, vp, vp, dbl, i32, i32, vp, vp, vp]),
             "orc_lanczos": (None, [i64, vp, vp, vp, i32, vp, i32, vp, vp, vp]),
@@ -301,6 +305,38 @@ def lml_exact(X, y, h: Hyper) -> dict:
     n = y.shape[0]
     return dict(lml=-0.5 * quad - 0.5 * logdet - 0.5 * n * LOG2PI, quad=quad, logdet=logdet, a=a,
                 A=A, chol=Lc)
+
+
+def cross_K(Xs, X, h: Hyper) -> np.ndarray:
+    """K(X*, X) (n* x n) by brute force over every (test, training) pair."""
+    X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, h.d))
+    Xs = np.ascontiguousarray(np.asarray(Xs, np.float64).reshape(-1, h.d))
+    Ks = np.empty((Xs.shape[0], X.shape[0]))
+    hr, _keep = h.c()
+    lib().orc_cross_K(Xs.shape[0], _p(Xs), X.shape[0], _p(X), hr, _p(Ks))
+    return Ks
+
+
+def prior_var(Xs, h: Hyper) -> np.ndarray:
+    """k(x*, x*) for every test point (the kernel definition at zero distance)."""
+    Xs = np.asarray(Xs, np.float64).reshape(-1, h.d)
+    return np.array([kernel(h, x, x) for x in Xs])
+
+
+def posterior(X, y, h: Hyper, Xs) -> dict:
+    """Eq. 2 with zero prior mean and A = K + sigma^2 I in place of the paper's K (the same
+    matrix whose inverse the LML of Sec. 3 uses):
+        mean_i = k(X, x*_i)^T A^{-1} y,   var_i = k(x*_i, x*_i) - k(X, x*_i)^T A^{-1} k(X, x*_i)
+    (the latent f* variance; the noisy y* adds sigma^2), by a dense Cholesky factorisation
+    (library routine) of the brute-force A."""
+    import scipy.linalg as sl
+    y = np.asarray(y, np.float64)
+    A = dense_A(X, h)
+    Lc = np.linalg.cholesky(A)
+    Ks = cross_K(Xs, X, h)
+    a = sl.cho_solve((Lc, True), y)
+    W = sl.solve_triangular(Lc, Ks.T, lower=True)          # L^{-1} k(X, x*)
+    return dict(mean=Ks @ a, var=prior_var(Xs, h) - np.sum(W * W, axis=0), a=a, Ks=Ks, A=A)
 
 
 def grad_contract(X, h: Hyper, csr: CSR, a, U=None, V=None, Wd=None) -> np.ndarray:

@@ -363,6 +363,29 @@ void orc_dense_A(int64_t n, const double *X, const orc_hyper *h, double *A)
     free(B);
 }
 
+/* Cross-covariance for the posterior of Sec. 3 (Eq. 2): Ks[i * n + j] = k(xs_i, x_j) for
+ * test points xs (ns x d) and training points x (n x d), every pair evaluated; the entry is
+ * nonzero only inside the support, d2 < r*r (strict), with d2 in the pattern's FP64 order.
+ * No noise term: a test point is a new location, never the same index as a training point. */
+void orc_cross_K(int64_t ns, const double *Xs, int64_t n, const double *X, const orc_hyper *h, double *Ks)
+{
+    const int d = h->d;
+    double *B = bump_table(n, X, h);
+    double *Bs = bump_table(ns, Xs, h);
+    if (!B || !Bs) { free(B); free(Bs); return; }
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < ns; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            const double *xi = Xs + (size_t)i * d, *xj = X + (size_t)j * d;
+            double v = 0.0;
+            if (orc_in_pattern(d, xi, xj, h->r))
+                v = kernel_from_bumps(h, xi, xj, Bs + (size_t)i * h->L, B + (size_t)j * h->L);
+            Ks[(size_t)i * n + j] = v;
+        }
+    free(B);
+    free(Bs);
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Sparse products and Krylov methods in FP64.                                          */
 /* ------------------------------------------------------------------------------------ */
