@@ -16,6 +16,8 @@ What each function follows:
   * ``posterior``       -- Eq. 2 (Sec. 3): posterior mean k(X,x*)^T A^{-1} y and latent variance
                            k(x*,x*) - k(X,x*)^T A^{-1} k(X,x*), A = K + sigma^2 I, by a dense
                            Cholesky factorisation of the brute-force A and cross-covariance.
+  * ``minres``          -- the solver the paper uses for K^{-1} y (App. B.6): MINRES (Paige &
+                           Saunders 1975), the Lanczos process with Givens rotations.
   * ``lml_slq``         -- where the paper leaves the log-determinant method open (Sec. 4.6,
                            App. B.7): Jacobi-scaled conjugate gradients for a = A^{-1} y,
                            stochastic Lanczos quadrature (Ubaru, Chen & Saad 2017) with
@@ -403,6 +405,60 @@ def cg(M: CSR, B, tol: float = 1e-10, maxit: int = 100000, kmax: int = 0):
     if st < 0:
         raise MemoryError("oracle cg")
     return (Xm.ravel() if one else Xm), steps, al[:, :kmax], be[:, :kmax], st
+
+
+def minres(M, b, tol: float = 1e-10, maxit: int = 100000):
+    """MINRES (Paige & Saunders 1975) for a symmetric M x = b, x0 = 0 (the paper's solver for
+    K^{-1} y, App. B.6).  M is a CSR or a callable v -> M v.  Lanczos with beta_1 v_1 = b:
+        u = M v_k - beta_k v_{k-1},  alpha_k = v_k^T u,  u -= alpha_k v_k,  beta_{k+1} v_{k+1} = u,
+    and the tridiagonal's QR factorisation by Givens rotations G_k = [[c_k, s_k], [-s_k, c_k]]:
+        eps_k = s_{k-2} beta_k,  dbar_k = c_{k-2} beta_k,
+        delta_k = c_{k-1} dbar_k + s_{k-1} alpha_k,  gbar_k = -s_{k-1} dbar_k + c_{k-1} alpha_k,
+        gamma_k = |(gbar_k, beta_{k+1})|,  c_k = gbar_k / gamma_k,  s_k = beta_{k+1} / gamma_k,
+        tau_k = c_k phibar_{k-1},  phibar_k = -s_k phibar_{k-1}   (phibar_0 = beta_1),
+        w_k = (v_k - delta_k w_{k-1} - eps_k w_{k-2}) / gamma_k,  x_k = x_{k-1} + tau_k w_k,
+    with |b - M x_k| = |phibar_k|.  Stops when |phibar_k| <= tol |b|.
+    Returns x, iterations, and the residual norms |phibar_k| (k = 0, 1, ...)."""
+    op = M.matmat if isinstance(M, CSR) else M
+    b = np.asarray(b, np.float64)
+    n = b.shape[0]
+    x = np.zeros(n)
+    beta1 = float(np.linalg.norm(b))
+    hist = [beta1]
+    if beta1 == 0.0:
+        return x, 0, hist
+    v_prev = np.zeros(n)
+    v = b / beta1
+    beta = beta1
+    c_km2, s_km2, c_km1, s_km1 = 1.0, 0.0, 1.0, 0.0
+    w_km2 = np.zeros(n)
+    w_km1 = np.zeros(n)
+    phibar = beta1
+    k = 0
+    while k < maxit:
+        k += 1
+        u = op(v) - beta * v_prev
+        alpha = float(v @ u)
+        u = u - alpha * v
+        beta_next = float(np.linalg.norm(u))
+        eps = s_km2 * beta
+        dbar = c_km2 * beta
+        delta = c_km1 * dbar + s_km1 * alpha
+        gbar = -s_km1 * dbar + c_km1 * alpha
+        gamma = math.hypot(gbar, beta_next)
+        c_k, s_k = gbar / gamma, beta_next / gamma
+        tau = c_k * phibar
+        phibar = -s_k * phibar
+        w = (v - delta * w_km1 - eps * w_km2) / gamma
+        x = x + tau * w
+        hist.append(abs(phibar))
+        if abs(phibar) <= tol * beta1 or beta_next == 0.0:
+            break
+        v_prev, v = v, u / beta_next
+        beta = beta_next
+        c_km2, s_km2, c_km1, s_km1 = c_km1, s_km1, c_k, s_k
+        w_km2, w_km1 = w_km1, w
+    return x, k, hist
 
 
 def lanczos(M: CSR, Q1, steps: int):

@@ -65,3 +65,53 @@ def test_posterior_outside_every_support(orc):
     np.testing.assert_allclose(p["var"], 0.25, rtol=1e-15)
     b = orc.bumps(h, w["X"][0])
     assert orc.prior_var(w["X"][:1], h)[0] == pytest.approx(float(np.sum(b * b)) + 0.25, rel=1e-14)
+
+
+# ------------------------------------------------------------------------------------------------
+# MINRES (the paper's solver, App. B.6) pins: the library's dense solve, an indefinite system
+# (what CG cannot do), the residual-norm recurrence against the true residual, the minimal-residual
+# property against CG's iterates, and exactness on an operator with few distinct eigenvalues.
+# ------------------------------------------------------------------------------------------------
+def test_minres_solves_spd_and_indefinite_systems(orc):
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.normal(size=(60, 60)))
+    for ev in (np.linspace(0.1, 10.0, 60), np.concatenate([-np.linspace(0.5, 3.0, 20), np.linspace(0.2, 5.0, 40)])):
+        M = (Q * ev) @ Q.T
+        b = rng.normal(size=60)
+        x, it, hist = orc.minres(lambda v: M @ v, b, tol=1e-12, maxit=500)
+        np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-9, atol=1e-10)
+        assert hist[-1] <= 1e-12 * np.linalg.norm(b) * 1.0001
+
+
+def test_minres_residual_recurrence_and_minimality(orc):
+    w = W.random_small(530, 400, 2, L=2, sigma2=1e-2, r=0.12)
+    h = orc.Hyper(**w["hyper"])
+    A = orc.dense_A(w["X"], h)
+    b = w["y"]
+    for k in (1, 2, 5, 12, 30):
+        x, it, hist = orc.minres(lambda v: A @ v, b, tol=0.0, maxit=k)
+        assert it == k
+        true = np.linalg.norm(b - A @ x)
+        assert abs(true - hist[-1]) <= 1e-9 * np.linalg.norm(b)
+        # minimal residual over the Krylov space: no larger than CG's residual after k steps
+        xc, _, _, _, _ = orc.cg(orc.CSR(400, *_dense_csr(A)), b, tol=0.0, maxit=k)
+        assert true <= np.linalg.norm(b - A @ xc) * (1 + 1e-9)
+    assert all(hist[i + 1] <= hist[i] * (1 + 1e-12) for i in range(len(hist) - 1))
+
+
+def test_minres_exact_with_few_distinct_eigenvalues(orc):
+    rng = np.random.default_rng(4)
+    Q, _ = np.linalg.qr(rng.normal(size=(50, 50)))
+    M = (Q * np.repeat([0.5, 2.0, -1.0], [20, 20, 10])) @ Q.T
+    b = rng.normal(size=50)
+    x, it, hist = orc.minres(lambda v: M @ v, b, tol=1e-13, maxit=50)
+    assert it <= 3 + 1
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-10, atol=1e-11)
+
+
+def _dense_csr(A):
+    n = A.shape[0]
+    rows, cols = np.nonzero(A)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr), cols.astype(np.int32), A[rows, cols].astype(np.float64)
