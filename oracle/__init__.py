@@ -18,6 +18,9 @@ What each function follows:
                            Cholesky factorisation of the brute-force A and cross-covariance.
   * ``minres``          -- the solver the paper uses for K^{-1} y (App. B.6): MINRES (Paige &
                            Saunders 1975), the Lanczos process with Givens rotations.
+  * ``mcmc``            -- App. D's block Metropolis-Hastings training: normal random-walk
+                           proposals per parameter block, a flat prior inside bounds, one LML
+                           evaluation per block per iteration.
   * ``lml_slq``         -- where the paper leaves the log-determinant method open (Sec. 4.6,
                            App. B.7): Jacobi-scaled conjugate gradients for a = A^{-1} y,
                            stochastic Lanczos quadrature (Ubaru, Chen & Saad 2017) with
@@ -545,6 +548,40 @@ def lml_slq(X, y, h: Hyper, m: int = 64, k: int = 100, seed: int = 0, tol: float
         out["grad"] = grad_contract(X, h, csr, a, U=U, V=V)
         out["U"], out["V"] = U, V
     return out
+
+
+def mcmc(logpost, theta0, block, step, lower, upper, normals, uniforms):
+    """Block Metropolis-Hastings (App. D): for every iteration t and every block b in order,
+        theta' = theta + step * normals[t]   on the components p with block[p] == b,
+    rejected outright if any component leaves [lower, upper] (the flat prior's support), else
+    accepted when log(uniforms[t, b]) < logpost(theta') - logpost(theta).  Components with
+    block -1 never move.  logpost(theta) is the log-density (the LML for a flat prior).
+    Returns the chain (iters x (P + 1): theta after the sweep, then its log-density) and the
+    acceptance flags (iters x nblocks)."""
+    theta = np.array(theta0, np.float64)
+    block = np.asarray(block)
+    step = np.asarray(step, np.float64)
+    normals = np.asarray(normals, np.float64)
+    uniforms = np.asarray(uniforms, np.float64)
+    iters, nblocks = uniforms.shape
+    cur = float(logpost(theta))
+    chain = np.empty((iters, theta.size + 1))
+    acc = np.zeros((iters, nblocks), np.int32)
+    for t in range(iters):
+        for b in range(nblocks):
+            sel = block == b
+            prop = theta.copy()
+            prop[sel] = theta[sel] + step[sel] * normals[t, sel]
+            if np.any(prop < lower) or np.any(prop > upper):
+                continue
+            new = float(logpost(prop))
+            logu = math.log(uniforms[t, b]) if uniforms[t, b] > 0.0 else -math.inf
+            if logu < new - cur:
+                theta, cur = prop, new
+                acc[t, b] = 1
+        chain[t, :-1] = theta
+        chain[t, -1] = cur
+    return chain, acc
 
 
 def num_threads() -> int:
