@@ -306,6 +306,37 @@ def spmm_roofline(gp, ctx, X, y, hyper, wopts, precision, flush, workload, n, pe
                                 "input and per output vector element"}
 
 
+def pattern_cached_evals(gp, ctx, X, y, hyper, wopts, precision, steps, flush, stream) -> dict:
+    """The survey's second figure: evaluations where theta changes (bump amplitudes and centers, as
+    an MCMC block that leaves r alone would) but X and r do not, so the assembly reuses the
+    pattern.  One untimed evaluation sets the pattern, then `steps` timed ones."""
+    import torch
+    opts = gp.default_opts(precision=precision, **wopts)
+    th0 = hyper.theta()
+    L, d = hyper.L, hyper.d
+
+    def theta(k):
+        th = th0.copy()
+        th[:L * d] += 0.002 * (k + 1)
+        th[L * d + L:L * d + 2 * L] *= 1.0 + 0.01 * (k + 1)
+        return hyper.with_theta(th)
+
+    ctx.lml_grad(X, y, theta(-1), opts)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    reused = 0
+    for k in range(steps):
+        flush.fill_(k & 0xff)
+        ev[k][0].record(stream)
+        _, _, info = ctx.lml_grad(X, y, theta(k), opts)
+        ev[k][1].record(stream)
+        reused += int(info["pattern_reused"])
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"value": steps / (sum(ms) / 1000.0), "unit": "evals/s", "ms_per_step": sum(ms) / steps,
+            "steps_with_pattern_reused": reused, "steps": steps, "ms_assemble": info["ms_assemble"],
+            "note": "bump centers and amplitudes change every step; X and r fixed"}
+
+
 def measure_workload(gp, ctx, workload, seed, n, steps, warmup, flush, stream, barrier, peak, peak_src,
                      sampler=None):
     """Device-timed evaluations (production options), the end-to-end form from host buffers, and
@@ -315,7 +346,9 @@ def measure_workload(gp, ctx, workload, seed, n, steps, warmup, flush, stream, b
     hyper = gp.Hyper(**w["hyper"])
     nn = w["X"].shape[0]
     precision = gp.PREC_MIXED if workload != "small_2d" else gp.PREC_FP64
-    opts = gp.default_opts(precision=precision, **wopts)
+    # every timed step rebuilds the pattern (the full evaluation); the pattern-cached figure below
+    # changes theta every step and lets the assembly reuse the pattern
+    opts = gp.default_opts(precision=precision, pattern_cache=1, **wopts)
     X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
     y = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
     Xh = torch.tensor(w["X"], dtype=torch.float64).pin_memory()
@@ -328,9 +361,10 @@ def measure_workload(gp, ctx, workload, seed, n, steps, warmup, flush, stream, b
     clocks = sampler.stop() if sampler is not None else None
     e2e_ms = e2e_evals(ctx, Xh, yh, hyper, opts, steps, flush)
     roof = spmm_roofline(gp, ctx, X, y, hyper, wopts, precision, flush, workload, nn, peak, peak_src)
+    cached = pattern_cached_evals(gp, ctx, X, y, hyper, wopts, precision, steps, flush, stream)
     i0 = infos[-1]
     return dict(w=w, hyper=hyper, opts=opts, wopts=wopts, precision=precision, X=X, y=y, n=int(nn),
-                step_ms=step_ms, infos=infos, e2e_ms=e2e_ms, roofline=roof, clocks=clocks,
+                step_ms=step_ms, infos=infos, e2e_ms=e2e_ms, roofline=roof, clocks=clocks, pattern_cached=cached,
                 h2d=int(Xh.numel() * 8 + yh.numel() * 8), d2h=int(8 + 8 * hyper.nparams),
                 config={"workload": workload, "n": int(nn), "d": int(hyper.d), "L": hyper.L, "nnz": int(i0["nnz"]),
                         "probes": int(opts.probes), "lanczos_steps": int(opts.lanczos_steps),
@@ -440,6 +474,7 @@ def run_gpu(args):
                     "d2h_bytes_per_step": m2["d2h"]},
             "assembly": assembly_roofline(m2["n"], int(m2["hyper"].d), int(m2["hyper"].L),
                                           int(m2["infos"][-1]["nnz"]), m2["infos"][-1]["ms_assemble"], peak),
+            "pattern_cached": m2["pattern_cached"],
             "gpu_launches": int(sum(i["launches"] for i in m2["infos"])), "detail": m2["detail"]}
         secondary["batch"] = batch_record(gp, torch, local, steps=1, warmup=1)
     if rank == 0:
@@ -467,6 +502,7 @@ def run_gpu(args):
                              "extrapolated": True},
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": main_m["h2d"],
                     "d2h_bytes_per_step": main_m["d2h"]},
+            "pattern_cached": main_m["pattern_cached"],
             "clocks": main_m["clocks"], "gpu_launches": launches,
             "errors": errors,
             "secondary": secondary or None,

@@ -63,6 +63,11 @@ typedef enum {
 } gp2s_precision;
 
 typedef enum {
+    GP2S_SOLVER_CG = 0,
+    GP2S_SOLVER_MINRES = 1
+} gp2s_solver;
+
+typedef enum {
     GP2S_LOGDET_AUTO = 0,   /* EXACT when n <= n_exact, else SLQ */
     GP2S_LOGDET_EXACT = 1,  /* dense FP64 Cholesky of A: log|A| = 2 sum log L_ii */
     GP2S_LOGDET_SLQ = 2     /* stochastic Lanczos quadrature on D^{-1/2} A D^{-1/2} */
@@ -91,7 +96,8 @@ typedef struct {
     int32_t probes;          /* Rademacher probes m for SLQ / Hutchinson: 0, 32, 64, 96 or 128; default 64 */
     int32_t lanczos_steps;   /* SLQ steps k per probe, default 100 */
     int32_t max_iter;        /* iteration cap per CG solve, default 20000 */
-    double tol_inner;        /* FP32 inner CG relative residual, default 1e-5 */
+    double tol_inner;        /* FP32 inner CG relative residual of the first y solve, default 1e-6
+                                (about the FP32 floor: one refinement step then reaches tol_refine) */
     double tol_refine;       /* target |y - A a| / |y| of the y solve (FP64 residual), default 1e-8 */
     double tol_probe;        /* relative residual of the probe solves used by the gradient, default 1e-5 */
     uint64_t seed;           /* probe seed, default 0 */
@@ -106,6 +112,14 @@ typedef struct {
     int32_t bj_block;        /* rows per block-Jacobi block (precond = 2): 64, 128, or 0 =
                                 automatic (128 when A has at least 64 stored entries per row and
                                 at least 768 rows per SM, else 64); default 0 */
+    int32_t pattern_cache;   /* 0 = reuse the last assembly's pattern when X (fingerprint), n, d,
+                                r, exact_support and precision are unchanged: only the bump
+                                tables and values are recomputed; 1 = always rebuild; default 0 */
+    int32_t solver;          /* solver of the y column: GP2S_SOLVER_CG (default; multi-RHS with the
+                                probes, FP32 in MIXED precision with FP64 refinement) or
+                                GP2S_SOLVER_MINRES (App. B.6's solver: FP64 MINRES on
+                                D^{-1/2} A D^{-1/2}, restarted on the FP64 residual until
+                                tol_refine); the probe columns always run CG */
     int32_t reserved;
 } gp2s_opts;
 
@@ -118,6 +132,8 @@ typedef struct {
     double guard_delta;      /* relative guard band used by the FP32 pre-test */
     double cell_h;           /* cell edge */
     float ms_geometry, ms_count, ms_fill, ms_values64;
+    int32_t pattern_reused;  /* 1 when the pattern of the previous assembly was reused */
+    int32_t reserved;
 } gp2s_assemble_info;
 
 typedef struct {
@@ -152,6 +168,8 @@ typedef struct {
     int32_t bj_block;        /* rows per block-Jacobi block of the probe columns (0: no block-Jacobi) */
     int32_t spmm_seg_tiles;  /* largest number of row-block tiles per reduction segment in the
                                 multi-RHS SpMM launches (1: every tile is its own segment) */
+    int32_t pattern_reused;  /* 1 when the assembly reused the previous pattern */
+    int32_t reserved2;
 } gp2s_lml_info;
 
 typedef struct gp2s_ctx gp2s_ctx;
@@ -252,6 +270,77 @@ gp2s_status gp2s_lml_grad(gp2s_ctx *ctx, int64_t n, const double *X, const doubl
 gp2s_status gp2s_lml_batched(gp2s_ctx *ctx, int32_t B, const int64_t *n, const double *const *X,
                              const double *const *y, const gp2s_hyper *hyper,
                              const gp2s_opts *opts, double *lml_host, gp2s_lml_info *info_host);
+
+/*
+ * Posterior of Eq. 2 (Sec. 3) at n_test new points, on the last solved problem (after gp2s_lml,
+ * gp2s_lml_grad or gp2s_solve on this context; the solution a = A^{-1} y is kept, as App. B.7
+ * keeps K^{-1} y).  With zero prior mean and A = K + sigma2 I in place of the paper's K:
+ *     mean_i = k(X, x*_i)^T a
+ *     var_i  = k(x*_i, x*_i) - k(X, x*_i)^T A^{-1} k(X, x*_i)       (latent f*, add sigma2 for y*)
+ * k(X, x*) holds the training points with d2 < r*r (the training matrix's FP64 support test and
+ * kernel value, no noise term), found through the training cell grid.  The mean is one FP64 pass.
+ * The variance solves A v = k(X, x*) for batches of up to 64 test points as the columns of one
+ * multi-RHS CG in the problem's precision (block-Jacobi PCG in MIXED) to opts.tol_probe of the
+ * last assembly, and evaluates k^T A^{-1} k in its second-order (energy) form
+ * 2 k^T v - v^T A v in FP64; it overwrites the probe solutions of the last gp2s_lml_grad (the
+ * gradient was already returned).
+ *   Xtest: n_test x d FP64, host or device.  mean: n_test FP64, host or device.  var: n_test FP64,
+ *   host or device, or NULL to skip the variance solves.  info: optional.
+ * Returns GP2S_ENOTREADY without a solved problem, GP2S_ENOCONV if a variance solve hits max_iter.
+ */
+typedef struct {
+    int64_t n_test;
+    int64_t cross_entries;   /* nonzero k(x*_i, x_j) found */
+    int32_t batches;         /* variance solves */
+    int32_t iters_max;       /* largest CG iteration count of those solves */
+    float ms_mean, ms_var;
+} gp2s_posterior_info;
+gp2s_status gp2s_posterior(gp2s_ctx *ctx, int64_t n_test, const double *Xtest, double *mean, double *var,
+                           gp2s_posterior_info *info);
+
+/*
+ * Block Metropolis-Hastings training of theta (Sec. 4.6, App. D).  Each iteration sweeps the
+ * parameter blocks in order; block b proposes theta' = theta + step * z on its components
+ * (z standard normal), rejects theta' outside [lower, upper] (a flat prior), and otherwise
+ * evaluates LML(theta') with gp2s_lml (opts, with pattern reuse forced on: blocks that leave r
+ * alone recompute only the values) and accepts when log u < LML(theta') - LML(theta).
+ * A proposal the engine refuses (GP2S_EINVAL, GP2S_ENOTPD) is a rejection.
+ *   block: P = L (d + 2) + 2 ints, the block of each theta component (-1 = held fixed); a block
+ *          without members is skipped.
+ *   step:  P proposal standard deviations.  lower / upper: P bounds each, or NULL (unbounded).
+ *   normals (iters x P) / uniforms (iters x nblocks): the random numbers, or NULL to let the
+ *          driver draw them (SplitMix64 counter stream keyed by seed; Box-Muller normals).
+ *   checkpoint: file written every checkpoint_every iterations (and after the last), or NULL.
+ *   resume = 1: continue from that file (its iteration count, theta and LML); rows before the
+ *          resumed iteration are not written.
+ *   chain: host, iters x (P + 1): theta after each iteration's sweep, then its LML.
+ *   accept: host, iters x nblocks acceptance flags, or NULL.
+ */
+typedef struct {
+    int32_t iters;
+    int32_t nblocks;                 /* 1..64 */
+    const int32_t *block;
+    const double *step;
+    const double *lower, *upper;
+    const double *normals, *uniforms;
+    uint64_t seed;
+    const char *checkpoint;
+    int32_t checkpoint_every;
+    int32_t resume;
+} gp2s_mcmc_opts;
+typedef struct {
+    int32_t start, done;             /* first iteration run by this call, iterations completed */
+    int32_t evals;                   /* LML evaluations */
+    int32_t pattern_reused;          /* of which reused the previous pattern */
+    int32_t accepted;                /* accepted proposals over the whole chain */
+    int32_t reserved;
+    double lml;                      /* LML of the final state */
+    float ms;
+    float reserved_f;
+} gp2s_mcmc_info;
+gp2s_status gp2s_mcmc(gp2s_ctx *ctx, int64_t n, const double *X, const double *y, const gp2s_hyper *hyper0,
+                      const gp2s_opts *opts, const gp2s_mcmc_opts *mcmc, double *chain, int32_t *accept,
+                      gp2s_mcmc_info *info);
 
 /*
  * Allocation-free exact LML for small problems.  The paper has no counterpart: this is a service

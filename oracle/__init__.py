@@ -570,6 +570,8 @@ def mcmc(logpost, theta0, block, step, lower, upper, normals, uniforms):
     for t in range(iters):
         for b in range(nblocks):
             sel = block == b
+            if not np.any(sel):
+                continue                      # a block without members proposes nothing
             prop = theta.copy()
             prop[sel] = theta[sel] + step[sel] * normals[t, sel]
             if np.any(prop < lower) or np.any(prop > upper):

@@ -31,6 +31,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ENOCONV", "EBREAKDOWN", "ETI
 WENDLAND_C2, WENDLAND_C6_PAPER = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 LOGDET_AUTO, LOGDET_EXACT, LOGDET_SLQ = 0, 1, 2
+SOLVER_CG, SOLVER_MINRES = 0, 1
 
 
 class _Hyper(ctypes.Structure):
@@ -46,7 +47,7 @@ class Opts(ctypes.Structure):
                 ("tol_inner", ctypes.c_double), ("tol_refine", ctypes.c_double), ("tol_probe", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("precond", ctypes.c_int32), ("exact_support", ctypes.c_int32),
                 ("max_outer", ctypes.c_int32), ("profile", ctypes.c_int32), ("bj_block", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("pattern_cache", ctypes.c_int32), ("solver", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class AssembleInfo(ctypes.Structure):
@@ -54,7 +55,7 @@ class AssembleInfo(ctypes.Structure):
                 ("band_pairs", ctypes.c_int64), ("ncells", ctypes.c_int64), ("nnz_row_min", ctypes.c_int32),
                 ("nnz_row_max", ctypes.c_int32), ("guard_delta", ctypes.c_double), ("cell_h", ctypes.c_double),
                 ("ms_geometry", ctypes.c_float), ("ms_count", ctypes.c_float), ("ms_fill", ctypes.c_float),
-                ("ms_values64", ctypes.c_float)]
+                ("ms_values64", ctypes.c_float), ("pattern_reused", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -76,7 +77,26 @@ class LmlInfo(ctypes.Structure):
                 ("ms_solve", ctypes.c_float), ("ms_logdet", ctypes.c_float), ("ms_grad", ctypes.c_float),
                 ("ms_total", ctypes.c_float), ("launches", ctypes.c_int64), ("spmm_launches", ctypes.c_int64),
                 ("spmm_bytes", ctypes.c_double), ("ms_spmm", ctypes.c_float), ("reserved_f", ctypes.c_float),
-                ("bj_block", ctypes.c_int32), ("spmm_seg_tiles", ctypes.c_int32)]
+                ("bj_block", ctypes.c_int32), ("spmm_seg_tiles", ctypes.c_int32),
+                ("pattern_reused", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+
+
+class PosteriorInfo(ctypes.Structure):
+    _fields_ = [("n_test", ctypes.c_int64), ("cross_entries", ctypes.c_int64), ("batches", ctypes.c_int32),
+                ("iters_max", ctypes.c_int32), ("ms_mean", ctypes.c_float), ("ms_var", ctypes.c_float)]
+
+
+class McmcOpts(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("nblocks", ctypes.c_int32), ("block", ctypes.c_void_p),
+                ("step", ctypes.c_void_p), ("lower", ctypes.c_void_p), ("upper", ctypes.c_void_p),
+                ("normals", ctypes.c_void_p), ("uniforms", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("checkpoint", ctypes.c_char_p), ("checkpoint_every", ctypes.c_int32), ("resume", ctypes.c_int32)]
+
+
+class McmcInfo(ctypes.Structure):
+    _fields_ = [("start", ctypes.c_int32), ("done", ctypes.c_int32), ("evals", ctypes.c_int32),
+                ("pattern_reused", ctypes.c_int32), ("accepted", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lml", ctypes.c_double), ("ms", ctypes.c_float), ("reserved_f", ctypes.c_float)]
 
 
 class CsrView(ctypes.Structure):
@@ -87,7 +107,7 @@ class CsrView(ctypes.Structure):
 
 EXPORTED = ["gp2s_opts_default", "gp2s_num_params", "gp2s_create", "gp2s_destroy", "gp2s_last_error",
             "gp2s_assemble", "gp2s_csr", "gp2s_solve", "gp2s_logdet", "gp2s_lml", "gp2s_lml_grad",
-            "gp2s_lml_batched", "gp2s_lml_exact_noalloc"]
+            "gp2s_lml_batched", "gp2s_posterior", "gp2s_mcmc", "gp2s_lml_exact_noalloc"]
 
 _lib = None
 
@@ -127,6 +147,8 @@ def load(path: str | None = None):
         "gp2s_lml_grad": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, vp]),
         "gp2s_lml_batched": (i32, [vp, i32, vp, vp, vp, vp, vp, vp, vp]),
         "gp2s_lml_exact_noalloc": (i32, [i64, vp, vp, vp, vp, vp]),
+        "gp2s_posterior": (i32, [vp, i64, vp, vp, vp, vp]),
+        "gp2s_mcmc": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(L, name)
@@ -327,6 +349,64 @@ class Context:
         self._check(self._lib.gp2s_lml_grad(self._h, int(kx.shape[0]), px, py, ctypes.byref(hc), ctypes.byref(o),
                                             ctypes.byref(out), g.ctypes.data, ctypes.byref(info)))
         return out.value, g, _struct_dict(info)
+
+    def posterior(self, Xtest, variance: bool = True) -> tuple:
+        """Posterior mean (and latent variance) of Eq. 2 at Xtest (n* x d) on the last solved
+        problem.  Outputs are CUDA tensors when Xtest is one, else numpy arrays."""
+        px, kx = _ptr(Xtest)
+        ns = int(kx.shape[0])
+        try:
+            import torch
+            on_dev = isinstance(kx, torch.Tensor) and kx.is_cuda
+        except ImportError:
+            on_dev = False
+        if on_dev:
+            mean = torch.empty(ns, dtype=torch.float64, device=kx.device)
+            var = torch.empty(ns, dtype=torch.float64, device=kx.device) if variance else None
+        else:
+            mean = np.empty(ns)
+            var = np.empty(ns) if variance else None
+        pm, km = _ptr(mean)
+        pv = _ptr(var)[0] if variance else None
+        info = PosteriorInfo()
+        self._check(self._lib.gp2s_posterior(self._h, ns, px, pm, pv, ctypes.byref(info)))
+        return mean, var, _struct_dict(info)
+
+    def mcmc(self, X, y, hyper0: Hyper, block, step, iters: int, opts: Opts | None = None, lower=None,
+             upper=None, normals=None, uniforms=None, seed: int = 0, checkpoint: str | None = None,
+             checkpoint_every: int = 0, resume: bool = False) -> tuple:
+        """Block Metropolis-Hastings over theta (App. D).  block / step / lower / upper: one entry per
+        theta component.  Returns (chain iters x (P + 1), accept iters x nblocks, info)."""
+        px, kx = _ptr(X)
+        py, ky = _ptr(y)
+        P = hyper0.nparams
+        blk = np.ascontiguousarray(np.asarray(block, np.int32))
+        stp = np.ascontiguousarray(np.asarray(step, np.float64))
+        if blk.shape != (P,) or stp.shape != (P,):
+            raise ValueError("block and step need one entry per theta component")
+        nb = int(blk.max()) + 1 if blk.size else 1
+        keep = [blk, stp]
+
+        def arr(a, shape):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(a, np.float64))
+            if a.shape != shape:
+                raise ValueError(f"expected shape {shape}, got {a.shape}")
+            keep.append(a)
+            return a.ctypes.data
+
+        mo = McmcOpts(int(iters), nb, blk.ctypes.data, stp.ctypes.data, arr(lower, (P,)), arr(upper, (P,)),
+                      arr(normals, (int(iters), P)), arr(uniforms, (int(iters), nb)), int(seed) & (2**64 - 1),
+                      checkpoint.encode() if checkpoint else None, int(checkpoint_every), 1 if resume else 0)
+        hc = hyper0.c()
+        o = opts or default_opts()
+        chain = np.full((int(iters), P + 1), np.nan)
+        acc = np.zeros((int(iters), nb), np.int32)
+        info = McmcInfo()
+        self._check(self._lib.gp2s_mcmc(self._h, int(kx.shape[0]), px, py, ctypes.byref(hc), ctypes.byref(o),
+                                        ctypes.byref(mo), chain.ctypes.data, acc.ctypes.data, ctypes.byref(info)))
+        return chain, acc, _struct_dict(info)
 
     def lml_batched(self, problems: list, opts: Opts | None = None) -> tuple:
         """problems: list of (X, y, Hyper).  Returns (lml array, list of info dicts)."""

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libgp2s.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wno-deprecated-declarations",
               "-diag-suppress", "1444", "-I", os.path.join(ROOT, "include")]
-SOURCES = ["prim.cu", "geometry.cu", "assemble.cu", "krylov.cu", "logdet.cu", "adjoint.cu", "batched.cu", "capi.cu"]
+SOURCES = ["prim.cu", "geometry.cu", "assemble.cu", "krylov.cu", "logdet.cu", "adjoint.cu", "posterior.cu", "minres.cu", "mcmc.cu", "batched.cu", "capi.cu"]
 HEADERS = ["gp2s_internal.cuh", "gp2s_geometry.cuh", "gp2s_kernel_math.cuh"]
 
 

@@ -107,16 +107,11 @@ k_assemble(AsmArgs a, GridParams g, SupportParams sp, KernelParams kp)
     int2 *rng_sorted = rng + NNB;
     int *pref = reinterpret_cast<int *>(rng_sorted + NNB);           // NNB + 1
     int *nr_sh = pref + NNB + 1;
-    float *c_B = reinterpret_cast<float *>(nr_sh + 4);               // kChunk x L (fill)
-    float *c_s = c_B + (FILL ? kChunk * kp.L : 0);
-    float *r_B = c_s + (FILL ? kChunk : 0);                          // kRowsPerItem x L
-    float *r_s = r_B + (FILL ? kRowsPerItem * kp.L : 0);
 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int4 item = a.items[blockIdx.x];
     const int cell = item.x, r0 = item.y, r1 = item.z;
     const int nrows = r1 - r0;
-    const int L = kp.L;
 
     // 1. neighbour cells and their point ranges
     const int cb = g.bits - g.fine_bits;
@@ -144,10 +139,6 @@ k_assemble(AsmArgs a, GridParams g, SupportParams sp, KernelParams kp)
         r_hi[t] = a.Xhi[r0 + t];
         r_lo[t] = a.Xlo[r0 + t];
         r_run[t] = 0;
-        if (FILL) {
-            for (int l = 0; l < L; ++l) r_B[t * L + l] = a.B32[(int64_t)(r0 + t) * L + l];
-            r_s[t] = a.s32[r0 + t];
-        }
     }
     __syncthreads();
     // 2. order the non-empty ranges by start (ranges of distinct cells are disjoint)
@@ -195,10 +186,6 @@ k_assemble(AsmArgs a, GridParams g, SupportParams sp, KernelParams kp)
             c_j[q] = j;
             c_hi[q] = a.Xhi[j];
             c_lo[q] = a.Xlo[j];
-            if (FILL) {
-                for (int l = 0; l < L; ++l) c_B[q * L + l] = a.B32[(int64_t)j * L + l];
-                c_s[q] = a.s32[j];
-            }
         }
         __syncthreads();
         for (int rs = wid; rs < nrows; rs += kAsmWarps) {
@@ -226,22 +213,9 @@ k_assemble(AsmArgs a, GridParams g, SupportParams sp, KernelParams kp)
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, acc);
                 if (FILL && acc) {
+                    // columns only: the values pass evaluates every stored pair in FP64
                     const int pos = run + __popc(bal & ((1u << lane) - 1u));
-                    float v;
-                    if (j == i) {
-                        v = 1.0f;                               // Ah_ii = A_ii / D_i = 1
-                    } else {
-                        float t = sqrtf(d2) * (float)kp.inv_r;
-                        float phi = wendland<float>(kp.kind, D, t);
-                        float S = 0.0f;
-                        for (int l = 0; l < L; ++l) S = fmaf(r_B[rs * L + l], c_B[q * L + l], S);
-                        S += (float)kp.w0;
-                        v = phi * S * (r_s[rs] * c_s[q]);
-                    }
-                    if (pos < rowlen) {
-                        a.col[obase + pos] = j;
-                        if (a.val) a.val[obase + pos] = v;
-                    }
+                    if (pos < rowlen) a.col[obase + pos] = j;
                 }
                 run += __popc(bal);
             }
@@ -264,7 +238,8 @@ size_t asm_smem_bytes(int D, bool fill, int L)
     int NNB = D == 1 ? 3 : D == 2 ? 9 : D == 3 ? 27 : 81;
     size_t b = sizeof(float4) * (2 * kChunk + 2 * kRowsPerItem) + sizeof(int) * (kChunk + kRowsPerItem) +
                sizeof(int2) * 2 * NNB + sizeof(int) * (NNB + 1 + 4);
-    if (fill) b += sizeof(float) * (kChunk * L + kChunk + kRowsPerItem * L + kRowsPerItem);
+    (void)fill;
+    (void)L;
     return b + 16;
 }
 
@@ -315,7 +290,7 @@ template <int D>
 __global__ void __launch_bounds__(256)
 k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowptr,
            const int32_t *__restrict__ col, int64_t n, KernelParams kp, const double *__restrict__ B64,
-           const double *__restrict__ s64, double *__restrict__ val64)
+           const double *__restrict__ s64, double *__restrict__ val64, float *__restrict__ val32)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -346,6 +321,7 @@ k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowp
                 v = (phi * (S + kp.w0)) * (si * s64[j]);
             }
             val64[p] = v;
+            if (val32) val32[p] = (float)v;   // the FP32 copy is the FP64 value rounded once
         }
     }
 }
@@ -446,6 +422,116 @@ KernelParams make_kernel_params(const gp2s_hyper *h)
     return kp;
 }
 
+// Order-independent 64-bit fingerprint of X (n x d FP64): the sum over elements of a SplitMix64-style
+// mix of (bits, position), so equal inputs give equal hashes whatever the thread schedule.
+__global__ void k_hash_x(const double *__restrict__ X, int64_t cnt, unsigned long long *__restrict__ out)
+{
+    unsigned long long acc = 0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long z = (unsigned long long)__double_as_longlong(X[e]) + 0x9E3779B97F4A7C15ull * (unsigned long long)(e + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        acc += z ^ (z >> 31);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+static gp2s_status hash_x(gp2s_ctx *c, const double *X, int64_t cnt, uint64_t *hash)
+{
+    GP2S_TRY(ensure(c, c->counters, 256));
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(c->counters.as<char>() + 160);
+    GP2S_CUDA(c, cudaMemsetAsync(acc, 0, sizeof(unsigned long long), c->stream));
+    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cnt, 256), (int64_t)c->num_sms * 8));
+    k_hash_x<<<gb, 256, 0, c->stream>>>(X, cnt, acc);
+    GP2S_LAUNCH(c);
+    unsigned long long h = 0;
+    GP2S_CUDA(c, cudaMemcpyAsync(&h, acc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    *hash = h;
+    return GP2S_OK;
+}
+
+template <int D>
+static void launch_bumps(gp2s_ctx *c, int64_t n, const KernelParams &kp, int *dbad)
+{
+    const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
+    k_bumps<D><<<gb, 256, 0, c->stream>>>(c->Xs64.as<double4_16a>(), n, kp, c->B64.as<double>(), c->B32.as<float>(),
+                                          c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad);
+}
+
+template <int D>
+static void launch_values(gp2s_ctx *c, int64_t n, const KernelParams &kp, bool mixed)
+{
+    const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 32);
+    k_values64<D><<<gb, 256, 0, c->stream>>>(c->Xs64.as<double4_16a>(), c->rowptr.as<int32_t>(), c->col.as<int32_t>(), n,
+                                             kp, c->B64.as<double>(), c->s64.as<double>(), c->val64.as<double>(),
+                                             mixed ? c->val32.as<float>() : nullptr);
+}
+
+// Bump tables (FP64 and FP32), the diagonal and the Jacobi scales of the current points.
+static gp2s_status bumps_and_checks(gp2s_ctx *c, int64_t n, int d, const KernelParams &kp, int *dbad)
+{
+    switch (d) {
+    case 1: launch_bumps<1>(c, n, kp, dbad); break;
+    case 2: launch_bumps<2>(c, n, kp, dbad); break;
+    case 3: launch_bumps<3>(c, n, kp, dbad); break;
+    default: launch_bumps<4>(c, n, kp, dbad); break;
+    }
+    GP2S_LAUNCH(c);
+    return GP2S_OK;
+}
+
+// The values of every stored pair of the current pattern.
+static gp2s_status values_pass(gp2s_ctx *c, int64_t n, int d, const KernelParams &kp, bool mixed)
+{
+    switch (d) {
+    case 1: launch_values<1>(c, n, kp, mixed); break;
+    case 2: launch_values<2>(c, n, kp, mixed); break;
+    case 3: launch_values<3>(c, n, kp, mixed); break;
+    default: launch_values<4>(c, n, kp, mixed); break;
+    }
+    GP2S_LAUNCH(c);
+    return GP2S_OK;
+}
+
+// Same points and the same r as the last assembly: the pattern (and the sorted points, the cell
+// table and the CSR structure) depend on nothing else, so only the bump tables, the diagonal and
+// the values are recomputed for the new hyperparameters (the "pattern cached" evaluation).
+static gp2s_status refresh_values(gp2s_ctx *c, const gp2s_hyper *h, const gp2s_opts *o)
+{
+    Assembled &A = c->A;
+    const int64_t n = A.n;
+    const int d = A.d;
+    cudaEvent_t ev[2];
+    for (int k = 0; k < 2; ++k) GP2S_CUDA(c, cudaEventCreate(&ev[k]));
+    struct EvGuard { cudaEvent_t *e; ~EvGuard() { for (int k = 0; k < 2; ++k) cudaEventDestroy(e[k]); } } guard{ev};
+    GP2S_CUDA(c, cudaEventRecord(ev[0], c->stream));
+    const KernelParams kp = make_kernel_params(h);
+    GP2S_TRY(ensure(c, c->counters, 256));
+    int *dbad = c->counters.as<int>();
+    GP2S_CUDA(c, cudaMemsetAsync(dbad, 0, sizeof(int), c->stream));
+    GP2S_TRY(bumps_and_checks(c, n, d, kp, dbad));
+    GP2S_TRY(values_pass(c, n, d, kp, o->precision == GP2S_PREC_MIXED));
+    GP2S_CUDA(c, cudaEventRecord(ev[1], c->stream));
+    int hbad = 0;
+    GP2S_CUDA(c, cudaMemcpyAsync(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hbad) {
+        c->pat_valid = false;
+        return set_err(c, GP2S_ENOTPD, "a diagonal entry of A is zero (sigma2 = 0 and the point lies outside every bump, w0 = 0)");
+    }
+    gp2s_assemble_info &info = A.info;
+    info.ms_geometry = info.ms_count = info.ms_fill = 0.0f;
+    cudaEventElapsedTime(&info.ms_values64, ev[0], ev[1]);
+    info.pattern_reused = 1;
+    A.kp = kp;
+    A.opts = *o;
+    A.valid = true;
+    return GP2S_OK;
+}
+
 gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const gp2s_hyper *h,
                              const gp2s_opts *o)
 {
@@ -457,6 +543,14 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     c->rb_valid = false;
     c->bj_valid = false;
     const int d = h->d;
+    uint64_t xhash = 0;
+    GP2S_TRY(hash_x(c, X_dev, n * d, &xhash));
+    if (o->pattern_cache == 0 && c->pat_valid && c->pat_n == n && c->pat_d == d &&
+        std::memcmp(&c->pat_r, &h->r, sizeof(double)) == 0 && c->pat_exact == o->exact_support &&
+        c->pat_precision == o->precision && c->pat_hash == xhash)
+        return refresh_values(c, h, o);
+    c->pat_valid = false;
+    c->rb_pattern_valid = false;
     cudaEvent_t ev[5];
     for (int k = 0; k < 5; ++k) GP2S_CUDA(c, cudaEventCreate(&ev[k]));
     struct EvGuard { cudaEvent_t *e; ~EvGuard() { for (int k = 0; k < 5; ++k) cudaEventDestroy(e[k]); } } guard{ev};
@@ -532,18 +626,7 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     unsigned long long *stats = reinterpret_cast<unsigned long long *>(c->counters.as<char>() + 64);
     int *mm = reinterpret_cast<int *>(c->counters.as<char>() + 128);
     GP2S_CUDA(c, cudaMemsetAsync(c->counters.p, 0, 256, c->stream));
-    {
-        unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
-        const double4_16a *x64 = c->Xs64.as<double4_16a>();
-        double *B64 = c->B64.as<double>();
-        switch (d) {
-        case 1: k_bumps<1><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
-        case 2: k_bumps<2><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
-        case 3: k_bumps<3><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
-        default: k_bumps<4><<<gb, 256, 0, c->stream>>>(x64, n, kp, B64, c->B32.as<float>(), c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad); break;
-        }
-        GP2S_LAUNCH(c);
-    }
+    GP2S_TRY(bumps_and_checks(c, n, d, kp, dbad));
     GP2S_CUDA(c, cudaEventRecord(ev[1], c->stream));
 
     // ---- count -> scan ----
@@ -578,25 +661,11 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     GP2S_TRY(ensure(c, c->val64, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1)));
     a.rowptr = c->rowptr.as<int32_t>();
     a.col = c->col.as<int32_t>();
-    a.val = mixed ? c->val32.as<float>() : nullptr;
     if (nitems > 0) GP2S_TRY(dispatch_assemble<true>(c, d, a, g, sp, kp, nitems));
     GP2S_CUDA(c, cudaEventRecord(ev[3], c->stream));
 
-    // ---- FP64 values ----
-    {
-        unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 32);
-        const double4_16a *x64 = c->Xs64.as<double4_16a>();
-        const int32_t *rp = c->rowptr.as<int32_t>(), *cl = c->col.as<int32_t>();
-        const double *B64 = c->B64.as<double>(), *s64 = c->s64.as<double>();
-        double *v64 = c->val64.as<double>();
-        switch (d) {
-        case 1: k_values64<1><<<gb, 256, 0, c->stream>>>(x64, rp, cl, n, kp, B64, s64, v64); break;
-        case 2: k_values64<2><<<gb, 256, 0, c->stream>>>(x64, rp, cl, n, kp, B64, s64, v64); break;
-        case 3: k_values64<3><<<gb, 256, 0, c->stream>>>(x64, rp, cl, n, kp, B64, s64, v64); break;
-        default: k_values64<4><<<gb, 256, 0, c->stream>>>(x64, rp, cl, n, kp, B64, s64, v64); break;
-        }
-        GP2S_LAUNCH(c);
-    }
+    // ---- values: every stored pair in FP64 (and its FP32 rounding in MIXED precision) ----
+    GP2S_TRY(values_pass(c, n, d, kp, mixed));
     GP2S_CUDA(c, cudaEventRecord(ev[4], c->stream));
     {
         int init[2] = {INT32_MAX, 0};
@@ -639,6 +708,13 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     A.sp = sp;
     A.opts = *o;
     A.valid = true;
+    c->pat_valid = true;
+    c->pat_n = n;
+    c->pat_d = d;
+    c->pat_r = h->r;
+    c->pat_exact = o->exact_support;
+    c->pat_precision = o->precision;
+    c->pat_hash = xhash;
     return GP2S_OK;
 }
 

@@ -165,6 +165,7 @@ static gp2s_status validate_opts(gp2s_ctx *c, const gp2s_opts *o)
     if (!(o->tol_inner > 0.0) || !(o->tol_refine > 0.0) || !(o->tol_probe > 0.0)) return set_err(c, GP2S_EINVAL, "tolerances must be > 0");
     if (o->max_outer < 0) return set_err(c, GP2S_EINVAL, "max_outer must be >= 0");
     if (o->precond < 0 || o->precond > 2) return set_err(c, GP2S_EINVAL, "precond must be 0, 1 or 2");
+    if (o->solver != GP2S_SOLVER_CG && o->solver != GP2S_SOLVER_MINRES) return set_err(c, GP2S_EINVAL, "unknown solver");
     if (o->bj_block != 0 && o->bj_block != 64 && o->bj_block != 128)
         return set_err(c, GP2S_EINVAL, "bj_block must be 0, 64 or 128");
     return GP2S_OK;
@@ -205,7 +206,7 @@ static gp2s_status do_assemble(gp2s_ctx *c, int64_t n, const double *X, const gp
 static gp2s_status do_solve(gp2s_ctx *c, int method, int m, CGResult *res)
 {
     const Assembled &A = c->A;
-    if (method == GP2S_LOGDET_EXACT && m == 0) {
+    if (method == GP2S_LOGDET_EXACT && m == 0 && A.opts.solver == GP2S_SOLVER_CG) {
         double ld = 0.0;
         GP2S_TRY(exact_logdet_solve(c, c->ys64.as<double>(), &ld, false));
         double rr = 0.0;
@@ -236,7 +237,7 @@ void gp2s_opts_default(gp2s_opts *o)
     o->probes = 64;
     o->lanczos_steps = 100;
     o->max_iter = 20000;
-    o->tol_inner = 1e-5;
+    o->tol_inner = 1e-6;
     o->tol_refine = 1e-8;
     o->tol_probe = 1e-5;
     o->seed = 0;
@@ -284,7 +285,8 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->val32, &c->val64, &c->counters, &c->vec, &c->vec64, &c->partials, &c->scal,
                       &c->Z, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
                       &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_tpart, &c->rb_seg,
-                      &c->bj_Minv, &c->bj_ld, &c->bj_Minv_y};
+                      &c->bj_Minv, &c->bj_ld, &c->bj_Minv_y, &c->post_X, &c->post_B, &c->post_cnt,
+                      &c->post_part, &c->mr_vec, &c->mc_X, &c->mc_y};
     for (DevBuf *b : bufs) free_buf(*b);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (gp2s_ctx *w : c->workers) gp2s_destroy(w);
@@ -476,6 +478,7 @@ static gp2s_status lml_impl(gp2s_ctx *c, int64_t n, const double *X, const doubl
         info->ms_spmm = (float)c->prof_ms;
         info->bj_block = (A.precision == GP2S_PREC_MIXED && A.opts.precond == 2 && c->bj_valid) ? c->bj_size : 0;
         info->spmm_seg_tiles = c->spmm_seg_tiles;
+        info->pattern_reused = A.info.pattern_reused;
     }
     c->profile = false;
     return GP2S_OK;
@@ -492,6 +495,34 @@ gp2s_status gp2s_lml_batched(gp2s_ctx *c, int32_t B, const int64_t *n, const dou
                              double *lml_host, gp2s_lml_info *info_host)
 {
     return batched_lml(c, B, n, X, y, hyper, opts, lml_host, info_host);
+}
+
+gp2s_status gp2s_mcmc(gp2s_ctx *c, int64_t n, const double *X, const double *y, const gp2s_hyper *h0,
+                      const gp2s_opts *o, const gp2s_mcmc_opts *mo, double *chain, int32_t *accept,
+                      gp2s_mcmc_info *info)
+{
+    if (!c) return GP2S_EINVAL;
+    c->err.clear();
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "cudaSetDevice");
+    gp2s_opts def;
+    if (!o) { gp2s_opts_default(&def); o = &def; }
+    GP2S_TRY(validate_hyper(c, h0));
+    GP2S_TRY(validate_opts(c, o));
+    if (!X || !y) return set_err(c, GP2S_EINVAL, "X / y is NULL");
+    // host inputs are staged once for the whole chain
+    const void *xd = nullptr, *yd = nullptr;
+    GP2S_TRY(stage_in(c, c->mc_X, X, sizeof(double) * (size_t)n * h0->d, &xd));
+    GP2S_TRY(stage_in(c, c->mc_y, y, sizeof(double) * (size_t)n, &yd));
+    return mcmc_run(c, n, (const double *)xd, (const double *)yd, h0, o, mo, chain, accept, info);
+}
+
+gp2s_status gp2s_posterior(gp2s_ctx *c, int64_t n_test, const double *Xtest, double *mean, double *var,
+                           gp2s_posterior_info *info)
+{
+    if (!c) return GP2S_EINVAL;
+    c->err.clear();
+    if (cudaSetDevice(c->device) != cudaSuccess) return cuda_err(c, cudaGetLastError(), "cudaSetDevice");
+    return posterior(c, n_test, Xtest, mean, var, info);
 }
 
 gp2s_status gp2s_lml_grad(gp2s_ctx *c, int64_t n, const double *X, const double *y, const gp2s_hyper *h,

@@ -117,9 +117,23 @@ struct gp2s_ctx {
     gp2s::DevBuf dense;
     // adjoint
     gp2s::DevBuf H, gpart;
+    // posterior (test points, their bump values / prior variances / outputs, counters, partials)
+    gp2s::DevBuf post_X, post_B, post_cnt, post_part;
+    // MINRES vectors and scalars
+    gp2s::DevBuf mr_vec;
+    // MCMC driver: the chain's inputs staged once
+    gp2s::DevBuf mc_X, mc_y;
     // host staging
     gp2s::HostPinned hbuf;
     gp2s::Assembled A;
+    // pattern cache: the last assembly's points (fingerprint), size and support radius; a later
+    // assembly with the same ones reuses the pattern and recomputes only the values
+    bool pat_valid = false;
+    int64_t pat_n = 0;
+    int pat_d = 0, pat_exact = 0, pat_precision = 0;
+    double pat_r = 0.0;
+    uint64_t pat_hash = 0;
+    bool rb_pattern_valid = false;   // the RB8 union structure matches the current pattern
     // last solve
     bool have_solution = false;
     bool have_probes = false;
@@ -191,6 +205,14 @@ struct CGResult {
 gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_probes, int m,
                          int ksteps, CGResult *res);
 gp2s_status slq_logdet(gp2s_ctx *c, int m, int ksteps, double *logdet_hat, double *stderr_hat);
+// FP64 MINRES on Ah (minres.cu): b (device, sorted order) -> x, until |b - Ah x| <= tol |b|.
+gp2s_status minres_solve(gp2s_ctx *c, const double *b, double *x, double tol, int maxit, int *steps);
+// Multi-RHS (P)CG on caller-supplied columns (no y column, no SLQ records): krylov_columns_buffers
+// gives the probe group's right-hand-side block rz (n x m, row-major, vector precision of the
+// assembled problem) to fill, and its solution block xz; krylov_columns_solve then runs the
+// columns to relative residual tol (xz: solutions, rz: final recursively updated residuals).
+gp2s_status krylov_columns_buffers(gp2s_ctx *c, int m, void **rz, void **xz);
+gp2s_status krylov_columns_solve(gp2s_ctx *c, int m, double tol, int *iters);
 gp2s_status exact_logdet_solve(gp2s_ctx *c, const double *y_sorted_dev, double *logdet_hat,
                                bool want_inverse);
 // Reductions used by several stages
@@ -199,6 +221,15 @@ gp2s_status dot_f64(gp2s_ctx *c, const double *a, const double *b, int64_t n, do
 
 // Adjoint (adjoint.cu) ---------------------------------------------------------------------------
 gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host);
+
+// Posterior (posterior.cu) -------------------------------------------------------------------
+gp2s_status posterior(gp2s_ctx *c, int64_t ns, const double *Xs, double *mean, double *var,
+                      gp2s_posterior_info *info);
+
+// Block Metropolis-Hastings driver (mcmc.cu) ----------------------------------------------------
+gp2s_status mcmc_run(gp2s_ctx *c, int64_t n, const double *X, const double *y, const gp2s_hyper *h0,
+                     const gp2s_opts *o, const gp2s_mcmc_opts *mo, double *chain, int32_t *accept,
+                     gp2s_mcmc_info *info);
 
 // Batched engine (batched.cu) ----------------------------------------------------------------
 gp2s_status batched_lml(gp2s_ctx *c, int32_t B, const int64_t *n, const double *const *X,

@@ -1523,14 +1523,18 @@ gp2s_status build_rb8(gp2s_ctx *c)
     const Assembled &A = c->A;
     const int64_t n = A.n;
     const int64_t nblk = ceil_div(n, kRB);
-    GP2S_TRY(ensure(c, c->rb_cnt, sizeof(int32_t) * (size_t)(nblk + 1)));
-    GP2S_TRY(ensure(c, c->rb_ptr, sizeof(int32_t) * (size_t)(nblk + 1)));
     const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(nblk * 32, 256), 152 * 16);
-    k_rb_build<false><<<gb, 256, 0, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val32.as<float>(),
-                                                 n, nblk, c->rb_cnt.as<int32_t>(), nullptr, nullptr, nullptr);
-    GP2S_LAUNCH(c);
-    int64_t nu = 0;
-    GP2S_TRY(scan_counts_i32(c, c->rb_cnt.as<int32_t>(), c->rb_ptr.as<int32_t>(), nblk, &nu));
+    int64_t nu = c->rb_entries;
+    if (!c->rb_pattern_valid) {
+        // the union structure depends on the pattern only: counted once per pattern
+        GP2S_TRY(ensure(c, c->rb_cnt, sizeof(int32_t) * (size_t)(nblk + 1)));
+        GP2S_TRY(ensure(c, c->rb_ptr, sizeof(int32_t) * (size_t)(nblk + 1)));
+        k_rb_build<false><<<gb, 256, 0, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(),
+                                                     c->val32.as<float>(), n, nblk, c->rb_cnt.as<int32_t>(), nullptr,
+                                                     nullptr, nullptr);
+        GP2S_LAUNCH(c);
+        GP2S_TRY(scan_counts_i32(c, c->rb_cnt.as<int32_t>(), c->rb_ptr.as<int32_t>(), nblk, &nu));
+    }
     GP2S_TRY(ensure(c, c->rb_col, sizeof(int32_t) * (size_t)(nu + 1)));
     GP2S_TRY(ensure(c, c->rb_val, sizeof(float) * kRB * (size_t)(nu + 1)));
     k_rb_build<true><<<gb, 256, 0, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->val32.as<float>(),
@@ -1544,6 +1548,7 @@ gp2s_status build_rb8(gp2s_ctx *c)
     GP2S_CUDA(c, cudaMemsetAsync(c->rb_seg.p, 0, sizeof(int) * kMaxPartBlocks, c->stream));
     c->rb_entries = nu;
     c->rb_valid = true;
+    c->rb_pattern_valid = true;
     return GP2S_OK;
 }
 
@@ -1831,6 +1836,61 @@ gp2s_status y_residual(gp2s_ctx *c, const double *y_sorted_dev, double *relres)
     return GP2S_OK;
 }
 
+// Layout of the Krylov vectors in c->vec: probe group x, r, p, q (n x m each), y group x, r, p, q
+// (n each), then z of the y column and z of the probe group (block-Jacobi PCG).
+static gp2s_status cg_layout(gp2s_ctx *c, int mm, CGBuffers *B)
+{
+    const int64_t n = c->A.n;
+    const size_t es = c->A.precision == GP2S_PREC_MIXED ? sizeof(float) : sizeof(double);
+    GP2S_TRY(ensure(c, c->vec, es * (size_t)n * (5 + 5 * (size_t)mm) + 256));
+    char *base = c->vec.as<char>();
+    size_t nz = es * (size_t)n * mm;
+    B->xz = base; B->rz = base + nz; B->pz = base + 2 * nz; B->qz = base + 3 * nz;
+    char *yb = base + 4 * nz;
+    B->xy = yb; B->ry = yb + es * n; B->py = yb + 2 * es * n; B->qy = yb + 3 * es * n;
+    B->zz = yb + 4 * es * n;
+    B->zy = (char *)B->zz + nz;
+    return GP2S_OK;
+}
+
+gp2s_status krylov_columns_buffers(gp2s_ctx *c, int m, void **rz, void **xz)
+{
+    CGBuffers B;
+    GP2S_TRY(cg_layout(c, m, &B));
+    *rz = B.rz;
+    *xz = B.xz;
+    return GP2S_OK;
+}
+
+gp2s_status krylov_columns_solve(gp2s_ctx *c, int m, double tol, int *iters)
+{
+    Assembled &A = c->A;
+    const int64_t n = A.n;
+    const bool mixed = A.precision == GP2S_PREC_MIXED;
+    CGBuffers B;
+    GP2S_TRY(cg_layout(c, m, &B));
+    if (mixed && A.opts.precond == 2 && !c->bj_valid) GP2S_TRY(build_block_jacobi(c));
+    if (mixed && !c->rb_valid) GP2S_TRY(build_rb8(c));
+    GP2S_TRY(ensure_host(c, c->hbuf, 4096));
+    // the y column is idle: a zero right-hand side leaves it inactive from the first step
+    GP2S_TRY(ensure(c, c->vec64, sizeof(double) * (size_t)n * 4 + 256));
+    double *zero = c->vec64.as<double>();   // slot 0 (the refinement's b), free after the solve
+    GP2S_CUDA(c, cudaMemsetAsync(zero, 0, sizeof(double) * n, c->stream));
+    int iy = 0, iz = 0;
+    bool brk = false;
+    if (mixed)
+        GP2S_TRY((cg_run<float, float>(c, m, c->val32.as<float>(), B, zero, 1.0, tol, 0, 0, nullptr, A.opts.max_iter,
+                                       &iy, &iz, &brk)));
+    else
+        GP2S_TRY((cg_run<double, double>(c, m, c->val64.as<double>(), B, zero, 1.0, tol, 0, 0, nullptr,
+                                         A.opts.max_iter, &iy, &iz, &brk)));
+    c->have_probes = false;
+    *iters = iz;
+    if (brk) return set_err(c, GP2S_EBREAKDOWN, "CG breakdown in a posterior-variance solve");
+    if (iz >= A.opts.max_iter) return set_err(c, GP2S_ENOCONV, "posterior-variance solve hit max_iter");
+    return GP2S_OK;
+}
+
 gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_probes, int m, int ksteps,
                          CGResult *res)
 {
@@ -1838,18 +1898,9 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
     const int64_t n = A.n;
     if (!with_probes) m = 0;
     const bool mixed = A.precision == GP2S_PREC_MIXED;
-    const size_t es = mixed ? sizeof(float) : sizeof(double);
     const int mm = m > 0 ? m : 0;
-    // vectors: y group 4 n, probe group 4 n m
-    GP2S_TRY(ensure(c, c->vec, es * (size_t)n * (5 + 5 * (size_t)mm) + 256));
     CGBuffers B;
-    char *base = c->vec.as<char>();
-    size_t nz = es * (size_t)n * mm;
-    B.xz = base; B.rz = base + nz; B.pz = base + 2 * nz; B.qz = base + 3 * nz;
-    char *yb = base + 4 * nz;
-    B.xy = yb; B.ry = yb + es * n; B.py = yb + 2 * es * n; B.qy = yb + 3 * es * n;
-    B.zz = yb + 4 * es * n;
-    B.zy = (char *)B.zz + nz;
+    GP2S_TRY(cg_layout(c, mm, &B));
     // block-Jacobi preconditioner (FP32 path, opts.precond == 2)
     if (mixed && A.opts.precond == 2 && !c->bj_valid) GP2S_TRY(build_block_jacobi(c));
     // FP64 refinement vectors: b64, xhat64, res64, a64 (solution in sorted order)
@@ -1880,6 +1931,50 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
     const double tol_z = c->probes_for_grad ? o.tol_probe : 1.0;
     int iy = 0, iz = 0;
     bool brk = false;
+    if (o.solver == GP2S_SOLVER_MINRES) {
+        // the probe columns run CG beside an idle y column (zero right-hand side) ...
+        if (mm > 0) {
+            GP2S_CUDA(c, cudaMemsetAsync(r64, 0, sizeof(double) * n, c->stream));
+            if (mixed)
+                GP2S_TRY((cg_run<float, float>(c, mm, c->val32.as<float>(), B, r64, 1.0, tol_z, ksteps, ksteps, rec,
+                                               o.max_iter, &iy, &iz, &brk)));
+            else
+                GP2S_TRY((cg_run<double, double>(c, mm, c->val64.as<double>(), B, r64, 1.0, tol_z, ksteps, ksteps, rec,
+                                                 o.max_iter, &iy, &iz, &brk)));
+            if (brk) return set_err(c, GP2S_EBREAKDOWN, "CG breakdown in a probe column");
+        }
+        // ... and the y column is MINRES's: FP64 on Ah, restarted on the FP64 residual
+        int st = 0, total = 0, outer = 0;
+        double relres = 0.0;
+        GP2S_TRY(minres_solve(c, b64, xh, 0.1 * o.tol_refine, o.max_iter, &st));
+        total += st;
+        for (;;) {
+            GP2S_TRY(y_residual(c, y_sorted_dev, &relres));
+            if (!(relres > o.tol_refine) || outer >= o.max_outer) break;
+            ++outer;
+            GP2S_TRY(minres_solve(c, r64, a64, std::min(0.5, 0.1 * o.tol_refine / relres), o.max_iter, &st));
+            total += st;
+            k_accum64<double><<<gbn, 256, 0, c->stream>>>(n, a64, xh);
+            GP2S_LAUNCH(c);
+        }
+        k_scale64<<<gbn, 256, 0, c->stream>>>(n, c->s64.as<double>(), xh, a64);
+        GP2S_LAUNCH(c);
+        res->iters_y = total;
+        res->iters_probes = iz;
+        res->outer = outer;
+        res->relres = relres;
+        c->have_solution = true;
+        c->have_probes = mm > 0;
+        c->solve_iters = total;
+        c->solve_outer = outer;
+        c->solve_relres = relres;
+        c->probe_iters = iz;
+        if (relres > o.tol_refine) {
+            res->status = GP2S_ENOCONV;
+            return set_err(c, GP2S_ENOCONV, "MINRES did not reach tol_refine within max_outer restarts");
+        }
+        return GP2S_OK;
+    }
     if (mixed)
         GP2S_TRY((cg_run<float, float>(c, mm, c->val32.as<float>(), B, b64, tol_first, tol_z, mm > 0 ? ksteps : 0,
                                        ksteps, rec, o.max_iter, &iy, &iz, &brk)));

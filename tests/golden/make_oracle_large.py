@@ -16,6 +16,8 @@ Cases (Sec. 3 LML, SLQ log-determinant and Hutchinson gradient with identical Ra
   clusters_3d_150k_t{0,1}  150,000 points of the same generator, the base and one drawn set
   sphere_4d_150k           150,000 points of the 4-D sphere x time x elevation generator
                            (60 entries per row), 32 probes x 100 steps
+  sphere_4d_10m            the full 10,000,000-point workload of that generator (about 600 M stored
+                           entries; the oracle's CG to 1e-8), 32 probes x 100 steps
 """
 import json
 import os
@@ -45,6 +47,8 @@ def cases():
                                       theta_index=0, probes=64, steps=100, seed=0)
     out["sphere_4d_150k"] = dict(workload="sphere_4d", n=150000, target=60.0, theta_set=None,
                                  theta_index=0, probes=32, steps=100, seed=0)
+    out["sphere_4d_10m"] = dict(workload="sphere_4d", n=10_000_000, target=60.0, theta_set=None,
+                                theta_index=0, probes=32, steps=100, seed=0, cg_tol=1e-8)
     return out
 
 
@@ -62,9 +66,10 @@ def run(name, spec):
     X, y, hyper = inputs(spec)
     h = oracle.Hyper(**hyper)
     t0 = time.time()
-    s = oracle.lml_slq(X, y, h, m=spec["probes"], k=spec["steps"], seed=spec["seed"], tol=CG_TOL)
+    tol = spec.get("cg_tol", CG_TOL)
+    s = oracle.lml_slq(X, y, h, m=spec["probes"], k=spec["steps"], seed=spec["seed"], tol=tol)
     rec = {
-        "case": name, **spec, "cg_tol": CG_TOL, "oracle_threads": oracle.num_threads(),
+        "case": name, **spec, "cg_tol": tol, "oracle_threads": oracle.num_threads(),
         "oracle_seconds": round(time.time() - t0, 1),
         "checksums": W.checksums(X, y),
         "hyper": {"d": hyper["d"], "r": hyper["r"], "sigma2": hyper["sigma2"], "beta": hyper["beta"],
