@@ -464,10 +464,13 @@ __global__ void k_update(int64_t n, int m, T *__restrict__ xz, T *__restrict__ r
 
 // p = r + beta p for active columns.  CTAs [0, gz) cover the probe group: thread t owns the four
 // columns 4 (t % (m/4)) .. +3 for the whole launch (beta and the active flags stay in registers)
-// and strides over rows; the remaining CTAs cover the y column.
+// and strides over rows; the remaining CTAs cover the y column.  With upd_x the probe group's
+// x += alpha p (alpha of this iteration, 0 for a column that was already idle) is applied first,
+// from the same read of p (the asynchronous block-Jacobi step leaves x to this kernel).
 template <class T>
 __global__ void k_direction(int64_t n, int m, const T *__restrict__ rz, T *__restrict__ pz, const T *__restrict__ ry,
-                            T *__restrict__ py, const double *__restrict__ sc, const int *__restrict__ active, int gz)
+                            T *__restrict__ py, const double *__restrict__ sc, const int *__restrict__ active, int gz,
+                            T *__restrict__ xz, int upd_x)
 {
     if ((int)blockIdx.x < gz) {
         const int cgs = m / 4;
@@ -475,12 +478,13 @@ __global__ void k_direction(int64_t n, int m, const T *__restrict__ rz, T *__res
         if ((int)threadIdx.x >= cgs * rows_per_step) return;
         const int cg = threadIdx.x % cgs;
         const int c0 = cg * 4;
-        T b[4];
+        T b[4], al[4];
         bool act[4], all = true;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             act[q] = active[c0 + q + 1] != 0;
             b[q] = (T)sc[(c0 + q + 1) * kScal + S_BETA];
+            al[q] = (T)sc[(c0 + q + 1) * kScal + S_ALPHA];
             all = all && act[q];
         }
         for (int64_t i = (int64_t)blockIdx.x * rows_per_step + threadIdx.x / cgs; i < n;
@@ -489,6 +493,13 @@ __global__ void k_direction(int64_t n, int m, const T *__restrict__ rz, T *__res
             T r4[4], p4[4];
             load_k<T, 4>(rz + e, r4);
             load_k<T, 4>(pz + e, p4);
+            if (upd_x) {
+                T x4[4];
+                load_k<T, 4>(xz + e, x4);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) x4[q] = x4[q] + al[q] * p4[q];
+                store_k<T, 4>(xz + e, x4);
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) p4[q] = (all || act[q]) ? r4[q] + b[q] * p4[q] : p4[q];
             store_k<T, 4>(pz + e, p4);
@@ -1440,6 +1451,209 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Probe-group PCG update with the bulk-copy engine: r -= alpha q, z = M^{-1} r and the partial
+// dots r^T z, r^T r on BJ-row blocks (x += alpha p is done by the direction kernel).  One
+// persistent CTA per SM takes blocks b = blockIdx.x + k gridDim.x; two shared-memory stages hold
+// M^{-1}_b (BJ x BJ) and r_b (BJ x m, contiguous in the row-major probe block), filled by
+// cp.async.bulk copies that one thread issues for block k + 2 as soon as block k has released the
+// stage, so the HBM reads of later blocks run under the product of the current one.  q of the
+// next block is prefetched into registers.  Every wait on a stage's mbarrier is bounded: after
+// about a second without the copy completing the kernel sets err and returns.
+// ---------------------------------------------------------------------------------------------
+constexpr int kPPThreads = 512;
+constexpr uint32_t kPPMaxSpins = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of bar; false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t spin = 0; spin < kPPMaxSpins; ++spin) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (spin > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+template <int BJ, int M>
+size_t pp_smem()
+{
+    return sizeof(float) * 2 * ((size_t)BJ * BJ + (size_t)BJ * M) + 64;
+}
+
+template <int BJ, int M>
+__global__ void __launch_bounds__(kPPThreads, 1)
+k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__restrict__ rz,
+           const float *__restrict__ qz, float *__restrict__ zz, const double *__restrict__ sc,
+           double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride, int *__restrict__ err)
+{
+    constexpr int CG = M / 4;                  // column groups of four
+    constexpr int NF4 = BJ * M / 4;            // float4 per residual block
+    constexpr int PER = NF4 / kPPThreads;      // float4 per thread
+    static_assert(NF4 % kPPThreads == 0 && kPPThreads % CG == 0, "block shape");
+    extern __shared__ __align__(128) unsigned char pp_sh[];
+    float *stage0 = reinterpret_cast<float *>(pp_sh);
+    float *stage1 = stage0 + BJ * BJ + BJ * M;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(stage1 + BJ * BJ + BJ * M);
+    const int tid = threadIdx.x;
+    const int cg = tid % CG;                   // this thread's four columns, in every phase
+    float a4[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a4[q] = (float)sc[(cg * 4 + q + 1) * kScal + S_ALPHA];
+    double drz[4] = {0.0, 0.0, 0.0, 0.0}, drr[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t nmine = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    auto issue = [&](int64_t k) {
+        const int64_t b = blockIdx.x + k * gridDim.x;
+        float *st = (k & 1) ? stage1 : stage0;
+        const int64_t i0 = b * BJ;
+        const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
+        const uint32_t mb = sizeof(float) * BJ * BJ, rb = sizeof(float) * (uint32_t)nb * M;
+        mbar_expect_tx(&bar[k & 1], mb + rb);
+        bulk_copy_g2s(st, Minv32 + b * BJ * BJ, mb, &bar[k & 1]);
+        bulk_copy_g2s(st + BJ * BJ, rz + i0 * M, rb, &bar[k & 1]);
+    };
+    auto load_q = [&](int64_t k, float4 (&q4)[PER]) {
+        const int64_t i0 = (blockIdx.x + k * gridDim.x) * BJ;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int e = tid + j * kPPThreads;
+            q4[j] = i0 + e / CG < n ? reinterpret_cast<const float4 *>(qz + i0 * M)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (nmine > 0) issue(0);
+        if (nmine > 1) issue(1);
+    }
+    float4 qn[PER];
+    if (nmine > 0) load_q(0, qn);
+    bool ok = true;
+    for (int64_t k = 0; k < nmine; ++k) {
+        float *MT = (k & 1) ? stage1 : stage0;
+        float *R = MT + BJ * BJ;
+        const int64_t i0 = (blockIdx.x + k * gridDim.x) * BJ;
+        const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
+        float4 qc[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) qc[j] = qn[j];
+        if (k + 1 < nmine) load_q(k + 1, qn);
+        if (!mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1))) {
+            ok = false;
+            break;
+        }
+        // r -= alpha q: in the stage, and back to the probe block; rows past the matrix are zero
+        float srr[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int e = tid + j * kPPThreads;
+            float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e / CG < nb) {
+                r4 = reinterpret_cast<const float4 *>(R)[e];
+                r4.x = r4.x - a4[0] * qc[j].x;
+                r4.y = r4.y - a4[1] * qc[j].y;
+                r4.z = r4.z - a4[2] * qc[j].z;
+                r4.w = r4.w - a4[3] * qc[j].w;
+                reinterpret_cast<float4 *>(rz + i0 * M)[e] = r4;
+                srr[0] = fmaf(r4.x, r4.x, srr[0]);
+                srr[1] = fmaf(r4.y, r4.y, srr[1]);
+                srr[2] = fmaf(r4.z, r4.z, srr[2]);
+                srr[3] = fmaf(r4.w, r4.w, srr[3]);
+            }
+            reinterpret_cast<float4 *>(R)[e] = r4;
+        }
+        __syncthreads();
+        // z = M^{-1} r (symmetric M^{-1}: its rows are its columns), written with r^T z
+        float srz[4] = {0.f, 0.f, 0.f, 0.f};
+        bj_tile_mm<BJ>(MT, R, M, [&](int it, int c0, float (&acc)[4][4]) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                if (it + a >= nb) continue;
+                *reinterpret_cast<float4 *>(zz + (i0 + it + a) * M + c0) =
+                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) srz[q] = fmaf(R[(it + a) * M + c0 + q], acc[a][q], srz[q]);
+            }
+        });
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            drz[q] += (double)srz[q];
+            drr[q] += (double)srr[q];
+        }
+        __syncthreads();   // the stage is free: refill it with block k + 2
+        if (tid == 0 && k + 2 < nmine) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(k + 2);
+        }
+    }
+    if (!ok) {
+        // a copy never completed: report, give the other stage's copy a bounded chance to land
+        // so that no copy still targets this CTA's shared memory, and leave
+        if (tid == 0) {
+            atomicExch(err, 1);
+            mbar_wait_bounded(&bar[0], 0);
+            mbar_wait_bounded(&bar[1], 0);
+        }
+        return;
+    }
+    // per-column partials of this CTA, summed in thread order
+    double *red = reinterpret_cast<double *>(stage0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        red[(size_t)tid * 8 + q] = drz[q];
+        red[(size_t)tid * 8 + 4 + q] = drr[q];
+    }
+    __syncthreads();
+    if (tid < M) {
+        const int g = tid / 4, q = tid % 4;
+        double s1 = 0.0, s2 = 0.0;
+        for (int t = g; t < kPPThreads; t += CG) {
+            s1 += red[(size_t)t * 8 + q];
+            s2 += red[(size_t)t * 8 + 4 + q];
+        }
+        part_rz[(int64_t)(tid + 1) * pstride + blockIdx.x] = s1;
+        part_rr[(int64_t)(tid + 1) * pstride + blockIdx.x] = s2;
+    }
+}
+
 // Dynamic shared memory of k_pc_step: the probe group stages the block's M^{-1} (BJ x BJ), the
 // BJ x m residual block and the (BJ / 4) x m partial dots; the y column stages kPCThreads
 // residuals (kPCThreads / BJ blocks of BJ rows).  The launch covers both.
@@ -1701,6 +1915,35 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         if (bjy == 128) GP2S_PCY_BJ(MODE, 128);                                                                     \
         else GP2S_PCY_BJ(MODE, 64);                                                                                 \
     } while (0)
+    // the probe group's UPDATE step on the bulk-copy pipelined kernel (FP32, m <= 64, 128-row
+    // blocks): one CTA per SM, x updated by the direction kernel.  With 64-row blocks the staged
+    // kernel at several CTAs per SM measured faster (sphere_4d at N = 10M: 2.60 against 2.72 s per
+    // evaluation), with 128-row blocks this one (clusters_3d at N = 1M: 1.78 against 1.85 s).
+    const bool pc_async = pc_avail && c->pc_async && m > 0 && m <= 64 && bjz == 128;
+    const int pga = (int)std::min<int64_t>(c->num_sms, nblkz);
+    int *dev_err = flags + 3;
+    if (pc_async) {
+        if (bjz == 128) {
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64>, pp_smem<128, 64>()));
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32>, pp_smem<128, 32>()));
+        } else {
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<64, 64>, pp_smem<64, 64>()));
+            GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<64, 32>, pp_smem<64, 32>()));
+        }
+    }
+    auto launch_pc_probe = [&](int mm) -> gp2s_status {
+        float *rzp = (float *)B.rz, *zzp = (float *)B.zz;
+        const float *qzp = (const float *)B.qz;
+#define GP2S_PP(BJ_, M_)                                                                                     \
+    k_pc_probe<BJ_, M_><<<pga, kPPThreads, pp_smem<BJ_, M_>(), c->stream>>>(n, nblkz, Minvz, rzp, qzp, zzp, sc, \
+                                                                           part, part_rr, pstride, dev_err)
+        if (bjz == 128 && mm == 64) GP2S_PP(128, 64);
+        else if (bjz == 128) GP2S_PP(128, 32);
+        else if (mm == 64) GP2S_PP(64, 64);
+        else GP2S_PP(64, 32);
+#undef GP2S_PP
+        return GP2S_OK;
+    };
     // initial state: probe group then y column
     if (m > 0) {
         if (pcz) GP2S_PCZ(PC_INIT, m);
@@ -1732,7 +1975,8 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         GP2S_LAUNCH(c);
         GP2S_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int) * 2, c->stream));
         if (mc > 0) {
-            if (pcz) GP2S_PCZ(PC_UPDATE, mc);
+            if (pcz && pc_async) GP2S_TRY(launch_pc_probe(mc));
+            else if (pcz) GP2S_PCZ(PC_UPDATE, mc);
             else k_update<T><<<nbz, ut, 0, c->stream>>>(n, m, (T *)B.xz, (T *)B.rz, (const T *)B.pz, (const T *)B.qz,
                                                          (T *)B.xy, (T *)B.ry, (const T *)B.py, (const T *)B.qy, sc,
                                                          part, pstride, nbz);
@@ -1743,8 +1987,9 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
                                                      (const T *)B.qz, (T *)B.xy, (T *)B.ry, (const T *)B.py,
                                                      (const T *)B.qy, sc, part, pstride, 0);
         GP2S_LAUNCH(c);
-        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, part_rr, pstride, pcy ? pgy : nby, pcz ? pgz : nbz, sc, active,
-                                               flags + 1, rec, ksteps, kmin_probe, pcy, pcz, lucky);
+        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, part_rr, pstride, pcy ? pgy : nby,
+                                               pcz ? (pc_async ? pga : pgz) : nbz, sc, active, flags + 1, rec, ksteps,
+                                               kmin_probe, pcy, pcz, lucky);
         GP2S_LAUNCH(c);
         {
             // direction: p = z + beta p (z = M^{-1} r for a preconditioned group, z = r otherwise)
@@ -1755,7 +2000,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
             const T *zzp = pcz ? (const T *)B.zz : (const T *)B.rz;
             const T *zyp = pcy ? (const T *)B.zy : (const T *)B.ry;
             k_direction<T><<<dgz + dgy, dthreads, 0, c->stream>>>(n, mc, zzp, (T *)B.pz, zyp, (T *)B.py, sc, active,
-                                                                 dgz);
+                                                                 dgz, (T *)B.xz, (pcz && pc_async) ? 1 : 0);
             GP2S_LAUNCH(c);
         }
         return GP2S_OK;
@@ -1785,9 +2030,10 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
                 GP2S_TRY(one_iter());
             }
         }
-        GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream));
+        GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
         GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
         GP2S_TRY(flush_profile(c));
+        if (hcount[3]) return set_err(c, GP2S_ETIMEOUT, "a block-Jacobi stage copy did not complete (bounded wait gave up)");
         if (hcount[1] == 0) break;
         if (mc > 0 && hcount[2] == 0) mc = 0;   // only the y column is left: y-only kernels
     }
