@@ -8,7 +8,9 @@ the order the paper states the method, using numpy / scipy library routines (Cho
 symmetric eigensolver, a k-d tree candidate search) as single steps.
 
 What each function follows:
-  * ``assemble``        -- Sec. 4.6: every pair is evaluated; A = K + sigma^2 I (Sec. 3).
+  * ``assemble``        -- Sec. 4.6: every pair is evaluated; A = K + sigma^2 I (Sec. 3), with the
+                           product kernel of Sec. 4.1 / 4.3 (family 0) or the Wendland
+                           convolution kernel of Eq. 6, Sec. 4.2 (family 1).
   * ``lml_exact``       -- the LML of Sec. 3 (Background) with m = 0, V = sigma^2 I, by a dense
                            Cholesky factorisation (solve and log-determinant exactly).
   * ``grad_exact``      -- the standard LML derivative 1/2 a^T dA a - 1/2 tr(A^{-1} dA) with the
@@ -62,7 +64,8 @@ class _Hyper(ctypes.Structure):
                 ("pad_", ctypes.c_int), ("r", ctypes.c_double), ("sigma2", ctypes.c_double),
                 ("beta", ctypes.c_double), ("w0", ctypes.c_double),
                 ("centers", ctypes.c_void_p), ("radii", ctypes.c_void_p),
-                ("amps", ctypes.c_void_p)]
+                ("amps", ctypes.c_void_p), ("family", ctypes.c_int), ("pad2_", ctypes.c_int),
+                ("ell", ctypes.c_void_p), ("G", ctypes.c_void_p)]
 
 
 def lib():
@@ -88,6 +91,9 @@ def lib():
             "orc_assemble_candidates": (i64, [i64, vp, hp, i64, vp, vp, vp, vp, vp]),
             "orc_dense_A": (None, [i64, vp, hp, vp]),
             "orc_cross_K": (None, [i64, vp, i64, vp, hp, vp]),
+            "orc_point_values": (None, [hp, i64, vp, vp]),
+            "orc_wc_q": (dbl, [i32, vp, vp, vp, vp]),
+            "orc_dphi_over_t": (dbl, [i32, i32, dbl]),
             "orc_spmm": (None, [i64, vp, vp, vp, i32, vp, vp]),
             "orc_cg": (i32, [i64, vp, vp, vp, i32, vp, vp, dbl, i32, i32, vp, vp, vp]),
             "orc_lanczos": (None, [i64, vp, vp, vp, i32, vp, i32, vp, vp, vp]),
@@ -121,6 +127,9 @@ class Hyper:
     beta: float = 1.0
     w0: float = 0.0
     kind: int = 0                # 0 = Wendland C2 reading, 1 = Eq. 3 C6
+    family: int = 0              # 0 = product kernel (Sec. 4.1 / 4.3), 1 = Wendland convolution (Eq. 6)
+    ell: np.ndarray | None = None   # family 1: d base length-scale factors
+    G: np.ndarray | None = None     # family 1: L x d weights of the length-scale field
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -129,28 +138,41 @@ class Hyper:
 
     @property
     def nparams(self) -> int:
+        if self.family == 1:
+            return self.L * (2 * self.d + 2) + self.d + 3
         return self.L * (self.d + 2) + 2
 
     def theta(self) -> np.ndarray:
-        """theta = [centers (L x d row-major), radii (L), amps (L), r, sigma2]."""
-        return np.concatenate([np.asarray(self.centers, np.float64).ravel(),
-                               np.asarray(self.radii, np.float64), np.asarray(self.amps, np.float64),
-                               [self.r, self.sigma2]])
+        """theta = [centers (L x d row-major), radii (L), amps (L), r, sigma2] (family 0), or
+        [centers, radii, amps, G (L x d), ell (d), w0, r, sigma2] (family 1)."""
+        head = [np.asarray(self.centers, np.float64).ravel(), np.asarray(self.radii, np.float64),
+                np.asarray(self.amps, np.float64)]
+        if self.family == 1:
+            head += [np.asarray(self.G, np.float64).ravel(), np.asarray(self.ell, np.float64), [self.w0]]
+        return np.concatenate(head + [[self.r, self.sigma2]])
 
     def with_theta(self, th) -> "Hyper":
         th = np.asarray(th, np.float64)
         L, d = self.L, self.d
-        return Hyper(d=d, centers=th[:L * d].reshape(L, d).copy(), radii=th[L * d:L * d + L].copy(),
-                     amps=th[L * d + L:L * d + 2 * L].copy(), r=float(th[-2]), sigma2=float(th[-1]),
-                     beta=self.beta, w0=self.w0, kind=self.kind)
+        kw = dict(d=d, centers=th[:L * d].reshape(L, d).copy(), radii=th[L * d:L * d + L].copy(),
+                  amps=th[L * d + L:L * d + 2 * L].copy(), r=float(th[-2]), sigma2=float(th[-1]),
+                  beta=self.beta, w0=self.w0, kind=self.kind, family=self.family)
+        if self.family == 1:
+            o = L * d + 2 * L
+            kw.update(G=th[o:o + L * d].reshape(L, d).copy(), ell=th[o + L * d:o + L * d + d].copy(),
+                      w0=float(th[o + L * d + d]))
+        return Hyper(**kw)
 
     def c(self):
         c = np.ascontiguousarray(np.asarray(self.centers, np.float64).reshape(self.L, self.d))
         rr = np.ascontiguousarray(np.asarray(self.radii, np.float64))
         aa = np.ascontiguousarray(np.asarray(self.amps, np.float64))
-        self._keep = [c, rr, aa]
+        ee = np.ascontiguousarray(np.asarray(self.ell if self.ell is not None else np.ones(self.d), np.float64))
+        gg = np.ascontiguousarray(np.asarray(self.G if self.G is not None else np.zeros((self.L, self.d)),
+                                             np.float64).reshape(self.L, self.d))
+        self._keep = [c, rr, aa, ee, gg]
         h = _Hyper(self.d, self.L, self.kind, 0, float(self.r), float(self.sigma2),
-                   float(self.beta), float(self.w0), _p(c), _p(rr), _p(aa))
+                   float(self.beta), float(self.w0), _p(c), _p(rr), _p(aa), int(self.family), 0, _p(ee), _p(gg))
         return ctypes.byref(h), h
 
 
@@ -249,8 +271,12 @@ def assemble(X, h: Hyper, method: str = "auto") -> CSR:
         return CSR(n, rowptr, col, val)
     if method == "tree":
         from scipy.spatial import cKDTree
-        # enlarged search radius: a superset of every pair with d2 < r*r in FP64
+        # enlarged search radius: a superset of every pair in the pattern (d2 < r*r; for the
+        # Wendland convolution Q < r*r needs |D| < r sqrt(max lambda))
         rs = float(h.r) * (1.0 + 1e-9) + 1e-300
+        if h.family == 1:
+            pv = point_values(X, h)
+            rs = float(h.r) * math.sqrt(float(pv[:, 1:].max())) * (1.0 + 1e-9) + 1e-300
         pairs = cKDTree(X).query_pairs(rs, output_type="ndarray").astype(np.int64)
         ci = np.ascontiguousarray(pairs[:, 0])
         cj = np.ascontiguousarray(pairs[:, 1])
@@ -261,6 +287,17 @@ def assemble(X, h: Hyper, method: str = "auto") -> CSR:
         L.orc_assemble_candidates(n, _p(X), hr, ci.shape[0], _p(ci), _p(cj), _p(rowptr), _p(col), _p(val))
         return CSR(n, rowptr, col, val)
     raise ValueError(method)
+
+
+def point_values(X, h: Hyper) -> np.ndarray:
+    """Per-point kernel quantities: the bump values (family 0, n x L) or [s, lambda_1..d]
+    (family 1, n x (d + 1))."""
+    X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, h.d))
+    w = h.d + 1 if h.family == 1 else h.L
+    out = np.empty((X.shape[0], max(w, 1)))
+    hr, _keep = h.c()
+    lib().orc_point_values(hr, X.shape[0], _p(X), _p(out))
+    return out
 
 
 def rows_brute(X, h: Hyper, rows) -> list:

@@ -50,6 +50,10 @@ typedef struct {
     const double *centers; /* L x d, row-major */
     const double *radii;   /* L */
     const double *amps;    /* L */
+    int family;            /* 0 = product kernel (Sec. 4.1 / 4.3), 1 = Wendland convolution (Eq. 6) */
+    int pad2_;
+    const double *ell;     /* family 1: d base length-scale factors */
+    const double *G;       /* family 1: L x d weights of the length-scale field */
 } orc_hyper;
 
 /* ------------------------------------------------------------------------------------ */
@@ -110,6 +114,20 @@ double orc_dphi(int kind, int d, double t)
     }
     if (d <= 3) return -20.0 * t * u * u * u;
     return -30.0 * t * u * u * u * u;
+}
+
+/* phi'(t) / t, finite at t = 0 (the derivative of each form carries a factor t). */
+double orc_dphi_over_t(int kind, int d, double t)
+{
+    if (!(t < 1.0)) return 0.0;
+    if (t < 0.0) t = 0.0;
+    double u = 1.0 - t;
+    if (kind == 1) {
+        double u2 = u * u, u4 = u2 * u2, u7 = u4 * u2 * u;
+        return -22.0 * u7 * (16.0 * t * t + 7.0 * t + 1.0);
+    }
+    if (d <= 3) return -20.0 * u * u * u;
+    return -30.0 * u * u * u * u;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -181,22 +199,119 @@ static double kernel_from_bumps(const orc_hyper *h, const double *xi, const doub
     return orc_phi(h->kind, h->d, t) * (s + h->w0);
 }
 
+
+
+/* ------------------------------------------------------------------------------------ */
+/* Wendland convolution kernel (Eq. 6, Sec. 4.2), family 1:                              */
+/*   k(xi, xj) = s(xi) s(xj) |S_i|^(1/4) |S_j|^(1/4) / |(S_i + S_j)/2|^(1/2) phi(sqrt(Q)/r0), */
+/*   Q = (xi - xj)^T ((S_i + S_j)/2)^{-1} (xi - xj),  support Q < r0^2.                    */
+/* The paper leaves the fields s (signal deviation) and S (length scale) parametric.      */
+/* Reading: S(x) = diag(lambda_1(x), .., lambda_d(x)) with                               */
+/*   lambda_k(x) = ell_k^2 + sum_l G_lk psi_l(x),   s(x) = w0 + sum_l a_l psi_l(x),       */
+/*   psi_l(x) = (1 - q_l / rho_l^2)^3 for q_l = |x - c_l|^2 < rho_l^2, else 0,            */
+/* a polynomial bump on the bumps' centers and radii.  With G = 0, ell = 1, a = 0, w0 = 1 */
+/* the kernel is Eq. 3's stationary Wendland taper.  Every step of lambda and Q is one    */
+/* FP64 round-to-nearest operation in the order written (the pattern depends on it).     */
+/* ------------------------------------------------------------------------------------ */
+static double wc_psi(const orc_hyper *h, int l, const double *x, double *s_out)
+{
+    const int d = h->d;
+    const double *c = h->centers + (size_t)l * d;
+    double q = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double dk = x[k] - c[k];
+        q = q + dk * dk;
+    }
+    double rho = h->radii[l];
+    double s = q / (rho * rho);
+    if (s_out) *s_out = s;
+    if (!(s < 1.0)) return 0.0;
+    double u = 1.0 - s;
+    return u * u * u;
+}
+
+/* [s(x), lambda_0(x), .., lambda_{d-1}(x)] */
+static void wc_point(const orc_hyper *h, const double *x, double *out)
+{
+    const int d = h->d, L = h->L;
+    double sig = 0.0, acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = 0; l < L; ++l) {
+        double psi = wc_psi(h, l, x, NULL);
+        sig = sig + h->amps[l] * psi;
+        for (int k = 0; k < d; ++k) acc[k] = acc[k] + h->G[(size_t)l * d + k] * psi;
+    }
+    out[0] = h->w0 + sig;
+    for (int k = 0; k < d; ++k) out[1 + k] = h->ell[k] * h->ell[k] + acc[k];
+}
+
+/* Q(i, j) = ((D0 D0 / m0 + D1 D1 / m1) + ...), m_k = (lambda_ik + lambda_jk) * 0.5 */
+double orc_wc_q(int d, const double *xi, const double *xj, const double *li, const double *lj)
+{
+    double q = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double dk = xi[k] - xj[k];
+        double m = (li[k] + lj[k]) * 0.5;
+        q = q + (dk * dk) / m;
+    }
+    return q;
+}
+
+static int point_width(const orc_hyper *h) { return h->family == 1 ? h->d + 1 : h->L; }
+
+static void point_values(const orc_hyper *h, const double *x, double *out)
+{
+    if (h->family == 1) wc_point(h, x, out);
+    else orc_bumps(h, x, out, NULL);
+}
+
+/* Pattern test of two distinct points (the diagonal is always stored). */
+static int pair_in(const orc_hyper *h, const double *xi, const double *xj, const double *pi, const double *pj)
+{
+    if (h->family == 1) return orc_wc_q(h->d, xi, xj, pi + 1, pj + 1) < h->r * h->r;
+    return orc_in_pattern(h->d, xi, xj, h->r);
+}
+
+/* Kernel value k(xi, xj) (no noise term) from the points' values. */
+static double pair_value(const orc_hyper *h, const double *xi, const double *xj, const double *pi, const double *pj)
+{
+    if (h->family != 1) return kernel_from_bumps(h, xi, xj, pi, pj);
+    const int d = h->d;
+    double q = orc_wc_q(d, xi, xj, pi + 1, pj + 1);
+    double pref = 1.0;
+    for (int k = 0; k < d; ++k) {
+        double li = pi[1 + k], lj = pj[1 + k];
+        pref = pref * sqrt(sqrt(li * lj)) / sqrt((li + lj) * 0.5);
+    }
+    return pi[0] * pj[0] * pref * orc_phi(h->kind, d, sqrt(q) / h->r);
+}
+
 double orc_kernel(const orc_hyper *h, const double *xi, const double *xj)
 {
     double bi[64], bj[64];
-    if (h->L > 64) return NAN;
-    orc_bumps(h, xi, bi, NULL);
-    orc_bumps(h, xj, bj, NULL);
-    return kernel_from_bumps(h, xi, xj, bi, bj);
+    if (point_width(h) > 64) return NAN;
+    point_values(h, xi, bi);
+    point_values(h, xj, bj);
+    return pair_value(h, xi, xj, bi, bj);
 }
 
-/* Bump table B (n x L): b_l(x_i) for every point (the definition evaluated once per point). */
+/* Per-point values for n points (n x point_width), for the pins and for choosing the
+ * k-d tree radius of the candidate search. */
+void orc_point_values(const orc_hyper *h, int64_t n, const double *X, double *out)
+{
+    const int w = point_width(h);
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) point_values(h, X + (size_t)i * h->d, out + (size_t)i * w);
+}
+
+/* Point table (n x point_width): the bump values b_l(x_i) (family 0) or [s, lambda] (family
+ * 1) of every point (the definition evaluated once per point). */
 static double *bump_table(int64_t n, const double *X, const orc_hyper *h)
 {
-    double *B = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(h->L > 0 ? h->L : 1));
+    const int w = point_width(h);
+    double *B = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(w > 0 ? w : 1));
     if (!B) return NULL;
     #pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) orc_bumps(h, X + (size_t)i * h->d, B + (size_t)i * h->L, NULL);
+    for (int64_t i = 0; i < n; ++i) point_values(h, X + (size_t)i * h->d, B + (size_t)i * w);
     return B;
 }
 
@@ -209,29 +324,30 @@ static double *bump_table(int64_t n, const double *X, const orc_hyper *h)
 int64_t orc_assemble_brute(int64_t n, const double *X, const orc_hyper *h,
                            int64_t *rowptr, int32_t *col, double *val)
 {
-    const int d = h->d;
+    const int d = h->d, w = point_width(h);
+    double *B = bump_table(n, X, h);
+    if (!B) return -1;
     if (!col) {
         #pragma omp parallel for schedule(dynamic, 64)
         for (int64_t i = 0; i < n; ++i) {
             int64_t c = 0;
             for (int64_t j = 0; j < n; ++j)
-                if (j == i || orc_in_pattern(d, X + (size_t)i * d, X + (size_t)j * d, h->r)) ++c;
+                if (j == i || pair_in(h, X + (size_t)i * d, X + (size_t)j * d, B + (size_t)i * w, B + (size_t)j * w)) ++c;
             rowptr[i + 1] = c;
         }
         rowptr[0] = 0;
         for (int64_t i = 0; i < n; ++i) rowptr[i + 1] += rowptr[i];
+        free(B);
         return rowptr[n];
     }
-    double *B = bump_table(n, X, h);
-    if (!B) return -1;
     #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i) {
         int64_t p = rowptr[i];
         const double *xi = X + (size_t)i * d;
         for (int64_t j = 0; j < n; ++j) {
             const double *xj = X + (size_t)j * d;
-            if (j == i || orc_in_pattern(d, xi, xj, h->r)) {
-                double v = kernel_from_bumps(h, xi, xj, B + (size_t)i * h->L, B + (size_t)j * h->L);
+            if (j == i || pair_in(h, xi, xj, B + (size_t)i * w, B + (size_t)j * w)) {
+                double v = pair_value(h, xi, xj, B + (size_t)i * w, B + (size_t)j * w);
                 if (j == i) v = v + h->sigma2;
                 col[p] = (int32_t)j;
                 if (val) val[p] = v;
@@ -250,15 +366,16 @@ int64_t orc_row_brute(int64_t n, const double *X, const orc_hyper *h, int64_t i,
 {
     const int d = h->d;
     double bi[64], bj[64];
-    if (h->L > 64) return -1;
+    if (point_width(h) > 64) return -1;
     const double *xi = X + (size_t)i * d;
-    orc_bumps(h, xi, bi, NULL);
+    point_values(h, xi, bi);
     int64_t c = 0;
     for (int64_t j = 0; j < n; ++j) {
         const double *xj = X + (size_t)j * d;
-        if (j == i || orc_in_pattern(d, xi, xj, h->r)) {
-            orc_bumps(h, xj, bj, NULL);
-            double v = kernel_from_bumps(h, xi, xj, bi, bj);
+        if (h->family == 1 && j != i) point_values(h, xj, bj);
+        if (j == i || pair_in(h, xi, xj, bi, bj)) {
+            if (h->family != 1 || j == i) point_values(h, xj, bj);
+            double v = pair_value(h, xi, xj, bi, bj);
             if (j == i) v = v + h->sigma2;
             cols[c] = (int32_t)j;
             if (vals) vals[c] = v;
@@ -298,33 +415,34 @@ int64_t orc_assemble_candidates(int64_t n, const double *X, const orc_hyper *h,
                                 int64_t ncand, const int64_t *cand_i, const int64_t *cand_j,
                                 int64_t *rowptr, int32_t *col, double *val)
 {
-    const int d = h->d;
+    const int d = h->d, w = point_width(h);
+    double *B = bump_table(n, X, h);
+    if (!B) return -1;
     if (!col) {
         for (int64_t i = 0; i <= n; ++i) rowptr[i] = 0;
         for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = 1;   /* the diagonal */
         for (int64_t p = 0; p < ncand; ++p) {
             int64_t i = cand_i[p], j = cand_j[p];
-            if (orc_in_pattern(d, X + (size_t)i * d, X + (size_t)j * d, h->r)) {
+            if (pair_in(h, X + (size_t)i * d, X + (size_t)j * d, B + (size_t)i * w, B + (size_t)j * w)) {
                 rowptr[i + 1] += 1;
                 rowptr[j + 1] += 1;
             }
         }
         for (int64_t i = 0; i < n; ++i) rowptr[i + 1] += rowptr[i];
+        free(B);
         return rowptr[n];
     }
     int64_t *fillp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-    if (!fillp) return -1;
+    if (!fillp) { free(B); return -1; }
     for (int64_t i = 0; i < n; ++i) { fillp[i] = rowptr[i] + 1; col[rowptr[i]] = (int32_t)i; }
     for (int64_t p = 0; p < ncand; ++p) {
         int64_t i = cand_i[p], j = cand_j[p];
-        if (orc_in_pattern(d, X + (size_t)i * d, X + (size_t)j * d, h->r)) {
+        if (pair_in(h, X + (size_t)i * d, X + (size_t)j * d, B + (size_t)i * w, B + (size_t)j * w)) {
             col[fillp[i]++] = (int32_t)j;
             col[fillp[j]++] = (int32_t)i;
         }
     }
     free(fillp);
-    double *B = bump_table(n, X, h);
-    if (!B) return -1;
     #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
         int64_t a = rowptr[i], e = rowptr[i + 1];
@@ -333,8 +451,7 @@ int64_t orc_assemble_candidates(int64_t n, const double *X, const orc_hyper *h,
             const double *xi = X + (size_t)i * d;
             for (int64_t p = a; p < e; ++p) {
                 int64_t j = col[p];
-                double v = kernel_from_bumps(h, xi, X + (size_t)j * d, B + (size_t)i * h->L,
-                                             B + (size_t)j * h->L);
+                double v = pair_value(h, xi, X + (size_t)j * d, B + (size_t)i * w, B + (size_t)j * w);
                 if (j == i) v = v + h->sigma2;
                 val[p] = v;
             }
@@ -347,7 +464,7 @@ int64_t orc_assemble_candidates(int64_t n, const double *X, const orc_hyper *h,
 /* Dense A = K + sigma^2 I (n x n, row-major), for the exact small-n path. */
 void orc_dense_A(int64_t n, const double *X, const orc_hyper *h, double *A)
 {
-    const int d = h->d;
+    const int d = h->d, w = point_width(h);
     double *B = bump_table(n, X, h);
     if (!B) return;
     #pragma omp parallel for schedule(dynamic, 16)
@@ -355,8 +472,8 @@ void orc_dense_A(int64_t n, const double *X, const orc_hyper *h, double *A)
         for (int64_t j = 0; j < n; ++j) {
             const double *xi = X + (size_t)i * d, *xj = X + (size_t)j * d;
             double v = 0.0;
-            if (j == i || orc_in_pattern(d, xi, xj, h->r))
-                v = kernel_from_bumps(h, xi, xj, B + (size_t)i * h->L, B + (size_t)j * h->L);
+            if (j == i || pair_in(h, xi, xj, B + (size_t)i * w, B + (size_t)j * w))
+                v = pair_value(h, xi, xj, B + (size_t)i * w, B + (size_t)j * w);
             if (j == i) v = v + h->sigma2;
             A[(size_t)i * n + j] = v;
         }
@@ -369,7 +486,7 @@ void orc_dense_A(int64_t n, const double *X, const orc_hyper *h, double *A)
  * No noise term: a test point is a new location, never the same index as a training point. */
 void orc_cross_K(int64_t ns, const double *Xs, int64_t n, const double *X, const orc_hyper *h, double *Ks)
 {
-    const int d = h->d;
+    const int d = h->d, w = point_width(h);
     double *B = bump_table(n, X, h);
     double *Bs = bump_table(ns, Xs, h);
     if (!B || !Bs) { free(B); free(Bs); return; }
@@ -378,8 +495,8 @@ void orc_cross_K(int64_t ns, const double *Xs, int64_t n, const double *X, const
         for (int64_t j = 0; j < n; ++j) {
             const double *xi = Xs + (size_t)i * d, *xj = X + (size_t)j * d;
             double v = 0.0;
-            if (orc_in_pattern(d, xi, xj, h->r))
-                v = kernel_from_bumps(h, xi, xj, Bs + (size_t)i * h->L, B + (size_t)j * h->L);
+            if (pair_in(h, xi, xj, Bs + (size_t)i * w, B + (size_t)j * w))
+                v = pair_value(h, xi, xj, Bs + (size_t)i * w, B + (size_t)j * w);
             Ks[(size_t)i * n + j] = v;
         }
     free(B);
@@ -602,17 +719,145 @@ static void pair_grad(const orc_hyper *h, const double *xi, const double *xj, in
     g[P - 1] = diag ? 1.0 : 0.0;
 }
 
+/* Family 1 (Eq. 6): per-point quantities for the gradient: s, lambda (d), psi (L) and
+ * d psi_l / d(c_l, rho_l) (L x (d + 1)). */
+typedef struct { double s, lam[4], psi[32], dpsi[32 * 5]; } wc_pt;
+
+static void wc_point_grad(const orc_hyper *h, const double *x, wc_pt *p)
+{
+    const int d = h->d, L = h->L;
+    double v[5];
+    wc_point(h, x, v);
+    p->s = v[0];
+    for (int k = 0; k < d; ++k) p->lam[k] = v[1 + k];
+    for (int l = 0; l < L; ++l) {
+        double s;
+        p->psi[l] = wc_psi(h, l, x, &s);
+        double *g = p->dpsi + (size_t)l * (d + 1);
+        if (s < 1.0) {
+            double u = 1.0 - s, rho = h->radii[l];
+            double dpds = -3.0 * u * u;
+            const double *c = h->centers + (size_t)l * d;
+            for (int k = 0; k < d; ++k) g[k] = dpds * (-2.0 * (x[k] - c[k]) / (rho * rho));
+            g[d] = dpds * (-2.0 * s / rho);
+        } else {
+            for (int k = 0; k <= d; ++k) g[k] = 0.0;
+        }
+    }
+}
+
+/* dA_ij / dtheta for one stored pair of the family-1 kernel; theta = [centers (L x d),
+ * radii (L), amps (L), G (L x d), ell (d), w0, r0, sigma2]. */
+static void pair_grad_wc(const orc_hyper *h, const double *xi, const double *xj, int diag, const wc_pt *pi,
+                         const wc_pt *pj, double *g)
+{
+    const int d = h->d, L = h->L;
+    const int P = L * (2 * d + 2) + d + 3;
+    const int oC = 0, oR = L * d, oA = L * d + L, oG = L * d + 2 * L, oE = L * (2 * d + 2), oW = oE + d;
+    for (int p = 0; p < P; ++p) g[p] = 0.0;
+    double ds[2], dl[2][4], dr0 = 0.0;
+    if (diag) {
+        /* k_ii = s_i^2 whatever lambda and r0: only s moves it */
+        ds[0] = pi->s;
+        ds[1] = pi->s;
+        for (int k = 0; k < d; ++k) dl[0][k] = dl[1][k] = 0.0;
+        g[P - 1] = 1.0;
+    } else {
+        double q = orc_wc_q(d, xi, xj, pi->lam, pj->lam);
+        double t = sqrt(q) / h->r;
+        double phi = orc_phi(h->kind, d, t);
+        double pref = 1.0;
+        for (int k = 0; k < d; ++k)
+            pref = pref * sqrt(sqrt(pi->lam[k] * pj->lam[k])) / sqrt((pi->lam[k] + pj->lam[k]) * 0.5);
+        double dphidq = orc_dphi_over_t(h->kind, d, t) / (2.0 * h->r * h->r);
+        double ss = pi->s * pj->s;
+        ds[0] = pj->s * pref * phi;
+        ds[1] = pi->s * pref * phi;
+        for (int k = 0; k < d; ++k) {
+            double m = (pi->lam[k] + pj->lam[k]) * 0.5;
+            double dk = xi[k] - xj[k];
+            double dq = -(dk * dk) / (2.0 * m * m);      /* dQ / d lambda_{i or j, k} */
+            dl[0][k] = ss * (pref * phi * (1.0 / (4.0 * pi->lam[k]) - 1.0 / (4.0 * m)) + pref * dphidq * dq);
+            dl[1][k] = ss * (pref * phi * (1.0 / (4.0 * pj->lam[k]) - 1.0 / (4.0 * m)) + pref * dphidq * dq);
+        }
+        dr0 = ss * pref * orc_dphi(h->kind, d, t) * (-t / h->r);
+    }
+    const wc_pt *side[2] = {pi, pj};
+    for (int e = 0; e < 2; ++e) {
+        const wc_pt *pp = side[e];
+        for (int l = 0; l < L; ++l) {
+            /* through psi_l: s gets a_l psi_l, lambda_k gets G_lk psi_l */
+            double w = ds[e] * h->amps[l];
+            for (int k = 0; k < d; ++k) w = w + dl[e][k] * h->G[(size_t)l * d + k];
+            for (int k = 0; k < d; ++k) g[oC + l * d + k] += w * pp->dpsi[(size_t)l * (d + 1) + k];
+            g[oR + l] += w * pp->dpsi[(size_t)l * (d + 1) + d];
+            g[oA + l] += ds[e] * pp->psi[l];
+            for (int k = 0; k < d; ++k) g[oG + l * d + k] += dl[e][k] * pp->psi[l];
+        }
+        for (int k = 0; k < d; ++k) g[oE + k] += dl[e][k] * 2.0 * h->ell[k];
+        g[oW] += ds[e];
+    }
+    g[oW + 1] = dr0;
+}
+
 /*
  * grad[P] = 1/2 sum over stored (i, j) of W_ij dA_ij.  The pattern is given in CSR
  * (rowptr, col; original index order).  If Wd (n x n) is non-NULL, W_ij = a_i a_j - Wd_ij;
  * otherwise W_ij = a_i a_j - (1/m) sum_s (U_is V_js + U_js V_is) / 2 with U, V n x m.
  * Row partial sums are added in row order (deterministic).
  */
+static double pair_w(int64_t n, int64_t i, int64_t j, const double *a, int m, const double *U, const double *V,
+                     const double *Wd)
+{
+    if (Wd) return a[i] * a[j] - Wd[(size_t)i * n + j];
+    double tr = 0.0;
+    for (int s = 0; s < m; ++s)
+        tr = tr + 0.5 * (U[(size_t)i * m + s] * V[(size_t)j * m + s] + U[(size_t)j * m + s] * V[(size_t)i * m + s]);
+    return a[i] * a[j] - tr / (double)m;
+}
+
+static int grad_contract_wc(int64_t n, const int64_t *rowptr, const int32_t *col, const double *X,
+                            const orc_hyper *h, const double *a, int m, const double *U, const double *V,
+                            const double *Wd, double *grad)
+{
+    const int d = h->d, L = h->L;
+    const int P = L * (2 * d + 2) + d + 3;
+    const int64_t chunk = 4096;
+    if (L > 32 || P > 512) return -1;
+    wc_pt *pts = (wc_pt *)malloc(sizeof(wc_pt) * (size_t)(n > 0 ? n : 1));
+    double *rowg = (double *)malloc(sizeof(double) * (size_t)chunk * P);
+    if (!pts || !rowg) { free(pts); free(rowg); return -1; }
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) wc_point_grad(h, X + (size_t)i * d, pts + i);
+    for (int p = 0; p < P; ++p) grad[p] = 0.0;
+    for (int64_t i0 = 0; i0 < n; i0 += chunk) {
+        int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
+        #pragma omp parallel for schedule(dynamic, 32)
+        for (int64_t i = i0; i < i1; ++i) {
+            double g[512];
+            double *acc = rowg + (size_t)(i - i0) * P;
+            for (int p = 0; p < P; ++p) acc[p] = 0.0;
+            for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+                int64_t j = col[e];
+                double w = pair_w(n, i, j, a, m, U, V, Wd);
+                pair_grad_wc(h, X + (size_t)i * d, X + (size_t)j * d, j == i, pts + i, pts + j, g);
+                for (int p = 0; p < P; ++p) acc[p] = acc[p] + 0.5 * w * g[p];
+            }
+        }
+        for (int64_t i = i0; i < i1; ++i)
+            for (int p = 0; p < P; ++p) grad[p] = grad[p] + rowg[(size_t)(i - i0) * P + p];
+    }
+    free(pts);
+    free(rowg);
+    return 0;
+}
+
 int orc_grad_contract(int64_t n, const int64_t *rowptr, const int32_t *col, const double *X,
                       const orc_hyper *h, const double *a, int m, const double *U,
                       const double *V, const double *Wd, double *grad)
 {
     const int d = h->d, L = h->L;
+    if (h->family == 1) return grad_contract_wc(n, rowptr, col, X, h, a, m, U, V, Wd, grad);
     const int P = L * (d + 2) + 2;
     const int64_t chunk = 4096;
     double *B = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(L > 0 ? L : 1));

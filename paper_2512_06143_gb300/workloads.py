@@ -41,12 +41,16 @@ FROZEN_R = {
 }
 
 
-def _hyper(d, r, sigma2, centers, radii, amps, beta=1.0, w0=0.0, kind=0):
-    return dict(d=int(d), r=float(r), sigma2=float(sigma2),
-                centers=np.ascontiguousarray(centers, np.float64).reshape(-1, d),
-                radii=np.ascontiguousarray(radii, np.float64),
-                amps=np.ascontiguousarray(amps, np.float64), beta=float(beta), w0=float(w0),
-                kind=int(kind))
+def _hyper(d, r, sigma2, centers, radii, amps, beta=1.0, w0=0.0, kind=0, family=0, ell=None, G=None):
+    h = dict(d=int(d), r=float(r), sigma2=float(sigma2),
+             centers=np.ascontiguousarray(centers, np.float64).reshape(-1, d),
+             radii=np.ascontiguousarray(radii, np.float64),
+             amps=np.ascontiguousarray(amps, np.float64), beta=float(beta), w0=float(w0),
+             kind=int(kind))
+    if family:
+        h.update(family=int(family), ell=np.ascontiguousarray(ell, np.float64).reshape(d),
+                 G=np.ascontiguousarray(G, np.float64).reshape(-1, d))
+    return h
 
 
 def tune_r(X: np.ndarray, target: float, seed: int = 0, sample: int = 10000,
@@ -191,6 +195,37 @@ def random_small(seed: int, n: int, d: int, L: int = 3, r: float | None = None, 
     hyp = _hyper(d, r, sigma2, rng.random((L, d)), rng.uniform(0.3, 0.6, L), rng.uniform(0.5, 1.5, L),
                  w0=w0, kind=kind)
     return dict(name=f"random_small[{seed}]", X=X, y=y, hyper=hyp)
+
+
+def random_wendconv(seed: int, n: int, d: int, L: int = 3, r: float | None = None, kind: int = 0,
+                    sigma2: float = 1e-3, clustered: bool = False, stationary: bool = False) -> dict:
+    """Problems for the Wendland convolution kernel (Eq. 6): the length-scale field's base
+    factors ell ~ U(0.7, 1.4)^d and bump weights G ~ U(0, 1.5)^(L x d), the signal field
+    w0 = 1 plus amplitudes U(0.2, 1) on bumps of radius U(0.3, 0.6).  stationary=True sets
+    G = 0, ell = 1, amplitudes 0 (the kernel is then Eq. 3's plain taper)."""
+    rng = np.random.default_rng(seed)
+    X = _clusters(rng, n, d, k=max(1, n // 200), sigma=0.05) if clustered else rng.random((n, d))
+    y = _sines(X, rng, 0.02)
+    if r is None:
+        vol = math.pi ** (d / 2) / math.gamma(d / 2 + 1)
+        r = (30.0 / (n * vol)) ** (1.0 / d)
+    centers, radii = rng.random((L, d)), rng.uniform(0.3, 0.6, L)
+    ell, G, amps = rng.uniform(0.7, 1.4, d), rng.uniform(0.0, 1.5, (L, d)), rng.uniform(0.2, 1.0, L)
+    if stationary:
+        ell, G, amps = np.ones(d), np.zeros((L, d)), np.zeros(L)
+    hyp = _hyper(d, r, sigma2, centers, radii, amps, w0=1.0, kind=kind, family=1, ell=ell, G=G)
+    return dict(name=f"random_wendconv[{seed}]", X=X, y=y, hyper=hyp)
+
+
+def f1_1d_wendconv(seed: int = 0, n: int = 2000, r: float = 0.02) -> dict:
+    """Sec. 5.1's 1-D test with the Wendland convolution kernel (the paper's choice for it)."""
+    rng = np.random.default_rng(seed)
+    X = np.sort(rng.random(n))[:, None]
+    y = f1(X[:, 0]) + rng.normal(0.0, 0.01, n)
+    L = 3
+    hyp = _hyper(1, r, 1e-4, rng.random((L, 1)), np.full(L, 0.3), rng.uniform(0.2, 0.8, L), w0=1.0,
+                 family=1, ell=np.ones(1), G=rng.uniform(0.0, 2.0, (L, 1)))
+    return dict(name="f1_1d_wendconv", X=X, y=y, hyper=hyp)
 
 
 def perturbed_hypers(hyper: dict, count: int, seed: int) -> list:
