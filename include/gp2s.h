@@ -73,7 +73,23 @@ typedef enum {
     GP2S_LOGDET_SLQ = 2     /* stochastic Lanczos quadrature on D^{-1/2} A D^{-1/2} */
 } gp2s_logdet_method;
 
-/* Kernel hyperparameters (Eq. 3, Eq. 7, Sec. 4.3) and noise (Sec. 3).  Host memory. */
+/* Kernel families.
+ *   GP2S_KERNEL_PRODUCT (Sec. 4.1 / 4.3): k = phi(|xi - xj| / r) (sum_l b_l(xi) b_l(xj) + w0), the
+ *     bumps b_l of Eq. 7; support |xi - xj| < r.
+ *   GP2S_KERNEL_WENDCONV (Eq. 6, Sec. 4.2): the non-stationary Wendland kernel by convolution,
+ *       k = s(xi) s(xj) |S_i|^(1/4) |S_j|^(1/4) / |(S_i + S_j)/2|^(1/2) phi(sqrt(Q) / r),
+ *       Q = (xi - xj)^T ((S_i + S_j)/2)^{-1} (xi - xj),  support Q < r^2,
+ *     with the paper's parametric fields read as S(x) = diag(lambda_k(x)),
+ *       lambda_k(x) = ell_k^2 + sum_l G_lk psi_l(x),   s(x) = w0 + sum_l amps_l psi_l(x),
+ *       psi_l(x) = (1 - |x - c_l|^2 / rho_l^2)^3 inside the bump l (centers c, radii rho), else 0.
+ *     Its hyperparameter vector is [centers (L x d), radii (L), amps (L), G (L x d), ell (d), w0,
+ *     r, sigma2]; beta is unused. */
+typedef enum {
+    GP2S_KERNEL_PRODUCT = 0,
+    GP2S_KERNEL_WENDCONV = 1
+} gp2s_kernel_family;
+
+/* Kernel hyperparameters (Eq. 3, Eq. 6, Eq. 7, Sec. 4.3) and noise (Sec. 3).  Host memory. */
 typedef struct {
     int32_t d;               /* input dimension, 1..4 */
     int32_t L;               /* number of bumps, 0..32 */
@@ -86,6 +102,10 @@ typedef struct {
     const double *centers;   /* host, L x d row-major */
     const double *radii;     /* host, L */
     const double *amps;      /* host, L */
+    int32_t family;          /* gp2s_kernel_family: GP2S_KERNEL_PRODUCT (0) or GP2S_KERNEL_WENDCONV (1) */
+    int32_t reserved2;
+    const double *ell;       /* WENDCONV: host, d base length-scale factors (> 0) */
+    const double *G;         /* WENDCONV: host, L x d weights (>= 0) of the length-scale field */
 } gp2s_hyper;
 
 /* Options.  gp2s_opts_default() fills the defaults listed here. */
@@ -93,7 +113,8 @@ typedef struct {
     int32_t precision;       /* gp2s_precision, default MIXED */
     int32_t logdet;          /* gp2s_logdet_method, default AUTO */
     int32_t n_exact;         /* AUTO threshold for the dense path, default 20000 */
-    int32_t probes;          /* Rademacher probes m for SLQ / Hutchinson: 0, 32, 64, 96 or 128; default 64 */
+    int32_t probes;          /* Rademacher probes m for SLQ / Hutchinson: 0, 16, 32, 48, 64, 96 or 128;
+                                default 64 */
     int32_t lanczos_steps;   /* SLQ steps k per probe, default 100 */
     int32_t max_iter;        /* iteration cap per CG solve, default 20000 */
     double tol_inner;        /* FP32 inner CG relative residual of the first y solve, default 1e-6
@@ -177,8 +198,10 @@ typedef struct gp2s_ctx gp2s_ctx;
 /* Fill *opts with the defaults above. */
 void gp2s_opts_default(gp2s_opts *opts);
 
-/* Number of hyperparameters of gp2s_lml_grad: L (d + 2) + 2. */
+/* Number of hyperparameters of gp2s_lml_grad: L (d + 2) + 2 (product kernel). */
 int32_t gp2s_num_params(int32_t d, int32_t L);
+/* The same for a given family: L (d + 2) + 2 (PRODUCT) or L (2 d + 2) + d + 3 (WENDCONV). */
+int32_t gp2s_num_params_family(int32_t d, int32_t L, int32_t family);
 
 /* Create a context on CUDA device `device` that issues all work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the handle. */
@@ -305,7 +328,8 @@ gp2s_status gp2s_posterior(gp2s_ctx *ctx, int64_t n_test, const double *Xtest, d
  * evaluates LML(theta') with gp2s_lml (opts, with pattern reuse forced on: blocks that leave r
  * alone recompute only the values) and accepts when log u < LML(theta') - LML(theta).
  * A proposal the engine refuses (GP2S_EINVAL, GP2S_ENOTPD) is a rejection.
- *   block: P = L (d + 2) + 2 ints, the block of each theta component (-1 = held fixed); a block
+ *   block: P = gp2s_num_params_family(d, L, family) ints, the block of each theta component (in
+ *          the order gp2s_lml_grad returns them; -1 = held fixed); a block
  *          without members is skipped.
  *   step:  P proposal standard deviations.  lower / upper: P bounds each, or NULL (unbounded).
  *   normals (iters x P) / uniforms (iters x nblocks): the random numbers, or NULL to let the
@@ -357,7 +381,7 @@ gp2s_status gp2s_mcmc(gp2s_ctx *ctx, int64_t n, const double *X, const double *y
  * allocating library routine.
  *   n: 1..GP2S_NOALLOC_MAX_N; larger n returns GP2S_EINVAL and does nothing.
  *   X_dev (n x d FP64), y_dev (n FP64): DEVICE pointers, original point order.
- *   hyper: host, as for gp2s_lml.
+ *   hyper: host, as for gp2s_lml; the product kernel family only (WENDCONV returns GP2S_EINVAL).
  *   out_dev: DEVICE pointer to 3 doubles receiving {LML, y^T A^{-1} y, log|A|}; NaN if a Cholesky
  *   pivot is not positive.
  *   cuda_stream: the stream all work is issued on (NULL = legacy default stream).  It must belong

@@ -32,13 +32,15 @@ WENDLAND_C2, WENDLAND_C6_PAPER = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 LOGDET_AUTO, LOGDET_EXACT, LOGDET_SLQ = 0, 1, 2
 SOLVER_CG, SOLVER_MINRES = 0, 1
+KERNEL_PRODUCT, KERNEL_WENDCONV = 0, 1
 
 
 class _Hyper(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("L", ctypes.c_int32), ("kind", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("r", ctypes.c_double), ("sigma2", ctypes.c_double),
                 ("beta", ctypes.c_double), ("w0", ctypes.c_double), ("centers", ctypes.c_void_p),
-                ("radii", ctypes.c_void_p), ("amps", ctypes.c_void_p)]
+                ("radii", ctypes.c_void_p), ("amps", ctypes.c_void_p), ("family", ctypes.c_int32),
+                ("reserved2", ctypes.c_int32), ("ell", ctypes.c_void_p), ("G", ctypes.c_void_p)]
 
 
 class Opts(ctypes.Structure):
@@ -105,7 +107,7 @@ class CsrView(ctypes.Structure):
                 ("val64", ctypes.c_void_p), ("dscale", ctypes.c_void_p)]
 
 
-EXPORTED = ["gp2s_opts_default", "gp2s_num_params", "gp2s_create", "gp2s_destroy", "gp2s_last_error",
+EXPORTED = ["gp2s_opts_default", "gp2s_num_params", "gp2s_num_params_family", "gp2s_create", "gp2s_destroy", "gp2s_last_error",
             "gp2s_assemble", "gp2s_csr", "gp2s_solve", "gp2s_logdet", "gp2s_lml", "gp2s_lml_grad",
             "gp2s_lml_batched", "gp2s_posterior", "gp2s_mcmc", "gp2s_lml_exact_noalloc"]
 
@@ -136,6 +138,7 @@ def load(path: str | None = None):
     sigs = {
         "gp2s_opts_default": (None, [vp]),
         "gp2s_num_params": (i32, [i32, i32]),
+        "gp2s_num_params_family": (i32, [i32, i32, i32]),
         "gp2s_create": (i32, [ctypes.POINTER(vp), ctypes.c_int, vp]),
         "gp2s_destroy": (None, [vp]),
         "gp2s_last_error": (ctypes.c_char_p, [vp]),
@@ -174,6 +177,9 @@ class Hyper:
     beta: float = 1.0
     w0: float = 0.0
     kind: int = WENDLAND_C2
+    family: int = KERNEL_PRODUCT
+    ell: np.ndarray | None = None     # KERNEL_WENDCONV: d base length-scale factors
+    G: np.ndarray | None = None       # KERNEL_WENDCONV: L x d weights of the length-scale field
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -182,27 +188,42 @@ class Hyper:
 
     @property
     def nparams(self) -> int:
+        if self.family == KERNEL_WENDCONV:
+            return self.L * (2 * self.d + 2) + self.d + 3
         return self.L * (self.d + 2) + 2
 
     def theta(self) -> np.ndarray:
-        """[centers (L x d), radii (L), amps (L), r, sigma2]."""
-        return np.concatenate([np.asarray(self.centers, np.float64).ravel(), np.asarray(self.radii, np.float64),
-                               np.asarray(self.amps, np.float64), [self.r, self.sigma2]])
+        """[centers (L x d), radii (L), amps (L), r, sigma2] (product kernel), or
+        [centers, radii, amps, G (L x d), ell (d), w0, r, sigma2] (Wendland convolution)."""
+        head = [np.asarray(self.centers, np.float64).ravel(), np.asarray(self.radii, np.float64),
+                np.asarray(self.amps, np.float64)]
+        if self.family == KERNEL_WENDCONV:
+            head += [np.asarray(self.G, np.float64).ravel(), np.asarray(self.ell, np.float64), [self.w0]]
+        return np.concatenate(head + [[self.r, self.sigma2]])
 
     def with_theta(self, th) -> "Hyper":
         th = np.asarray(th, np.float64)
         L, d = self.L, self.d
-        return Hyper(d=d, centers=th[:L * d].reshape(L, d).copy(), radii=th[L * d:L * d + L].copy(),
-                     amps=th[L * d + L:L * d + 2 * L].copy(), r=float(th[-2]), sigma2=float(th[-1]),
-                     beta=self.beta, w0=self.w0, kind=self.kind)
+        kw = dict(d=d, centers=th[:L * d].reshape(L, d).copy(), radii=th[L * d:L * d + L].copy(),
+                  amps=th[L * d + L:L * d + 2 * L].copy(), r=float(th[-2]), sigma2=float(th[-1]),
+                  beta=self.beta, w0=self.w0, kind=self.kind, family=self.family)
+        if self.family == KERNEL_WENDCONV:
+            o = L * d + 2 * L
+            kw.update(G=th[o:o + L * d].reshape(L, d).copy(), ell=th[o + L * d:o + L * d + d].copy(),
+                      w0=float(th[o + L * d + d]))
+        return Hyper(**kw)
 
     def c(self) -> _Hyper:
         c = np.ascontiguousarray(np.asarray(self.centers, np.float64).reshape(self.L, self.d))
         r = np.ascontiguousarray(np.asarray(self.radii, np.float64))
         a = np.ascontiguousarray(np.asarray(self.amps, np.float64))
-        self._keep = [c, r, a]
+        e = np.ascontiguousarray(np.asarray(self.ell if self.ell is not None else np.ones(self.d), np.float64))
+        g = np.ascontiguousarray(np.asarray(self.G if self.G is not None else np.zeros((self.L, self.d)),
+                                            np.float64).reshape(self.L, self.d))
+        self._keep = [c, r, a, e, g]
         return _Hyper(self.d, self.L, int(self.kind), 0, float(self.r), float(self.sigma2), float(self.beta),
-                      float(self.w0), c.ctypes.data, r.ctypes.data, a.ctypes.data)
+                      float(self.w0), c.ctypes.data, r.ctypes.data, a.ctypes.data, int(self.family), 0,
+                      e.ctypes.data, g.ctypes.data)
 
 
 def default_opts(**kw) -> Opts:

@@ -51,6 +51,13 @@ __global__ void k_probe_bits(const int32_t *__restrict__ perm, int64_t n, int m,
 
 __device__ __forceinline__ float flip(float x, uint32_t bit) { return __int_as_float(__float_as_int(x) ^ (int)(bit << 31)); }
 
+__device__ __forceinline__ double warp_sum_adj(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <class T>
 __device__ __forceinline__ float to_f(T v) { return (float)v; }
 
@@ -61,11 +68,13 @@ __device__ __forceinline__ float probe_cross(const T *__restrict__ xa, const uin
 {
     float acc = 0.0f;
 #pragma unroll
-    for (int w = 0; w < M / 32; ++w) {
+    for (int w = 0; w < (M + 31) / 32; ++w) {
         const uint32_t ba = za[w], bb = zb[w];
+        constexpr int NB = M < 32 ? M : 32;
 #pragma unroll 8
-        for (int b = 0; b < 32; ++b) {
+        for (int b = 0; b < NB; ++b) {
             const int s = w * 32 + b;
+            if (s >= M) break;
             acc += flip(to_f(xa[s]), (bb >> b) & 1u) + flip(to_f(xb[s]), (ba >> b) & 1u);
         }
     }
@@ -94,7 +103,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int L = kp.L;
     const T *U = reinterpret_cast<const T *>(g.U);
-    constexpr int WZ = M / 32 > 0 ? M / 32 : 1;
+    constexpr int WZ = M > 0 ? (M + 31) / 32 : 1;
     const float inv_r = (float)kp.inv_r;
     const float inv2m = M > 0 ? 0.5f / (float)M : 0.0f;
     double gr = 0.0, gs = 0.0;
@@ -238,16 +247,234 @@ k_bump_grad(const double4_16a *__restrict__ X64, const float *__restrict__ H, in
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Wendland convolution kernel (Eq. 6): with W_ij as above and, for a stored pair i != j,
+//     dk/ds_i      = s_j P phi,
+//     dk/dlambda_ik = s_i s_j P [phi (1/(4 lambda_ik) - 1/(4 m_k)) - (phi'(t)/t) / (2 r^2) D_k^2 / (2 m_k^2)],
+//     dk/dr        = s_i s_j P phi'(t) (-t / r),
+// (P the determinant prefactor, m_k = (lambda_ik + lambda_jk)/2, t = sqrt(Q)/r; on the diagonal
+// k_ii = s_i^2 and only dk/ds_i = s_i remains), the row sums Hs_i = sum_j W_ij dk/ds_i and
+// Hl_ik = sum_j W_ij dk/dlambda_ik carry every field parameter (the sum over ordered pairs counts
+// each point once as the first argument: g = sum_i ds_i/dtheta Hs_i + dlambda_ik/dtheta Hl_ik),
+// and g_r = 1/2 sum_ij W_ij dk/dr, g_sigma2 = 1/2 sum_i W_ii.  FP64 per pair.
+// ---------------------------------------------------------------------------------------------
+struct AdjWcArgs {
+    const int32_t *rowptr, *col;
+    const double4_16a *X64, *Lam;
+    const double *Sig;
+    const double *a, *s64;
+    const void *U;
+    const uint32_t *zbits;
+    int64_t n;
+    int m;
+    double *Hs;               // n
+    double *Hl;               // n x 4
+    double *part;             // per block: [g_r, g_s2]
+};
+
+template <int D, class T, int M>
+__global__ void __launch_bounds__(256) k_adjoint_wc(AdjWcArgs g, KernelParams kp)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const T *U = reinterpret_cast<const T *>(g.U);
+    constexpr int WZ = M > 0 ? (M + 31) / 32 : 1;
+    const double inv2m = M > 0 ? 0.5 / (double)M : 0.0;
+    const double r = kp.r;
+    double gr = 0.0, gs = 0.0;
+    for (int64_t i = w0; i < g.n; i += nw) {
+        const double4_16a xiv = g.X64[i], liv = g.Lam[i];
+        const double xi[4] = {xiv.x, xiv.y, xiv.z, xiv.w}, li[4] = {liv.x, liv.y, liv.z, liv.w};
+        const double ai = g.a[i], si = g.s64[i], sgi = g.Sig[i];
+        const T *Ui = U + i * M;
+        uint32_t zi[WZ];
+#pragma unroll
+        for (int w = 0; w < WZ; ++w) zi[w] = M > 0 ? g.zbits[i * WZ + w] : 0u;
+        double hs = 0.0, hl[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) hl[k] = 0.0;
+        const int p1 = g.rowptr[i + 1];
+        for (int p = g.rowptr[i] + lane; p < p1; p += 32) {
+            const int j = g.col[p];
+            double tr = 0.0;
+            if (M > 0) {
+                uint32_t zj[WZ];
+#pragma unroll
+                for (int w = 0; w < WZ; ++w) zj[w] = g.zbits[(int64_t)j * WZ + w];
+                tr = (double)probe_cross<T, M>(Ui, zi, U + (int64_t)j * M, zj);
+            }
+            const double W = ai * g.a[j] - si * g.s64[j] * tr * inv2m;
+            const double sgj = g.Sig[j];
+            if (j == i) {
+                gs += W;
+                hs += W * sgi;
+                continue;
+            }
+            const double4_16a xjv = g.X64[j], ljv = g.Lam[j];
+            const double xj[4] = {xjv.x, xjv.y, xjv.z, xjv.w}, lj[4] = {ljv.x, ljv.y, ljv.z, ljv.w};
+            double q = 0.0, pref = 1.0, dd[D], mm[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const double dk = xi[k] - xj[k];
+                mm[k] = (li[k] + lj[k]) * 0.5;
+                dd[k] = dk * dk;
+                q += dd[k] / mm[k];
+                pref *= sqrt(sqrt(li[k] * lj[k])) / sqrt(mm[k]);
+            }
+            const double t = sqrt(q) / r;
+            const double phi = wendland<double>(kp.kind, D, t);
+            const double dphit = wendland_dt_over_t<double>(kp.kind, D, t);
+            const double ss = sgi * sgj;
+            hs += W * sgj * pref * phi;
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+                hl[k] += W * ss * pref * (phi * (0.25 / li[k] - 0.25 / mm[k]) - dphit / (2.0 * r * r) * dd[k] / (2.0 * mm[k] * mm[k]));
+            gr += W * ss * pref * (dphit * t) * (-t / r);
+        }
+        // the row's sums over the warp
+        hs = warp_sum_adj(hs);
+#pragma unroll
+        for (int k = 0; k < D; ++k) hl[k] = warp_sum_adj(hl[k]);
+        if (lane == 0) {
+            g.Hs[i] = hs;
+#pragma unroll
+            for (int k = 0; k < D; ++k) g.Hl[i * 4 + k] = hl[k];
+        }
+    }
+    __shared__ double sh[2][8];
+    gr = warp_sum_adj(gr);
+    gs = warp_sum_adj(gs);
+    if (lane == 0) {
+        sh[0][threadIdx.x >> 5] = gr;
+        sh[1][threadIdx.x >> 5] = gs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[0][w]; b += sh[1][w]; }
+        g.part[blockIdx.x * 2 + 0] = a;
+        g.part[blockIdx.x * 2 + 1] = b;
+    }
+}
+
+// Field parameters of the convolution kernel from the row sums: thread t of a block handles bump
+// l = t % L for points i = t / L, t / L + R, ... (R = threads / L); for psi_l at x_i,
+//     w = Hs_i a_l + sum_k Hl_ik G_lk   ->   centers: w dpsi/dc,  radii: w dpsi/drho,
+//     amps: Hs_i psi,  G_lk: Hl_ik psi;
+// threads of bump 0 also sum ell_k: 2 ell_k Hl_ik and w0: Hs_i.  Per-block partials of the
+// parameters [centers, radii, amps, G, ell, w0] in that order.
+template <int D>
+__global__ void __launch_bounds__(256)
+k_wc_field_grad(const double4_16a *__restrict__ X64, const double *__restrict__ Hs, const double *__restrict__ Hl,
+                int64_t n, KernelParams kp, double *__restrict__ part)
+{
+    const int L = kp.L;
+    constexpr int NA = 3 * D + 3;                 // per thread: 2 D + 2 bump terms, D + 1 shared terms
+    const int Pf = L * (2 * D + 2) + D + 1;
+    extern __shared__ double wacc_sh[];           // blockDim.x x NA
+    const int l = L > 0 ? (int)threadIdx.x % L : 0;
+    const int R = L > 0 ? (int)blockDim.x / L : (int)blockDim.x;
+    double acc[NA];
+#pragma unroll
+    for (int p = 0; p < NA; ++p) acc[p] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * R + threadIdx.x / (L > 0 ? L : 1); i < n && (int)threadIdx.x < R * (L > 0 ? L : 1);
+         i += (int64_t)gridDim.x * R) {
+        const double hs = Hs[i];
+        double hl[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) hl[k] = Hl[i * 4 + k];
+        if (l == 0) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc[2 * D + 2 + k] += 2.0 * kp.ell[k] * hl[k];
+            acc[3 * D + 2] += hs;
+        }
+        if (L == 0) continue;
+        const double4_16a xv = X64[i];
+        const double x[4] = {xv.x, xv.y, xv.z, xv.w};
+        double q = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double dk = x[k] - kp.centers[l * D + k];
+            q += dk * dk;
+        }
+        const double rho = kp.radii[l];
+        const double s = q / (rho * rho);
+        if (!(s < 1.0)) continue;
+        const double u = 1.0 - s;
+        const double psi = u * u * u;
+        const double dpds = -3.0 * u * u;
+        double w = hs * kp.amps[l];
+#pragma unroll
+        for (int k = 0; k < D; ++k) w += hl[k] * kp.G[l * D + k];
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] += w * dpds * (-2.0 * (x[k] - kp.centers[l * D + k]) / (rho * rho));
+        acc[D] += w * dpds * (-2.0 * s / rho);
+        acc[D + 1] += hs * psi;
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[D + 2 + k] += hl[k] * psi;
+    }
+#pragma unroll
+    for (int p = 0; p < NA; ++p) wacc_sh[threadIdx.x * NA + p] = acc[p];
+    __syncthreads();
+    double *out = part + (int64_t)blockIdx.x * Pf;
+    if ((int)threadIdx.x < L) {
+        double v[2 * D + 2];
+#pragma unroll
+        for (int p = 0; p < 2 * D + 2; ++p) v[p] = 0.0;
+        for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+            for (int p = 0; p < 2 * D + 2; ++p) v[p] += wacc_sh[(rr * L + threadIdx.x) * NA + p];
+        const int t = threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[t * D + k] = v[k];
+        out[L * D + t] = v[D];
+        out[L * D + L + t] = v[D + 1];
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[L * D + 2 * L + t * D + k] = v[D + 2 + k];
+    }
+    if (threadIdx.x == 0) {
+        double v[D + 1];
+#pragma unroll
+        for (int p = 0; p <= D; ++p) v[p] = 0.0;
+        const int stride = L > 0 ? L : 1;
+        for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+            for (int p = 0; p <= D; ++p) v[p] += wacc_sh[(rr * stride) * NA + 2 * D + 2 + p];
+#pragma unroll
+        for (int p = 0; p <= D; ++p) out[L * (2 * D + 2) + p] = v[p];
+    }
+}
+
+template <int D, class T>
+gp2s_status launch_adjoint_wc(gp2s_ctx *c, const AdjWcArgs &g, const KernelParams &kp, unsigned gb)
+{
+    switch (g.m) {
+    case 0: k_adjoint_wc<D, T, 0><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 16: k_adjoint_wc<D, T, 16><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 32: k_adjoint_wc<D, T, 32><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 48: k_adjoint_wc<D, T, 48><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 64: k_adjoint_wc<D, T, 64><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 96: k_adjoint_wc<D, T, 96><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 128: k_adjoint_wc<D, T, 128><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    default: return set_err(c, GP2S_EINVAL, "probes must be 0, 16, 32, 48, 64, 96 or 128");
+    }
+    GP2S_LAUNCH(c);
+    return GP2S_OK;
+}
+
 template <int D, class T>
 gp2s_status launch_adjoint(gp2s_ctx *c, const AdjArgs &g, const KernelParams &kp, unsigned gb)
 {
     switch (g.m) {
     case 0: k_adjoint<D, T, 0><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 16: k_adjoint<D, T, 16><<<gb, 256, 0, c->stream>>>(g, kp); break;
     case 32: k_adjoint<D, T, 32><<<gb, 256, 0, c->stream>>>(g, kp); break;
+    case 48: k_adjoint<D, T, 48><<<gb, 256, 0, c->stream>>>(g, kp); break;
     case 64: k_adjoint<D, T, 64><<<gb, 256, 0, c->stream>>>(g, kp); break;
     case 96: k_adjoint<D, T, 96><<<gb, 256, 0, c->stream>>>(g, kp); break;
     case 128: k_adjoint<D, T, 128><<<gb, 256, 0, c->stream>>>(g, kp); break;
-    default: return set_err(c, GP2S_EINVAL, "probes must be 0, 32, 64, 96 or 128");
+    default: return set_err(c, GP2S_EINVAL, "probes must be 0, 16, 32, 48, 64, 96 or 128");
     }
     GP2S_LAUNCH(c);
     return GP2S_OK;
@@ -266,8 +493,11 @@ gp2s_status dispatch_adjoint(gp2s_ctx *c, int d, const AdjArgs &g, const KernelP
 
 }  // namespace
 
+static gp2s_status adjoint_gradient_wc(gp2s_ctx *c, int m, double *grad_host);
+
 gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
 {
+    if (c->A.kp.family == 1) return adjoint_gradient_wc(c, m, grad_host);
     const Assembled &A = c->A;
     const int64_t n = A.n;
     const int d = A.d, L = A.L;
@@ -275,7 +505,7 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
     if (!c->have_solution) return set_err(c, GP2S_ENOTREADY, "gradient needs the solve");
     if (m > 0 && !c->have_probes) return set_err(c, GP2S_ENOTREADY, "gradient needs the probe solves");
     const bool mixed = A.precision == GP2S_PREC_MIXED;
-    const int W = m > 0 ? m / 32 : 0;
+    const int W = m > 0 ? (m + 31) / 32 : 0;
     GP2S_TRY(ensure(c, c->Z, sizeof(uint32_t) * (size_t)n * (W > 0 ? W : 1) + 64));
     GP2S_TRY(ensure(c, c->H, sizeof(float) * (size_t)n * (L > 0 ? L : 1) + 64));
     const int nb = 152 * 8;
@@ -327,6 +557,82 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
     for (int p = 0; p < P; ++p) grad_host[p] = 0.0;
     for (int b = 0; b < nbf && Pb > 0; ++b)
         for (int p = 0; p < Pb; ++p) grad_host[p] += hb[(size_t)b * Pb + p];
+    double gr = 0.0, gs = 0.0;
+    for (int b = 0; b < nb; ++b) { gr += hp[2 * b]; gs += hp[2 * b + 1]; }
+    grad_host[P - 2] = 0.5 * gr;
+    grad_host[P - 1] = 0.5 * gs;
+    return GP2S_OK;
+}
+
+// The Wendland convolution kernel's gradient: [centers, radii, amps, G, ell, w0, r, sigma2].
+static gp2s_status adjoint_gradient_wc(gp2s_ctx *c, int m, double *grad_host)
+{
+    const Assembled &A = c->A;
+    const int64_t n = A.n;
+    const int d = A.d, L = A.L;
+    const int P = L * (2 * d + 2) + d + 3;
+    const int Pf = P - 2;
+    if (!c->have_solution) return set_err(c, GP2S_ENOTREADY, "gradient needs the solve");
+    if (m > 0 && !c->have_probes) return set_err(c, GP2S_ENOTREADY, "gradient needs the probe solves");
+    const bool mixed = A.precision == GP2S_PREC_MIXED;
+    const int W = m > 0 ? (m + 31) / 32 : 0;
+    GP2S_TRY(ensure(c, c->Z, sizeof(uint32_t) * (size_t)n * (W > 0 ? W : 1) + 64));
+    GP2S_TRY(ensure(c, c->H, sizeof(double) * (size_t)n * 5 + 64));
+    const int nb = 152 * 8;
+    const int nbf = 152 * 2;
+    GP2S_TRY(ensure(c, c->gpart, sizeof(double) * ((size_t)nb * 2 + (size_t)nbf * Pf + 64)));
+    double *part = c->gpart.as<double>();
+    double *fpart = part + (size_t)nb * 2;
+    if (m > 0) {
+        unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * W, 256), 152 * 8);
+        k_probe_bits<<<gb, 256, 0, c->stream>>>(c->perm.as<int32_t>(), n, m, A.opts.seed, c->Z.as<uint32_t>());
+        GP2S_LAUNCH(c);
+    }
+    AdjWcArgs g;
+    std::memset(&g, 0, sizeof(g));
+    g.rowptr = c->rowptr.as<int32_t>();
+    g.col = c->col.as<int32_t>();
+    g.X64 = c->Xs64.as<double4_16a>();
+    g.Lam = c->wc_lam.as<double4_16a>();
+    g.Sig = c->wc_sig.as<double>();
+    g.a = c->vec64.as<double>() + 3 * n;
+    g.s64 = c->s64.as<double>();
+    g.U = c->vec.p;
+    g.zbits = c->Z.as<uint32_t>();
+    g.n = n;
+    g.m = m;
+    g.Hs = c->H.as<double>();
+    g.Hl = g.Hs + n;
+    g.part = part;
+#define GP2S_AWC(DD)                                                                         \
+    (mixed ? launch_adjoint_wc<DD, float>(c, g, A.kp, nb) : launch_adjoint_wc<DD, double>(c, g, A.kp, nb))
+    switch (d) {
+    case 1: GP2S_TRY(GP2S_AWC(1)); break;
+    case 2: GP2S_TRY(GP2S_AWC(2)); break;
+    case 3: GP2S_TRY(GP2S_AWC(3)); break;
+    default: GP2S_TRY(GP2S_AWC(4)); break;
+    }
+#undef GP2S_AWC
+    {
+        const int thr = L > 0 ? L * (256 / L) : 256;
+        const size_t smem = sizeof(double) * (size_t)thr * (3 * d + 3);
+        const double *Hs = g.Hs, *Hl = g.Hl;
+        const double4_16a *x64 = c->Xs64.as<double4_16a>();
+        switch (d) {
+        case 1: k_wc_field_grad<1><<<nbf, thr, smem, c->stream>>>(x64, Hs, Hl, n, A.kp, fpart); break;
+        case 2: k_wc_field_grad<2><<<nbf, thr, smem, c->stream>>>(x64, Hs, Hl, n, A.kp, fpart); break;
+        case 3: k_wc_field_grad<3><<<nbf, thr, smem, c->stream>>>(x64, Hs, Hl, n, A.kp, fpart); break;
+        default: k_wc_field_grad<4><<<nbf, thr, smem, c->stream>>>(x64, Hs, Hl, n, A.kp, fpart); break;
+        }
+        GP2S_LAUNCH(c);
+    }
+    std::vector<double> hp((size_t)nb * 2), hb((size_t)nbf * Pf);
+    GP2S_CUDA(c, cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb * 2, cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaMemcpyAsync(hb.data(), fpart, sizeof(double) * (size_t)nbf * Pf, cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int p = 0; p < P; ++p) grad_host[p] = 0.0;
+    for (int b = 0; b < nbf; ++b)
+        for (int p = 0; p < Pf; ++p) grad_host[p] += hb[(size_t)b * Pf + p];
     double gr = 0.0, gs = 0.0;
     for (int b = 0; b < nb; ++b) { gr += hp[2 * b]; gs += hp[2 * b + 1]; }
     grad_host[P - 2] = 0.5 * gr;

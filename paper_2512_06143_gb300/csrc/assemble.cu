@@ -12,6 +12,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "gp2s_geometry.cuh"
 #include "gp2s_kernel_math.cuh"
@@ -34,6 +35,7 @@ struct AsmArgs {
     int64_t ncells;
     const float *B32;     // n x L
     const float *s32;     // n
+    const double4_16a *Lam;   // Wendland convolution: lambda_k of every sorted point (padded to 4)
     const int32_t *rowptr;
     int32_t *rowcnt;
     int32_t *col;
@@ -89,6 +91,62 @@ __device__ __forceinline__ bool exact_in(const double4_16a &a, const double4_16a
         q = __dadd_rn(q, __dmul_rn(dk, dk));
     }
     return q < r2;
+}
+
+// Wendland convolution kernel (Eq. 6): the polynomial bump psi_l(x) = (1 - |x - c_l|^2 / rho_l^2)^3,
+// the signal field s(x) = w0 + sum_l a_l psi_l(x) and the length-scale field lambda_k(x) =
+// ell_k^2 + sum_l G_lk psi_l(x), every operation one FP64 round-to-nearest step in the written
+// order (no contraction): the pattern test below depends on lambda bit for bit.
+template <int D>
+__device__ __forceinline__ double wc_psi(const double *x, const KernelParams &kp, int l)
+{
+    double q = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const double dk = __dsub_rn(x[k], kp.centers[l * D + k]);
+        q = __dadd_rn(q, __dmul_rn(dk, dk));
+    }
+    const double rho = kp.radii[l];
+    const double s = __ddiv_rn(q, __dmul_rn(rho, rho));
+    if (!(s < 1.0)) return 0.0;
+    const double u = __dsub_rn(1.0, s);
+    return __dmul_rn(__dmul_rn(u, u), u);
+}
+
+template <int D>
+__device__ __forceinline__ void wc_fields(const double *x, const KernelParams &kp, double &sig, double *lam,
+                                          double *psi_out)
+{
+    double sg = 0.0, acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = 0.0;
+    for (int l = 0; l < kp.L; ++l) {
+        const double ps = wc_psi<D>(x, kp, l);
+        if (psi_out) psi_out[l] = ps;
+        sg = __dadd_rn(sg, __dmul_rn(kp.amps[l], ps));
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] = __dadd_rn(acc[k], __dmul_rn(kp.G[l * D + k], ps));
+    }
+    sig = __dadd_rn(kp.w0, sg);
+#pragma unroll
+    for (int k = 0; k < D; ++k) lam[k] = __dadd_rn(__dmul_rn(kp.ell[k], kp.ell[k]), acc[k]);
+}
+
+// Q(i, j) = ((D0 D0 / m0 + D1 D1 / m1) + ...), m_k = (lambda_ik + lambda_jk) * 0.5
+template <int D>
+__device__ __forceinline__ double wc_q(const double4_16a &a, const double4_16a &b, const double4_16a &la,
+                                       const double4_16a &lb)
+{
+    const double xa[4] = {a.x, a.y, a.z, a.w}, xb[4] = {b.x, b.y, b.z, b.w};
+    const double ma[4] = {la.x, la.y, la.z, la.w}, mb[4] = {lb.x, lb.y, lb.z, lb.w};
+    double q = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const double dk = __dsub_rn(xa[k], xb[k]);
+        const double m = __dmul_rn(__dadd_rn(ma[k], mb[k]), 0.5);
+        q = __dadd_rn(q, __ddiv_rn(__dmul_rn(dk, dk), m));
+    }
+    return q;
 }
 
 template <int D, bool FILL>
@@ -208,7 +266,10 @@ k_assemble(AsmArgs a, GridParams g, SupportParams sp, KernelParams kp)
                         acc = true;
                     } else if (d2 <= sp.thr_hi) {
                         ++band;
-                        acc = exact_in<D>(a.X64[i], a.X64[j], sp.r2);
+                        // the Wendland convolution's support is Q < r^2; the FP32 band around
+                        // the Euclidean bound r sqrt(max lambda) only rejects
+                        acc = kp.family == 1 ? wc_q<D>(a.X64[i], a.X64[j], a.Lam[i], a.Lam[j]) < sp.r2
+                                             : exact_in<D>(a.X64[i], a.X64[j], sp.r2);
                     }
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, acc);
@@ -245,15 +306,43 @@ size_t asm_smem_bytes(int D, bool fill, int L)
 
 // Bump tables (Eq. 7) in FP64 (+ an FP32 copy), the diagonal D_i = A_ii = (sum_l b_l^2 + w0)
 // + sigma^2 and the Jacobi scales s_i = D_i^{-1/2}.
+// Wendland convolution (family 1): B64 holds psi_l (the gradient's chain rule needs it), Lam the
+// length-scale field, Sig the signal field, and D_i = s(x_i)^2 + sigma^2 (Q = 0 and the
+// prefactor is 1 on the diagonal).
 template <int D>
 __global__ void k_bumps(const double4_16a *__restrict__ X64, int64_t n, KernelParams kp,
                         double *__restrict__ B64, float *__restrict__ B32, double *__restrict__ D64,
-                        double *__restrict__ s64, float *__restrict__ s32, int *__restrict__ bad)
+                        double *__restrict__ s64, float *__restrict__ s32, int *__restrict__ bad,
+                        double4_16a *__restrict__ Lam, double *__restrict__ Sig)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double4_16a xv = X64[i];
         const double x[4] = {xv.x, xv.y, xv.z, xv.w};
+        if (kp.family == 1) {
+            double sig, lam[D];
+            wc_fields<D>(x, kp, sig, lam, B64 + i * kp.L);
+            double4_16a lv;
+            lv.x = lam[0];
+            lv.y = D > 1 ? lam[D > 1 ? 1 : 0] : 1.0;
+            lv.z = D > 2 ? lam[D > 2 ? 2 : 0] : 1.0;
+            lv.w = D > 3 ? lam[D > 3 ? 3 : 0] : 1.0;
+            Lam[i] = lv;
+            Sig[i] = sig;
+            for (int l = 0; l < kp.L; ++l) B32[i * kp.L + l] = (float)B64[i * kp.L + l];
+            const double Dii = sig * sig + kp.sigma2;
+            D64[i] = Dii;
+            if (!(Dii > 0.0) || !isfinite(Dii)) {
+                atomicOr(bad, 1);
+                s64[i] = 0.0;
+                s32[i] = 0.0f;
+            } else {
+                const double sc = 1.0 / sqrt(Dii);
+                s64[i] = sc;
+                s32[i] = (float)sc;
+            }
+            continue;
+        }
         double S = 0.0;
         for (int l = 0; l < kp.L; ++l) {
             double q = 0.0;
@@ -290,7 +379,8 @@ template <int D>
 __global__ void __launch_bounds__(256)
 k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowptr,
            const int32_t *__restrict__ col, int64_t n, KernelParams kp, const double *__restrict__ B64,
-           const double *__restrict__ s64, double *__restrict__ val64, float *__restrict__ val32)
+           const double *__restrict__ s64, double *__restrict__ val64, float *__restrict__ val32,
+           const double4_16a *__restrict__ Lam, const double *__restrict__ Sig)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -305,6 +395,16 @@ k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowp
             double v;
             if (j == i) {
                 v = 1.0;
+            } else if (kp.family == 1) {
+                // Eq. 6: s_i s_j prod_k (l_ik l_jk)^(1/4) / ((l_ik + l_jk) / 2)^(1/2) phi(sqrt(Q) / r)
+                const double4_16a li = Lam[i], lj = Lam[j];
+                const double q = wc_q<D>(xi, X64[j], li, lj);
+                const double ai[4] = {li.x, li.y, li.z, li.w}, aj[4] = {lj.x, lj.y, lj.z, lj.w};
+                double pref = 1.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) pref = pref * (sqrt(sqrt(ai[k] * aj[k])) / sqrt((ai[k] + aj[k]) * 0.5));
+                const double phi = wendland<double>(kp.kind, D, sqrt(q) * kp.inv_r);
+                v = (Sig[i] * Sig[j] * pref * phi) * (si * s64[j]);
             } else {
                 const double4_16a xj = X64[j];
                 const double a[4] = {xi.x, xi.y, xi.z, xi.w}, b[4] = {xj.x, xj.y, xj.z, xj.w};
@@ -393,6 +493,15 @@ gp2s_status validate_hyper(gp2s_ctx *c, const gp2s_hyper *h)
     if (h->kind != GP2S_WENDLAND_C2 && h->kind != GP2S_WENDLAND_C6_PAPER) return set_err(c, GP2S_EINVAL, "unknown Wendland kind");
     if (h->kind == GP2S_WENDLAND_C6_PAPER && h->d > 3) return set_err(c, GP2S_EINVAL, "Eq. 3 C6 form is positive definite only for d <= 3");
     if (h->L > 0 && (!h->centers || !h->radii || !h->amps)) return set_err(c, GP2S_EINVAL, "bump arrays are NULL");
+    if (h->family != GP2S_KERNEL_PRODUCT && h->family != GP2S_KERNEL_WENDCONV)
+        return set_err(c, GP2S_EINVAL, "unknown kernel family");
+    if (h->family == GP2S_KERNEL_WENDCONV) {
+        if (!h->ell || (h->L > 0 && !h->G)) return set_err(c, GP2S_EINVAL, "ell / G arrays are NULL");
+        for (int k = 0; k < h->d; ++k)
+            if (!(h->ell[k] > 0.0) || !std::isfinite(h->ell[k])) return set_err(c, GP2S_EINVAL, "ell must be finite and > 0");
+        for (int e = 0; e < h->L * h->d; ++e)
+            if (!(h->G[e] >= 0.0) || !std::isfinite(h->G[e])) return set_err(c, GP2S_EINVAL, "G must be finite and >= 0");
+    }
     for (int l = 0; l < h->L; ++l) {
         if (!(h->radii[l] > 0.0) || !std::isfinite(h->radii[l]) || !std::isfinite(h->amps[l]))
             return set_err(c, GP2S_EINVAL, "bump radius must be > 0 and amplitudes finite");
@@ -414,12 +523,62 @@ KernelParams make_kernel_params(const gp2s_hyper *h)
     kp.sigma2 = h->sigma2;
     kp.beta = h->beta;
     kp.w0 = h->w0;
+    kp.family = h->family;
     for (int l = 0; l < h->L; ++l) {
         for (int k = 0; k < h->d; ++k) kp.centers[l * h->d + k] = h->centers[l * h->d + k];
         kp.radii[l] = h->radii[l];
         kp.amps[l] = h->amps[l];
     }
+    if (h->family == GP2S_KERNEL_WENDCONV) {
+        for (int k = 0; k < h->d; ++k) kp.ell[k] = h->ell[k];
+        for (int e = 0; e < h->L * h->d; ++e) kp.G[e] = h->G[e];
+    }
     return kp;
+}
+
+// Largest lambda_k(x_i) of the Wendland convolution's length-scale field over the points (per-CTA
+// maxima): the cell edge must cover r sqrt(max lambda), the farthest a stored pair can reach.
+template <int D>
+__global__ void k_wc_lammax(const double *__restrict__ X, int64_t n, KernelParams kp, double *__restrict__ part)
+{
+    __shared__ double sh[256];
+    double mx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double x[D], sig, lam[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = X[i * D + k];
+        wc_fields<D>(x, kp, sig, lam, nullptr);
+#pragma unroll
+        for (int k = 0; k < D; ++k) mx = fmax(mx, lam[k]);
+    }
+    sh[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+static gp2s_status wc_lambda_max(gp2s_ctx *c, const double *X, int64_t n, const KernelParams &kp, double *lmax)
+{
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), (int64_t)c->num_sms * 2));
+    GP2S_TRY(ensure(c, c->bbox_part, sizeof(double) * (size_t)(nb > 2 * kMaxDim * 304 ? nb : 2 * kMaxDim * 304) + 64));
+    double *part = c->bbox_part.as<double>();
+    switch (kp.d) {
+    case 1: k_wc_lammax<1><<<nb, 256, 0, c->stream>>>(X, n, kp, part); break;
+    case 2: k_wc_lammax<2><<<nb, 256, 0, c->stream>>>(X, n, kp, part); break;
+    case 3: k_wc_lammax<3><<<nb, 256, 0, c->stream>>>(X, n, kp, part); break;
+    default: k_wc_lammax<4><<<nb, 256, 0, c->stream>>>(X, n, kp, part); break;
+    }
+    GP2S_LAUNCH(c);
+    std::vector<double> h(nb);
+    GP2S_CUDA(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    double m = 0.0;
+    for (double v : h) m = std::fmax(m, v);
+    *lmax = m;
+    return GP2S_OK;
 }
 
 // Order-independent 64-bit fingerprint of X (n x d FP64): the sum over elements of a SplitMix64-style
@@ -458,7 +617,8 @@ static void launch_bumps(gp2s_ctx *c, int64_t n, const KernelParams &kp, int *db
 {
     const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
     k_bumps<D><<<gb, 256, 0, c->stream>>>(c->Xs64.as<double4_16a>(), n, kp, c->B64.as<double>(), c->B32.as<float>(),
-                                          c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad);
+                                          c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad,
+                                          c->wc_lam.as<double4_16a>(), c->wc_sig.as<double>());
 }
 
 template <int D>
@@ -467,7 +627,8 @@ static void launch_values(gp2s_ctx *c, int64_t n, const KernelParams &kp, bool m
     const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 32);
     k_values64<D><<<gb, 256, 0, c->stream>>>(c->Xs64.as<double4_16a>(), c->rowptr.as<int32_t>(), c->col.as<int32_t>(), n,
                                              kp, c->B64.as<double>(), c->s64.as<double>(), c->val64.as<double>(),
-                                             mixed ? c->val32.as<float>() : nullptr);
+                                             mixed ? c->val32.as<float>() : nullptr, c->wc_lam.as<double4_16a>(),
+                                             c->wc_sig.as<double>());
 }
 
 // Bump tables (FP64 and FP32), the diagonal and the Jacobi scales of the current points.
@@ -545,7 +706,7 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     const int d = h->d;
     uint64_t xhash = 0;
     GP2S_TRY(hash_x(c, X_dev, n * d, &xhash));
-    if (o->pattern_cache == 0 && c->pat_valid && c->pat_n == n && c->pat_d == d &&
+    if (o->pattern_cache == 0 && h->family == GP2S_KERNEL_PRODUCT && c->pat_valid && c->pat_n == n && c->pat_d == d &&
         std::memcmp(&c->pat_r, &h->r, sizeof(double)) == 0 && c->pat_exact == o->exact_support &&
         c->pat_precision == o->precision && c->pat_hash == xhash)
         return refresh_values(c, h, o);
@@ -565,7 +726,18 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     GridParams g;
     std::memset(&g, 0, sizeof(g));
     g.d = d;
-    double h_cell = h->r * (1.0 + std::ldexp(1.0, -20));
+    // the farthest a stored pair reaches: r (product kernel), r sqrt(max lambda) (convolution)
+    double r_eff = h->r;
+    if (h->family == GP2S_KERNEL_WENDCONV) {
+        double lmax = 0.0;
+        GP2S_TRY(ensure(c, c->wc_lam, sizeof(double4_16a) * (size_t)n));
+        GP2S_TRY(ensure(c, c->wc_sig, sizeof(double) * (size_t)n));
+        GP2S_TRY(wc_lambda_max(c, X_dev, n, make_kernel_params(h), &lmax));
+        if (!(lmax > 0.0) || !std::isfinite(lmax)) return set_err(c, GP2S_EINVAL, "length-scale field not finite");
+        r_eff = h->r * std::sqrt(lmax) * (1.0 + std::ldexp(1.0, -30));
+        A.wc_lmax = lmax;
+    }
+    double h_cell = r_eff * (1.0 + std::ldexp(1.0, -20));
     double M = 0.0;
     for (int k = 0; k < d; ++k) {
         M = std::fmax(M, std::fmax(std::fabs(box[k]), std::fabs(box[kMaxDim + k])));
@@ -594,18 +766,20 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     }
     SupportParams sp;
     sp.r2 = h->r * h->r;
+    const double re2 = r_eff * r_eff;
     const double u = std::ldexp(1.0, -24);
-    const double ratio = M / h->r;
-    bool exact = o->exact_support != 0 || ratio > 1e6 || sp.r2 < 1e-30 || M > 1e18;
+    const double ratio = M / r_eff;
+    bool exact = o->exact_support != 0 || ratio > 1e6 || re2 < 1e-30 || M > 1e18;
     double delta = 32.0 * u + 16.0 * d * u * u * ratio;
     if (exact) {
         sp.thr_lo = -1.0f;
         sp.thr_hi = FLT_MAX;
         delta = INFINITY;
     } else {
-        sp.thr_lo = round_down_f(sp.r2 * (1.0 - delta));
-        sp.thr_hi = round_up_f(sp.r2 * (1.0 + delta));
+        sp.thr_lo = round_down_f(re2 * (1.0 - delta));
+        sp.thr_hi = round_up_f(re2 * (1.0 + delta));
     }
+    if (h->family == GP2S_KERNEL_WENDCONV) sp.thr_lo = -1.0f;   // the FP32 test only rejects
 
     // ---- sort, permute, cells ----
     GP2S_TRY(geom_sort(c, X_dev, n, g));
@@ -643,6 +817,7 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     a.ncells = ncells;
     a.B32 = c->B32.as<float>();
     a.s32 = c->s32.as<float>();
+    a.Lam = c->wc_lam.as<double4_16a>();
     a.rowcnt = c->rowcnt.as<int32_t>();
     a.stats = stats;
     if (nitems > 0) GP2S_TRY(dispatch_assemble<false>(c, d, a, g, sp, kp, nitems));

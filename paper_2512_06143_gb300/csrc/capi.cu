@@ -159,7 +159,9 @@ static gp2s_status validate_opts(gp2s_ctx *c, const gp2s_opts *o)
     if (!o) return set_err(c, GP2S_EINVAL, "opts is NULL");
     if (o->precision != GP2S_PREC_FP64 && o->precision != GP2S_PREC_MIXED) return set_err(c, GP2S_EINVAL, "bad precision");
     if (o->logdet < GP2S_LOGDET_AUTO || o->logdet > GP2S_LOGDET_SLQ) return set_err(c, GP2S_EINVAL, "bad logdet method");
-    if (o->probes < 0 || o->probes > 128 || o->probes % 32 != 0) return set_err(c, GP2S_EINVAL, "probes must be 0, 32, 64, 96 or 128");
+    if (!(o->probes == 0 || o->probes == 16 || o->probes == 32 || o->probes == 48 || o->probes == 64 ||
+          o->probes == 96 || o->probes == 128))
+        return set_err(c, GP2S_EINVAL, "probes must be 0, 16, 32, 48, 64, 96 or 128");
     if (o->lanczos_steps < 1 || o->lanczos_steps > 4096) return set_err(c, GP2S_EINVAL, "lanczos_steps must be in 1..4096");
     if (o->max_iter < 1) return set_err(c, GP2S_EINVAL, "max_iter must be >= 1");
     if (!(o->tol_inner > 0.0) || !(o->tol_refine > 0.0) || !(o->tol_probe > 0.0)) return set_err(c, GP2S_EINVAL, "tolerances must be > 0");
@@ -248,6 +250,11 @@ void gp2s_opts_default(gp2s_opts *o)
 
 int32_t gp2s_num_params(int32_t d, int32_t L) { return L * (d + 2) + 2; }
 
+int32_t gp2s_num_params_family(int32_t d, int32_t L, int32_t family)
+{
+    return family == GP2S_KERNEL_WENDCONV ? L * (2 * d + 2) + d + 3 : L * (d + 2) + 2;
+}
+
 gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
 {
     if (!ctx) return GP2S_EINVAL;
@@ -288,7 +295,7 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->Z, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
                       &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_tpart, &c->rb_seg,
                       &c->bj_Minv, &c->bj_ld, &c->bj_Minv_y, &c->post_X, &c->post_B, &c->post_cnt,
-                      &c->post_part, &c->mr_vec, &c->mc_X, &c->mc_y};
+                      &c->post_part, &c->mr_vec, &c->mc_X, &c->mc_y, &c->wc_lam, &c->wc_sig};
     for (DevBuf *b : bufs) free_buf(*b);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (gp2s_ctx *w : c->workers) gp2s_destroy(w);

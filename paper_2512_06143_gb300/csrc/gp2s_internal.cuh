@@ -20,11 +20,13 @@ constexpr int kWarp = 32;
 // Kernel hyperparameters passed by value to kernels (Eq. 3, Eq. 7, Sec. 4.3).
 // ------------------------------------------------------------------------------------------
 struct KernelParams {
-    int d, L, kind, pad;
+    int d, L, kind, family;
     double r, inv_r, sigma2, beta, w0;
     double centers[kMaxBumps * kMaxDim];
     double radii[kMaxBumps];
     double amps[kMaxBumps];
+    double ell[kMaxDim];              // Wendland convolution (family 1): base length-scale factors
+    double G[kMaxBumps * kMaxDim];    // family 1: weights of the length-scale field
 };
 
 // Geometry of the cell grid: cell edge h >= r, FP64 origin, F fine bits per dimension below the
@@ -69,6 +71,7 @@ struct Assembled {
     SupportParams sp{};
     gp2s_opts opts{};
     gp2s_assemble_info info{};
+    double wc_lmax = 0.0;     // Wendland convolution: largest lambda_k over the points (cell edge r sqrt)
 };
 
 struct Timer {
@@ -92,6 +95,8 @@ struct gp2s_ctx {
     gp2s::DevBuf cell_start, cell_flag, items, item_cnt;
     // bumps / diagonal
     gp2s::DevBuf B64, B32, D64, s64, s32;
+    // Wendland convolution: length-scale field (double4 per point) and signal field
+    gp2s::DevBuf wc_lam, wc_sig;
     // CSR
     gp2s::DevBuf rowcnt, rowptr, col, val32, val64, counters;
     // Krylov

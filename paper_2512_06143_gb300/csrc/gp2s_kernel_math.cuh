@@ -41,4 +41,20 @@ __device__ __forceinline__ T wendland_dt(int kind, int d, T t)
     return T(-30) * t * (u2 * u2);
 }
 
+// phi'(t) / t, finite at t = 0 (each form's derivative carries a factor t).
+template <class T>
+__device__ __forceinline__ T wendland_dt_over_t(int kind, int d, T t)
+{
+    if (!(t < T(1))) return T(0);
+    if (t < T(0)) t = T(0);
+    const T u = T(1) - t;
+    const T u2 = u * u;
+    if (kind == 1) {
+        const T u7 = u2 * u2 * u2 * u;
+        return T(-22) * u7 * ((T(16) * t + T(7)) * t + T(1));
+    }
+    if (d <= 3) return T(-20) * (u2 * u);
+    return T(-30) * (u2 * u2);
+}
+
 }  // namespace gp2s

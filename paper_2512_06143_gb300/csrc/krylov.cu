@@ -168,7 +168,7 @@ template <class T> struct Staged;
 template <> struct Staged<float> { int j; float v; };
 template <> struct Staged<double> { int j; int pad; double v; };
 
-template <class T, class V, int K, bool HAS_Y>
+template <class T, class V, int M, bool HAS_Y>
 __global__ void __launch_bounds__(kSpmmThreads, 1)
 k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const V *__restrict__ val,
        int64_t n, const int32_t *__restrict__ row_split, const T *__restrict__ py, const T *__restrict__ pz,
@@ -176,7 +176,9 @@ k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, cons
        const int *__restrict__ active)
 {
     using Acc = typename AccOf<T>::type;
-    constexpr int M = 32 * K;
+    // K columns per lane; with M < 32 (or not a multiple of 32) the last lanes hold none
+    constexpr int K = (M + 31) / 32;
+    const bool lon = (threadIdx.x & 31) * K < M;
     __shared__ Staged<T> stage[kSpmmWarps][kWarp];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t r_begin = row_split[blockIdx.x];
@@ -209,14 +211,14 @@ k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, cons
                 for (int t = 0; t < cnt; ++t) {
                     const Staged<T> s = stage[wid][t];
                     T pv[K > 0 ? K : 1];
-                    load_k<T, (K > 0 ? K : 1)>(pz + (int64_t)s.j * M + lane * K, pv);
+                    if (lon) load_k<T, (K > 0 ? K : 1)>(pz + (int64_t)s.j * M + lane * K, pv);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc[k] += s.v * pv[k];
+                    for (int k = 0; k < K; ++k) acc[k] += lon ? s.v * pv[k] : T(0);
                 }
                 __syncwarp();
             }
         }
-        if (K > 0) {
+        if (K > 0 && lon) {
             store_k<T, (K > 0 ? K : 1)>(qz + i * M + lane * K, acc);
             T pi[K > 0 ? K : 1];
             load_k<T, (K > 0 ? K : 1)>(pz + i * M + lane * K, pi);
@@ -238,14 +240,18 @@ k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, cons
     __shared__ double red[HW][M + 1];
     if (wid >= HW) {
         if (HAS_Y && lane == 0) red[wid - HW][M] = dy.value();
+        if (lon) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[wid - HW][lane * K + k] = dz[k].value();
+            for (int k = 0; k < K; ++k) red[wid - HW][lane * K + k] = dz[k].value();
+        }
     }
     __syncthreads();
     if (wid < HW) {
         if (HAS_Y && lane == 0) red[wid][M] += dy.value();
+        if (lon) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[wid][lane * K + k] += dz[k].value();
+            for (int k = 0; k < K; ++k) red[wid][lane * K + k] += dz[k].value();
+        }
     }
     __syncthreads();
     for (int cidx = threadIdx.x; cidx < M + 1; cidx += kSpmmThreads) {
@@ -618,7 +624,7 @@ struct CGBuffers {
     void *zz, *zy;   // preconditioned residuals (block-Jacobi PCG)
 };
 
-template <int K>
+template <int KH>
 gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts);
 
 // y-only SpMV (the y column after every probe column has stopped, and the refinement solves):
@@ -706,10 +712,9 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
     const int32_t *rp = c->rowptr.as<int32_t>(), *cl = c->col.as<int32_t>();
     const T *py = (const T *)B.py, *pz = (const T *)B.pz;
     T *qy = (T *)B.qy, *qz = (T *)B.qz;
-#define GP2S_SPMM_CASE(KK, HY)                                                                    \
-    k_spmm<T, V, KK, HY><<<nb, kSpmmThreads, 0, c->stream>>>(rp, cl, val, A.n, rsplit, py, pz, qy, qz, \
+#define GP2S_SPMM_CASE(MM, HY)                                                                    \
+    k_spmm<T, V, MM, HY><<<nb, kSpmmThreads, 0, c->stream>>>(rp, cl, val, A.n, rsplit, py, pz, qy, qz, \
                                                              part, pstride, active)
-    int K = m / 32;
     // multi-RHS launches: algorithmic bytes = values + column indices + row pointers + every input
     // and output element once
     const bool counted = m > 0;
@@ -733,16 +738,18 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
         GP2S_CUDA(c, cudaEventRecord(ev_a, c->stream));
     }
     if (rb_launch<T>(c, m, has_y)) {
-        switch (K) {
-        case 1: GP2S_TRY(launch_rb<1>(c, B, part, pstride, nb, nparts)); break;
-        case 2: GP2S_TRY(launch_rb<2>(c, B, part, pstride, nb, nparts)); break;
-        case 3: GP2S_TRY(launch_rb<3>(c, B, part, pstride, nb, nparts)); break;
-        default: GP2S_TRY(launch_rb<4>(c, B, part, pstride, nb, nparts)); break;
+        switch (m) {
+        case 16: GP2S_TRY(launch_rb<1>(c, B, part, pstride, nb, nparts)); break;
+        case 32: GP2S_TRY(launch_rb<2>(c, B, part, pstride, nb, nparts)); break;
+        case 48: GP2S_TRY(launch_rb<3>(c, B, part, pstride, nb, nparts)); break;
+        case 64: GP2S_TRY(launch_rb<4>(c, B, part, pstride, nb, nparts)); break;
+        case 96: GP2S_TRY(launch_rb<6>(c, B, part, pstride, nb, nparts)); break;
+        default: GP2S_TRY(launch_rb<8>(c, B, part, pstride, nb, nparts)); break;
         }
         if (ev_b) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
         return GP2S_OK;
     }
-    if (has_y && K == 0) {
+    if (has_y && m == 0) {
         const int nbv = (int)std::min<int64_t>(std::min(kSpmvBlocks, pstride),
                                                std::max<int64_t>(1, ceil_div(A.n * kWarp, kSpmvThreads)));
         k_spmv_y<T, V><<<nbv, kSpmvThreads, 0, c->stream>>>(rp, cl, val, A.n, py, qy, part);
@@ -752,19 +759,23 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
         return GP2S_OK;
     }
     if (has_y) {
-        switch (K) {
+        switch (m) {
         case 0: GP2S_SPMM_CASE(0, true); break;
-        case 1: GP2S_SPMM_CASE(1, true); break;
-        case 2: GP2S_SPMM_CASE(2, true); break;
-        case 3: GP2S_SPMM_CASE(3, true); break;
-        default: GP2S_SPMM_CASE(4, true); break;
+        case 16: GP2S_SPMM_CASE(16, true); break;
+        case 32: GP2S_SPMM_CASE(32, true); break;
+        case 48: GP2S_SPMM_CASE(48, true); break;
+        case 64: GP2S_SPMM_CASE(64, true); break;
+        case 96: GP2S_SPMM_CASE(96, true); break;
+        default: GP2S_SPMM_CASE(128, true); break;
         }
     } else {
-        switch (K) {
-        case 1: GP2S_SPMM_CASE(1, false); break;
-        case 2: GP2S_SPMM_CASE(2, false); break;
-        case 3: GP2S_SPMM_CASE(3, false); break;
-        default: GP2S_SPMM_CASE(4, false); break;
+        switch (m) {
+        case 16: GP2S_SPMM_CASE(16, false); break;
+        case 32: GP2S_SPMM_CASE(32, false); break;
+        case 48: GP2S_SPMM_CASE(48, false); break;
+        case 64: GP2S_SPMM_CASE(64, false); break;
+        case 96: GP2S_SPMM_CASE(96, false); break;
+        default: GP2S_SPMM_CASE(128, false); break;
         }
     }
 #undef GP2S_SPMM_CASE
@@ -862,21 +873,20 @@ struct RBWork {
     unsigned int pad;
 };
 
-template <int K, bool HAS_Y>
-__global__ void __launch_bounds__(RBCfg<K>::threads, 1)
+template <int KH, bool HAS_Y>
+__global__ void __launch_bounds__(RBCfg<KH>::threads, 1)
 k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, const float *__restrict__ uval,
           int64_t n, const float *__restrict__ py, const float *__restrict__ pz, float *__restrict__ qy,
           float *__restrict__ qz, double *__restrict__ part, int pstride, RBWork *__restrict__ work,
           int tile_blocks, int ntiles, double *__restrict__ tpart, int *__restrict__ seg_cnt, int seg_tiles)
 {
-    constexpr int M = 32 * K;
+    constexpr int M = 16 * KH;
     // Each half-warp covers all M probe columns (KH = M / 16 per lane) and the two halves take
     // alternate union entries of the same row block: one shared-memory broadcast of an entry's
     // column and 8 values then feeds 8 x KH products per lane (twice the products per staged entry
     // of a lane-per-column layout), and every lane keeps D independent 4 KH-byte gathers in flight.
-    constexpr int KH = 2 * K;
-    constexpr int D = K >= 3 ? 4 : 8;
-    constexpr int W = RBCfg<K>::warps;
+    constexpr int D = KH >= 6 ? 4 : 8;
+    constexpr int W = RBCfg<KH>::warps;
     extern __shared__ __align__(16) unsigned char rb_sh[];
     int *s_col = reinterpret_cast<int *>(rb_sh);                                    // W x 32
     float4 *s_val = reinterpret_cast<float4 *>(rb_sh + sizeof(int) * W * kWarp);  // W x 32 x 2
@@ -1065,18 +1075,16 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
         if (last) {
             __threadfence();
             const double *q = tpart + (int64_t)sg * seg_tiles * (M + 1);
-            double sz[K], sy = 0.0;
-#pragma unroll
-            for (int k = 0; k < K; ++k) sz[k] = 0.0;
+            // column cc = lane, lane + 32, ...: the segment's tiles in tile order
+            for (int cc = lane; cc < M; cc += kWarp) {
+                double sz = 0.0;
 #pragma unroll 4
-            for (int i = 0; i < need; ++i) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) sz[k] += __ldcg(q + (int64_t)i * (M + 1) + 1 + lane * K + k);
-                if (lane == 0) sy += __ldcg(q + (int64_t)i * (M + 1));
+                for (int i = 0; i < need; ++i) sz += __ldcg(q + (int64_t)i * (M + 1) + 1 + cc);
+                part[(int64_t)(1 + cc) * pstride + sg] = sz;
             }
-#pragma unroll
-            for (int k = 0; k < K; ++k) part[(int64_t)(1 + lane * K + k) * pstride + sg] = sz[k];
             if (lane == 0) {
+                double sy = 0.0;
+                for (int i = 0; i < need; ++i) sy += __ldcg(q + (int64_t)i * (M + 1));
                 part[sg] = sy;
                 seg_cnt[sg] = 0;
             }
@@ -1096,10 +1104,10 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
     }
 }
 
-template <int K>
+template <int KH>
 size_t rb_smem()
 {
-    constexpr int W = RBCfg<K>::warps;
+    constexpr int W = RBCfg<KH>::warps;
     return sizeof(int) * W * kWarp + sizeof(float4) * W * kWarp * 2;
 }
 
@@ -1128,16 +1136,16 @@ inline RBTiles rb_tiles(int64_t nblk, int nb)
     return t;
 }
 
-template <int K>
+template <int KH>
 gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts)
 {
-    const size_t smem = rb_smem<K>();
-    auto kern = k_spmm_rb<K, true>;
+    const size_t smem = rb_smem<KH>();
+    auto kern = k_spmm_rb<KH, true>;
     GP2S_TRY(smem_attr(c, (const void *)kern, smem));
     const RBTiles tl = rb_tiles(ceil_div(c->A.n, kRB), nb);
-    GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (32 * K + 1)));
+    GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (16 * KH + 1)));
     RBWork *work = reinterpret_cast<RBWork *>(c->counters.as<char>() + kRBWorkOffset);
-    kern<<<tl.ctas, RBCfg<K>::threads, smem, c->stream>>>(c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
+    kern<<<tl.ctas, RBCfg<KH>::threads, smem, c->stream>>>(c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
                                                      c->rb_val.as<float>(), c->A.n, (const float *)B.py,
                                                      (const float *)B.pz, (float *)B.qy, (float *)B.qz, part,
                                                      pstride, work, tl.tile_blocks, tl.ntiles,

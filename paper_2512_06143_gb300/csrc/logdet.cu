@@ -604,6 +604,7 @@ extern "C" gp2s_status gp2s_lml_exact_noalloc(int64_t n, const double *X_dev, co
     if (n < 1 || n > kNoAllocMaxN) return GP2S_EINVAL;
     if (!X_dev || !y_dev || !out_dev) return GP2S_EINVAL;
     if (validate_hyper(nullptr, hyper) != GP2S_OK) return GP2S_EINVAL;
+    if (hyper->family != GP2S_KERNEL_PRODUCT) return GP2S_EINVAL;   // the product kernel only
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     // the scratch address is per device: a stream of another device would get this device's
     // address, so such a stream is refused (the legacy and per-thread default streams follow the

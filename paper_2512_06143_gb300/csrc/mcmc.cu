@@ -47,10 +47,7 @@ double std_normal(uint64_t seed, uint64_t counter)
     return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
 }
 
-struct Theta {
-    std::vector<double> v;   // [centers (L x d), radii (L), amps (L), r, sigma2]
-};
-
+// theta of either family: [centers, radii, amps, (G, ell, w0,) r, sigma2]
 gp2s_hyper hyper_from(const gp2s_hyper &h0, const std::vector<double> &th)
 {
     gp2s_hyper h = h0;
@@ -58,9 +55,32 @@ gp2s_hyper hyper_from(const gp2s_hyper &h0, const std::vector<double> &th)
     h.centers = th.data();
     h.radii = th.data() + L * d;
     h.amps = th.data() + L * d + L;
-    h.r = th[L * d + 2 * L];
-    h.sigma2 = th[L * d + 2 * L + 1];
+    const int P = (int)th.size();
+    if (h0.family == GP2S_KERNEL_WENDCONV) {
+        h.G = th.data() + L * d + 2 * L;
+        h.ell = th.data() + 2 * L * d + 2 * L;
+        h.w0 = th[2 * L * d + 2 * L + d];
+    }
+    h.r = th[P - 2];
+    h.sigma2 = th[P - 1];
     return h;
+}
+
+std::vector<double> theta_of(const gp2s_hyper &h0)
+{
+    const int L = h0.L, d = h0.d;
+    std::vector<double> th;
+    for (int k = 0; k < L * d; ++k) th.push_back(h0.centers[k]);
+    for (int l = 0; l < L; ++l) th.push_back(h0.radii[l]);
+    for (int l = 0; l < L; ++l) th.push_back(h0.amps[l]);
+    if (h0.family == GP2S_KERNEL_WENDCONV) {
+        for (int k = 0; k < L * d; ++k) th.push_back(h0.G[k]);
+        for (int k = 0; k < d; ++k) th.push_back(h0.ell[k]);
+        th.push_back(h0.w0);
+    }
+    th.push_back(h0.r);
+    th.push_back(h0.sigma2);
+    return th;
 }
 
 bool write_checkpoint(const char *path, int done, const std::vector<double> &th, double lml,
@@ -103,7 +123,7 @@ gp2s_status mcmc_run(gp2s_ctx *c, int64_t n, const double *X, const double *y, c
     if (!h0 || !mo || !chain) return set_err(c, GP2S_EINVAL, "hyper / mcmc options / chain is NULL");
     const int L = h0->L, d = h0->d;
     if (d < 1 || d > kMaxDim || L < 0 || L > kMaxBumps) return set_err(c, GP2S_EINVAL, "bad d / L");
-    const int P = L * (d + 2) + 2;
+    const int P = h0->family == GP2S_KERNEL_WENDCONV ? L * (2 * d + 2) + d + 3 : L * (d + 2) + 2;
     const int nb = mo->nblocks;
     if (mo->iters < 0 || nb < 1 || nb > 64 || !mo->block || !mo->step)
         return set_err(c, GP2S_EINVAL, "iters >= 0, 1 <= nblocks <= 64, block and step arrays required");
@@ -114,14 +134,7 @@ gp2s_status mcmc_run(gp2s_ctx *c, int64_t n, const double *X, const double *y, c
     if (mo->checkpoint_every < 0) return set_err(c, GP2S_EINVAL, "checkpoint_every must be >= 0");
     gp2s_opts opts = *o;
     opts.pattern_cache = 0;
-    std::vector<double> th(P);
-    for (int k = 0; k < L * d; ++k) th[k] = h0->centers[k];
-    for (int l = 0; l < L; ++l) {
-        th[L * d + l] = h0->radii[l];
-        th[L * d + L + l] = h0->amps[l];
-    }
-    th[L * d + 2 * L] = h0->r;
-    th[L * d + 2 * L + 1] = h0->sigma2;
+    std::vector<double> th = theta_of(*h0);
     std::vector<int> acc_blocks(nb, 0);
     int start = 0;
     double cur = 0.0;

@@ -15,6 +15,7 @@
 // solve's accuracy whatever the precision the solve ran in.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "gp2s_geometry.cuh"
 #include "gp2s_kernel_math.cuh"
@@ -29,7 +30,8 @@ constexpr int kPostBatch = 64;   // test points per variance solve (the probe gr
 
 struct PostArgs {
     const double *Xs;             // ns x d, caller order
-    const double *Bs;             // ns x L bump values of the test points (FP64)
+    const double *Bs;             // ns x L bump values of the test points (FP64); Wendland convolution:
+                                  // ns x 5, [s, lambda_1..4]
     int64_t ns;
     const double4_16a *X64;       // training points, sorted order
     const double *B64;            // n x L
@@ -37,7 +39,42 @@ struct PostArgs {
     const int32_t *cell_start;    // ncells + 1
     const uint64_t *cell_key;     // ncells
     int64_t ncells;
+    const double4_16a *Lam;       // Wendland convolution: training lambda (sorted order)
+    const double *Sig;            // Wendland convolution: training s
+    int sw;                       // stencil half-width in cells (1; more when a test point's length
+                                  // scale exceeds every training point's)
 };
+
+// The Wendland convolution kernel's fields at a point (the assembly's arithmetic, Eq. 6 reading):
+// psi_l = (1 - |x - c_l|^2 / rho_l^2)^3, s = w0 + sum a_l psi_l, lambda_k = ell_k^2 + sum G_lk psi_l.
+template <int D>
+__device__ __forceinline__ void post_wc_fields(const double *x, const KernelParams &kp, double &sig, double *lam)
+{
+    double sg = 0.0, acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = 0.0;
+    for (int l = 0; l < kp.L; ++l) {
+        double q = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double dk = __dsub_rn(x[k], kp.centers[l * D + k]);
+            q = __dadd_rn(q, __dmul_rn(dk, dk));
+        }
+        const double rho = kp.radii[l];
+        const double s = __ddiv_rn(q, __dmul_rn(rho, rho));
+        double ps = 0.0;
+        if (s < 1.0) {
+            const double u = __dsub_rn(1.0, s);
+            ps = __dmul_rn(__dmul_rn(u, u), u);
+        }
+        sg = __dadd_rn(sg, __dmul_rn(kp.amps[l], ps));
+#pragma unroll
+        for (int k = 0; k < D; ++k) acc[k] = __dadd_rn(acc[k], __dmul_rn(kp.G[l * D + k], ps));
+    }
+    sig = __dadd_rn(kp.w0, sg);
+#pragma unroll
+    for (int k = 0; k < D; ++k) lam[k] = __dadd_rn(__dmul_rn(kp.ell[k], kp.ell[k]), acc[k]);
+}
 
 __device__ __forceinline__ int64_t lower_bound_key(const uint64_t *__restrict__ keys, int64_t n, uint64_t k)
 {
@@ -63,22 +100,23 @@ __device__ __forceinline__ void for_each_neighbour(const PostArgs &a, const Grid
         x[k] = a.Xs[t * D + k];
         double y = __dmul_rn(__dsub_rn(x[k], g.origin[k]), g.inv_h);   // cell units, as the training keys
         // far outside the grid no cell is adjacent: clamp before the integer conversion
-        y = fmin(fmax(y, -4.0), (double)g.dims[k] + 4.0);
+        y = fmin(fmax(y, -4.0 - a.sw), (double)g.dims[k] + 4.0 + a.sw);
         cc[k] = (int64_t)floor(y);
     }
     const double r2 = kp.r * kp.r;
     const int L = kp.L;
+    const int span = 2 * a.sw + 1;
     int ncomb = 1;
 #pragma unroll
-    for (int k = 0; k < D; ++k) ncomb *= 3;
+    for (int k = 0; k < D; ++k) ncomb *= span;
     for (int o = 0; o < ncomb; ++o) {
         int64_t nc[D];
         bool inside = true;
         int rest = o;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            nc[k] = cc[k] + (rest % 3) - 1;
-            rest /= 3;
+            nc[k] = cc[k] + (rest % span) - a.sw;
+            rest /= span;
             inside = inside && nc[k] >= 0 && nc[k] < g.dims[k];
         }
         if (!inside) continue;
@@ -90,6 +128,23 @@ __device__ __forceinline__ void for_each_neighbour(const PostArgs &a, const Grid
             const double4_16a xv = a.X64[p];
             const double xj[4] = {xv.x, xv.y, xv.z, xv.w};
             double q = 0.0;
+            if (kp.family == 1) {
+                // Q = sum_k D_k D_k / ((lambda*_k + lambda_jk) * 0.5), support Q < r^2 (Eq. 6)
+                const double4_16a lv = a.Lam[p];
+                const double lj[4] = {lv.x, lv.y, lv.z, lv.w};
+                const double *ls = a.Bs + t * 5 + 1;
+                double pref = 1.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const double dk = __dsub_rn(x[k], xj[k]);
+                    const double m = __dmul_rn(__dadd_rn(ls[k], lj[k]), 0.5);
+                    q = __dadd_rn(q, __ddiv_rn(__dmul_rn(dk, dk), m));
+                    pref = pref * (sqrt(sqrt(ls[k] * lj[k])) / sqrt(m));
+                }
+                if (!(q < r2)) continue;
+                fn(p, a.Bs[t * 5] * a.Sig[p] * pref * wendland<double>(kp.kind, D, sqrt(q) * kp.inv_r));
+                continue;
+            }
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const double dk = __dsub_rn(x[k], xj[k]);
@@ -118,6 +173,16 @@ __global__ void k_post_bumps(const double *__restrict__ Xs, int64_t ns, KernelPa
                              double *__restrict__ kss)
 {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns; t += (int64_t)gridDim.x * blockDim.x) {
+        if (kp.family == 1) {
+            double x[D], sig, lam[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) x[k] = Xs[t * D + k];
+            post_wc_fields<D>(x, kp, sig, lam);
+            Bs[t * 5] = sig;
+            for (int k = 0; k < 4; ++k) Bs[t * 5 + 1 + k] = k < D ? lam[k < D ? k : 0] : 1.0;
+            kss[t] = sig * sig;   // Q = 0 and the prefactor is 1 at zero distance
+            continue;
+        }
         double S = 0.0;
         for (int l = 0; l < kp.L; ++l) {
             double q = 0.0;
@@ -331,9 +396,10 @@ gp2s_status posterior(gp2s_ctx *c, int64_t ns, const double *Xs, double *mean, d
         GP2S_CUDA(c, cudaMemcpyAsync(c->post_X.p, Xs, sizeof(double) * (size_t)ns * d, cudaMemcpyHostToDevice, c->stream));
         xs_dev = c->post_X.as<double>();
     }
-    GP2S_TRY(ensure(c, c->post_B, sizeof(double) * (size_t)ns * (L > 0 ? L : 1) + sizeof(double) * (size_t)ns * 3));
+    const int bw = A.kp.family == 1 ? 5 : (L > 0 ? L : 1);   // per-test-point values
+    GP2S_TRY(ensure(c, c->post_B, sizeof(double) * (size_t)ns * bw + sizeof(double) * (size_t)ns * 3));
     double *Bs = c->post_B.as<double>();
-    double *kss = Bs + (size_t)ns * (L > 0 ? L : 1);
+    double *kss = Bs + (size_t)ns * bw;
     double *mean_buf = kss + ns, *var_buf = mean_buf + ns;
     const bool mean_dev = is_device_ptr_post(mean);
     const bool var_dev = var && is_device_ptr_post(var);
@@ -360,6 +426,22 @@ gp2s_status posterior(gp2s_ctx *c, int64_t ns, const double *Xs, double *mean, d
     pa.cell_start = c->cell_start.as<int32_t>();
     pa.cell_key = cell_keys_ptr(c, A.ncells);
     pa.ncells = A.ncells;
+    pa.Lam = c->wc_lam.as<double4_16a>();
+    pa.Sig = c->wc_sig.as<double>();
+    pa.sw = 1;
+    if (A.kp.family == 1) {
+        // a test point reaches |D_k| < r sqrt((lambda*_k + lambda_jk) / 2); cells have edge
+        // >= r sqrt(max training lambda): widen the stencil if a test point's field is larger
+        std::vector<double> hb((size_t)ns * 5);
+        GP2S_CUDA(c, cudaMemcpyAsync(hb.data(), Bs, sizeof(double) * (size_t)ns * 5, cudaMemcpyDeviceToHost, c->stream));
+        GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+        double lmax = 0.0;
+        for (int64_t t = 0; t < ns; ++t)
+            for (int k = 0; k < d; ++k) lmax = std::fmax(lmax, hb[(size_t)t * 5 + 1 + k]);
+        const double reach = std::sqrt(0.5 * (lmax + A.wc_lmax)) * A.kp.r;
+        pa.sw = std::max(1, (int)std::ceil(reach / A.gp.h * (1.0 + 1e-12)));
+        if (pa.sw > 4) return set_err(c, GP2S_EINVAL, "test points' length scales exceed the training grid's reach by more than 4 cells");
+    }
     switch (d) {
     case 1: GP2S_TRY(posterior_d<1>(c, pa, mean_out, var_out, kss, info)); break;
     case 2: GP2S_TRY(posterior_d<2>(c, pa, mean_out, var_out, kss, info)); break;
