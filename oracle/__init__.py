@@ -9,8 +9,9 @@ symmetric eigensolver, a k-d tree candidate search) as single steps.
 
 What each function follows:
   * ``assemble``        -- Sec. 4.6: every pair is evaluated; A = K + sigma^2 I (Sec. 3), with the
-                           product kernel of Sec. 4.1 / 4.3 (family 0) or the Wendland
-                           convolution kernel of Eq. 6, Sec. 4.2 (family 1).
+                           product kernel of Sec. 4.1 / 4.3 (family 0), the Wendland
+                           convolution kernel of Eq. 6, Sec. 4.2 (family 1), or the far-field
+                           form of Sec. 4.5 with a global core (family 2).
   * ``lml_exact``       -- the LML of Sec. 3 (Background) with m = 0, V = sigma^2 I, by a dense
                            Cholesky factorisation (solve and log-determinant exactly).
   * ``grad_exact``      -- the standard LML derivative 1/2 a^T dA a - 1/2 tr(A^{-1} dA) with the
@@ -140,6 +141,8 @@ class Hyper:
     def nparams(self) -> int:
         if self.family == 1:
             return self.L * (2 * self.d + 2) + self.d + 3
+        if self.family == 2:
+            return self.L * (self.d + 2) + 4
         return self.L * (self.d + 2) + 2
 
     def theta(self) -> np.ndarray:
@@ -149,6 +152,8 @@ class Hyper:
                 np.asarray(self.amps, np.float64)]
         if self.family == 1:
             head += [np.asarray(self.G, np.float64).ravel(), np.asarray(self.ell, np.float64), [self.w0]]
+        if self.family == 2:
+            head += [[float(np.asarray(self.ell, np.float64).ravel()[0]), self.w0]]
         return np.concatenate(head + [[self.r, self.sigma2]])
 
     def with_theta(self, th) -> "Hyper":
@@ -161,13 +166,16 @@ class Hyper:
             o = L * d + 2 * L
             kw.update(G=th[o:o + L * d].reshape(L, d).copy(), ell=th[o + L * d:o + L * d + d].copy(),
                       w0=float(th[o + L * d + d]))
+        if self.family == 2:
+            o = L * d + 2 * L
+            kw.update(ell=np.array([th[o]]), w0=float(th[o + 1]))
         return Hyper(**kw)
 
     def c(self):
         c = np.ascontiguousarray(np.asarray(self.centers, np.float64).reshape(self.L, self.d))
         rr = np.ascontiguousarray(np.asarray(self.radii, np.float64))
         aa = np.ascontiguousarray(np.asarray(self.amps, np.float64))
-        ee = np.ascontiguousarray(np.asarray(self.ell if self.ell is not None else np.ones(self.d), np.float64))
+        ee = np.ascontiguousarray(np.asarray(self.ell if self.ell is not None else np.ones(self.d), np.float64).ravel())
         gg = np.ascontiguousarray(np.asarray(self.G if self.G is not None else np.zeros((self.L, self.d)),
                                              np.float64).reshape(self.L, self.d))
         self._keep = [c, rr, aa, ee, gg]
@@ -259,7 +267,7 @@ def assemble(X, h: Hyper, method: str = "auto") -> CSR:
     X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, h.d))
     n = X.shape[0]
     if method == "auto":
-        method = "brute" if n <= 20000 else "tree"
+        method = "brute" if n <= 20000 or h.family == 2 else "tree"
     hr, _keep = h.c()
     rowptr = np.zeros(n + 1, np.int64)
     L = lib()
@@ -273,6 +281,8 @@ def assemble(X, h: Hyper, method: str = "auto") -> CSR:
         from scipy.spatial import cKDTree
         # enlarged search radius: a superset of every pair in the pattern (d2 < r*r; for the
         # Wendland convolution Q < r*r needs |D| < r sqrt(max lambda))
+        if h.family == 2:
+            raise ValueError("the far-field kernel's pattern is not a Euclidean ball: use method='brute'")
         rs = float(h.r) * (1.0 + 1e-9) + 1e-300
         if h.family == 1:
             pv = point_values(X, h)
@@ -293,7 +303,7 @@ def point_values(X, h: Hyper) -> np.ndarray:
     """Per-point kernel quantities: the bump values (family 0, n x L) or [s, lambda_1..d]
     (family 1, n x (d + 1))."""
     X = np.ascontiguousarray(np.asarray(X, np.float64).reshape(-1, h.d))
-    w = h.d + 1 if h.family == 1 else h.L
+    w = h.d + 1 if h.family == 1 else (2 * h.L if h.family == 2 else h.L)
     out = np.empty((X.shape[0], max(w, 1)))
     hr, _keep = h.c()
     lib().orc_point_values(hr, X.shape[0], _p(X), _p(out))

@@ -256,11 +256,44 @@ double orc_wc_q(int d, const double *xi, const double *xj, const double *li, con
     return q;
 }
 
-static int point_width(const orc_hyper *h) { return h->family == 1 ? h->d + 1 : h->L; }
+/* ------------------------------------------------------------------------------------ */
+/* Far-field kernel (Sec. 4.5, the extension for small core length scales), family 2:    */
+/*   k(xi, xj) = w0 phi(|xi - xj| / r) + kappa(|xi - xj|) sum_l b_l(xi) b_l(xj),          */
+/*   kappa(rho) = exp(-rho^2 / (2 lc^2)),                                                */
+/* a local Wendland term (k_core1 = w0, constant) plus the bumps' far-field term tied to a */
+/* globally supported squared-exponential core k_core2 = kappa (lc = ell[0]), active only  */
+/* inside the bumps' support.  Pattern: i == j, or d2 < r^2, or both points strictly inside */
+/* one bump (s_l < 1, s_l = q_l / (rho_l rho_l) in the FP64 order of Eq. 7's bumps).       */
+/* ------------------------------------------------------------------------------------ */
+static void ff_point(const orc_hyper *h, const double *x, double *out)
+{
+    const int L = h->L, d = h->d;
+    orc_bumps(h, x, out, NULL);
+    for (int l = 0; l < L; ++l) {
+        const double *c = h->centers + (size_t)l * d;
+        double q = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double dk = x[k] - c[k];
+            q = q + dk * dk;
+        }
+        double rho = h->radii[l];
+        out[L + l] = (q / (rho * rho)) < 1.0 ? 1.0 : 0.0;
+    }
+}
+
+static double ff_kappa(const orc_hyper *h, double q) { return exp(-q / (2.0 * h->ell[0] * h->ell[0])); }
+
+static int point_width(const orc_hyper *h)
+{
+    if (h->family == 1) return h->d + 1;
+    if (h->family == 2) return 2 * h->L;
+    return h->L;
+}
 
 static void point_values(const orc_hyper *h, const double *x, double *out)
 {
     if (h->family == 1) wc_point(h, x, out);
+    else if (h->family == 2) ff_point(h, x, out);
     else orc_bumps(h, x, out, NULL);
 }
 
@@ -268,12 +301,25 @@ static void point_values(const orc_hyper *h, const double *x, double *out)
 static int pair_in(const orc_hyper *h, const double *xi, const double *xj, const double *pi, const double *pj)
 {
     if (h->family == 1) return orc_wc_q(h->d, xi, xj, pi + 1, pj + 1) < h->r * h->r;
+    if (h->family == 2) {
+        if (orc_in_pattern(h->d, xi, xj, h->r)) return 1;
+        for (int l = 0; l < h->L; ++l)
+            if (pi[h->L + l] != 0.0 && pj[h->L + l] != 0.0) return 1;
+        return 0;
+    }
     return orc_in_pattern(h->d, xi, xj, h->r);
 }
 
 /* Kernel value k(xi, xj) (no noise term) from the points' values. */
 static double pair_value(const orc_hyper *h, const double *xi, const double *xj, const double *pi, const double *pj)
 {
+    if (h->family == 2) {
+        double q = orc_sqdist(h->d, xi, xj);
+        double loc = q < h->r * h->r ? h->w0 * orc_phi(h->kind, h->d, sqrt(q) / h->r) : 0.0;
+        double sb = 0.0;
+        for (int l = 0; l < h->L; ++l) sb = sb + pi[l] * pj[l];
+        return loc + ff_kappa(h, q) * sb;
+    }
     if (h->family != 1) return kernel_from_bumps(h, xi, xj, pi, pj);
     const int d = h->d;
     double q = orc_wc_q(d, xi, xj, pi + 1, pj + 1);
@@ -800,6 +846,33 @@ static void pair_grad_wc(const orc_hyper *h, const double *xi, const double *xj,
     g[oW + 1] = dr0;
 }
 
+/* dA_ij / dtheta for one stored pair of the far-field kernel (family 2); theta = [centers
+ * (L x d), radii (L), amps (L), lc, w0, r, sigma2]. */
+static void pair_grad_ff(const orc_hyper *h, const double *xi, const double *xj, int diag, const double *bi,
+                         const double *dbi, const double *bj, const double *dbj, double *g)
+{
+    const int d = h->d, L = h->L;
+    const int P = L * (d + 2) + 4;
+    double q = orc_sqdist(d, xi, xj);
+    double kap = ff_kappa(h, q);
+    int in_ball = diag || q < h->r * h->r;
+    double t = sqrt(q) / h->r;
+    double sb = 0.0;
+    for (int l = 0; l < L; ++l) sb = sb + bi[l] * bj[l];
+    for (int p = 0; p < P; ++p) g[p] = 0.0;
+    for (int l = 0; l < L; ++l) {
+        for (int k = 0; k < d; ++k)
+            g[l * d + k] = kap * (dbi[l * (d + 2) + k] * bj[l] + bi[l] * dbj[l * (d + 2) + k]);
+        g[L * d + l] = kap * (dbi[l * (d + 2) + d] * bj[l] + bi[l] * dbj[l * (d + 2) + d]);
+        g[L * d + L + l] = kap * (dbi[l * (d + 2) + d + 1] * bj[l] + bi[l] * dbj[l * (d + 2) + d + 1]);
+    }
+    double lc = h->ell[0];
+    g[P - 4] = sb * kap * q / (lc * lc * lc);                       /* d kappa / d lc */
+    g[P - 3] = in_ball ? orc_phi(h->kind, d, t) : 0.0;             /* d / d w0 */
+    g[P - 2] = in_ball ? h->w0 * orc_dphi(h->kind, d, t) * (-t / h->r) : 0.0;
+    g[P - 1] = diag ? 1.0 : 0.0;
+}
+
 /*
  * grad[P] = 1/2 sum over stored (i, j) of W_ij dA_ij.  The pattern is given in CSR
  * (rowptr, col; original index order).  If Wd (n x n) is non-NULL, W_ij = a_i a_j - Wd_ij;
@@ -858,7 +931,7 @@ int orc_grad_contract(int64_t n, const int64_t *rowptr, const int32_t *col, cons
 {
     const int d = h->d, L = h->L;
     if (h->family == 1) return grad_contract_wc(n, rowptr, col, X, h, a, m, U, V, Wd, grad);
-    const int P = L * (d + 2) + 2;
+    const int P = h->family == 2 ? L * (d + 2) + 4 : L * (d + 2) + 2;
     const int64_t chunk = 4096;
     double *B = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(L > 0 ? L : 1));
     double *dB = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * (size_t)(L * (d + 2) > 0 ? L * (d + 2) : 1));
@@ -887,9 +960,14 @@ int orc_grad_contract(int64_t n, const int64_t *rowptr, const int32_t *col, cons
                                          U[(size_t)j * m + s] * V[(size_t)i * m + s]);
                     w = a[i] * a[j] - tr / (double)m;
                 }
-                pair_grad(h, X + (size_t)i * d, X + (size_t)j * d, j == i,
-                          B + (size_t)i * L, dB + (size_t)i * L * (d + 2),
-                          B + (size_t)j * L, dB + (size_t)j * L * (d + 2), g);
+                if (h->family == 2)
+                    pair_grad_ff(h, X + (size_t)i * d, X + (size_t)j * d, j == i,
+                                 B + (size_t)i * L, dB + (size_t)i * L * (d + 2),
+                                 B + (size_t)j * L, dB + (size_t)j * L * (d + 2), g);
+                else
+                    pair_grad(h, X + (size_t)i * d, X + (size_t)j * d, j == i,
+                              B + (size_t)i * L, dB + (size_t)i * L * (d + 2),
+                              B + (size_t)j * L, dB + (size_t)j * L * (d + 2), g);
                 for (int p = 0; p < P; ++p) acc[p] = acc[p] + 0.5 * w * g[p];
             }
         }

@@ -217,6 +217,22 @@ def random_wendconv(seed: int, n: int, d: int, L: int = 3, r: float | None = Non
     return dict(name=f"random_wendconv[{seed}]", X=X, y=y, hyper=hyp)
 
 
+def random_farfield(seed: int, n: int, d: int, L: int = 4, r: float | None = None, radius: float = 0.12,
+                    lc: float = 0.3, w0: float = 1.0, sigma2: float = 1e-3) -> dict:
+    """Problems for the far-field kernel (Sec. 4.5): a local Wendland term of amplitude w0 plus the
+    bumps' far-field term on a squared-exponential core of length lc; small bumps (radius
+    `radius`, centers U[0,1]^d, amplitudes U(0.5, 1.5)) keep the far-field blocks sparse."""
+    rng = np.random.default_rng(seed)
+    X = rng.random((n, d))
+    y = _sines(X, rng, 0.02)
+    if r is None:
+        vol = math.pi ** (d / 2) / math.gamma(d / 2 + 1)
+        r = (30.0 / (n * vol)) ** (1.0 / d)
+    hyp = _hyper(d, r, sigma2, rng.random((L, d)), np.full(L, radius), rng.uniform(0.5, 1.5, L), w0=w0)
+    hyp.update(family=2, ell=np.array([lc]), G=np.zeros((L, d)))
+    return dict(name=f"random_farfield[{seed}]", X=X, y=y, hyper=hyp)
+
+
 def f1_1d_wendconv(seed: int = 0, n: int = 2000, r: float = 0.02) -> dict:
     """Sec. 5.1's 1-D test with the Wendland convolution kernel (the paper's choice for it)."""
     rng = np.random.default_rng(seed)
