@@ -536,7 +536,8 @@ def main():
 
 def batch_record(gp, torch, local, steps=1, warmup=1, seed=0) -> dict:
     """256 independent problems (N log-uniform in [2048, 65536], d in {1,2,3}, 10-200 entries per
-    row), one gp2s_lml_batched call per step (SLQ, 32 probes x 100 steps): the mixed-precision form
+    row), one gp2s_lml_batched call per step (SLQ, 16 probes x 100 steps, so 17 right-hand sides
+    per problem with y): the mixed-precision form
     timed with inputs on the device and from host buffers, and the plain FP64 GPU form timed once
     beside it, with the accuracy of the two against each other."""
     from paper_2512_06143_gb300 import workloads as W
@@ -545,8 +546,8 @@ def batch_record(gp, torch, local, steps=1, warmup=1, seed=0) -> dict:
              for w in ws_]
     host = [(w["X"], w["y"], gp.Hyper(**w["hyper"])) for w in ws_]
     ctx = gp.Context(local, torch.cuda.current_stream().cuda_stream)
-    mixed = gp.default_opts(precision=gp.PREC_MIXED, logdet=gp.LOGDET_SLQ, probes=32, lanczos_steps=100)
-    fp64 = gp.default_opts(precision=gp.PREC_FP64, logdet=gp.LOGDET_SLQ, probes=32, lanczos_steps=100, precond=1)
+    mixed = gp.default_opts(precision=gp.PREC_MIXED, logdet=gp.LOGDET_SLQ, probes=16, lanczos_steps=100)
+    fp64 = gp.default_opts(precision=gp.PREC_FP64, logdet=gp.LOGDET_SLQ, probes=16, lanczos_steps=100, precond=1)
     for _ in range(warmup):
         ctx.lml_batched(probs, mixed)
     stream = torch.cuda.current_stream()
@@ -578,7 +579,11 @@ def batch_record(gp, torch, local, steps=1, warmup=1, seed=0) -> dict:
     return {"metric": "batched LML evals/s", "value": len(probs) / t_mixed, "unit": "evals/s", "steps": steps,
             "warmup": warmup, "ms_per_step": 1000.0 * t_mixed, "higher_is_better": True,
             "config": {"workload": "batch", "problems": len(probs),
-                       "n_total": int(sum(p[0].shape[0] for p in probs)), "probes": 32, "lanczos_steps": 100},
+                       "n_total": int(sum(p[0].shape[0] for p in probs)), "probes": 16, "lanczos_steps": 100,
+                       "rhs_per_problem": 17},
+            "autotuner": {"configs_used": {str(k): int(sum(1 for i in infos if i["batch_config"] == k))
+                                           for k in (0, 1, 2, 3)},
+                          "configs": ["bj 64, eager", "bj 128, eager", "bj 64, graphs", "bj 128, graphs"]},
             "e2e": {"value": len(probs) / t_e2e, "unit": "evals/s",
                     "h2d_bytes_per_step": int(sum(w["X"].nbytes + w["y"].nbytes for w in ws_)),
                     "d2h_bytes_per_step": 8 * len(probs)},

@@ -83,10 +83,18 @@ typedef enum {
  *       lambda_k(x) = ell_k^2 + sum_l G_lk psi_l(x),   s(x) = w0 + sum_l amps_l psi_l(x),
  *       psi_l(x) = (1 - |x - c_l|^2 / rho_l^2)^3 inside the bump l (centers c, radii rho), else 0.
  *     Its hyperparameter vector is [centers (L x d), radii (L), amps (L), G (L x d), ell (d), w0,
- *     r, sigma2]; beta is unused. */
+ *     r, sigma2]; beta is unused.
+ *   GP2S_KERNEL_FARFIELD (Sec. 4.5, small core length scales): the bumps' far-field term tied to
+ *     a globally supported core, active only inside the bumps,
+ *       k = w0 phi(|xi - xj| / r) + kappa(|xi - xj|) sum_l b_l(xi) b_l(xj),
+ *       kappa(rho) = exp(-rho^2 / (2 lc^2)),  lc = ell[0],
+ *     stored where |xi - xj| < r or where both points lie strictly inside one bump (L <= 31).
+ *     Its hyperparameter vector is [centers (L x d), radii (L), amps (L), lc, w0, r, sigma2].
+ *     gp2s_posterior does not take this family. */
 typedef enum {
     GP2S_KERNEL_PRODUCT = 0,
-    GP2S_KERNEL_WENDCONV = 1
+    GP2S_KERNEL_WENDCONV = 1,
+    GP2S_KERNEL_FARFIELD = 2
 } gp2s_kernel_family;
 
 /* Kernel hyperparameters (Eq. 3, Eq. 6, Eq. 7, Sec. 4.3) and noise (Sec. 3).  Host memory. */
@@ -102,9 +110,9 @@ typedef struct {
     const double *centers;   /* host, L x d row-major */
     const double *radii;     /* host, L */
     const double *amps;      /* host, L */
-    int32_t family;          /* gp2s_kernel_family: GP2S_KERNEL_PRODUCT (0) or GP2S_KERNEL_WENDCONV (1) */
+    int32_t family;          /* gp2s_kernel_family: PRODUCT (0), WENDCONV (1) or FARFIELD (2) */
     int32_t reserved2;
-    const double *ell;       /* WENDCONV: host, d base length-scale factors (> 0) */
+    const double *ell;       /* WENDCONV: host, d base length-scale factors (> 0); FARFIELD: ell[0] = lc */
     const double *G;         /* WENDCONV: host, L x d weights (>= 0) of the length-scale field */
 } gp2s_hyper;
 
@@ -190,7 +198,9 @@ typedef struct {
     int32_t spmm_seg_tiles;  /* largest number of row-block tiles per reduction segment in the
                                 multi-RHS SpMM launches (1: every tile is its own segment) */
     int32_t pattern_reused;  /* 1 when the assembly reused the previous pattern */
-    int32_t reserved2;
+    int32_t batch_config;    /* gp2s_lml_batched: the autotuner's launch configuration for this
+                                problem (0: 64-row blocks, 1: 128-row blocks, 2 and 3: the same with
+                                CUDA-graph replay), -1 when not tuned */
 } gp2s_lml_info;
 
 typedef struct gp2s_ctx gp2s_ctx;
@@ -200,7 +210,8 @@ void gp2s_opts_default(gp2s_opts *opts);
 
 /* Number of hyperparameters of gp2s_lml_grad: L (d + 2) + 2 (product kernel). */
 int32_t gp2s_num_params(int32_t d, int32_t L);
-/* The same for a given family: L (d + 2) + 2 (PRODUCT) or L (2 d + 2) + d + 3 (WENDCONV). */
+/* The same for a given family: L (d + 2) + 2 (PRODUCT), L (2 d + 2) + d + 3 (WENDCONV) or
+ * L (d + 2) + 4 (FARFIELD). */
 int32_t gp2s_num_params_family(int32_t d, int32_t L, int32_t family);
 
 /* Create a context on CUDA device `device` that issues all work on `cuda_stream`
@@ -285,8 +296,12 @@ gp2s_status gp2s_lml_grad(gp2s_ctx *ctx, int64_t n, const double *X, const doubl
  * SLQ; EXACT only when opts->logdet == EXACT, AUTO is read as SLQ).  The problems are spread over
  * a pool of worker contexts owned by ctx, each with its own CUDA stream and workspace (at most 16,
  * or GP2S_BATCH_WORKERS), largest problems first; the call first synchronises ctx's stream so
- * that device inputs produced there are complete.  Results equal those of single gp2s_lml calls
- * with the same options bit for bit.  lml_host: B doubles (NaN for a failed problem).
+ * that device inputs produced there are complete.  In MIXED precision with precond = 2 and
+ * bj_block = 0 an autotuner picks, per shape class (family, d, floor(log2 n)), the block-Jacobi
+ * block size and CUDA-graph replay from timings of the class's first problems (kept in ctx for
+ * later calls; GP2S_BATCH_TUNE=0 turns it off).  Each problem's result equals that of a single
+ * gp2s_lml call with the same options and opts.bj_block = info.bj_block, bit for bit.
+ * lml_host: B doubles (NaN for a failed problem).
  * info_host: optional, B entries.  On failure the status and message are those of the first
  * failing problem ("problem b: ...").
  */

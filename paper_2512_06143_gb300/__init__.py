@@ -32,7 +32,7 @@ WENDLAND_C2, WENDLAND_C6_PAPER = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 LOGDET_AUTO, LOGDET_EXACT, LOGDET_SLQ = 0, 1, 2
 SOLVER_CG, SOLVER_MINRES = 0, 1
-KERNEL_PRODUCT, KERNEL_WENDCONV = 0, 1
+KERNEL_PRODUCT, KERNEL_WENDCONV, KERNEL_FARFIELD = 0, 1, 2
 
 
 class _Hyper(ctypes.Structure):
@@ -80,7 +80,7 @@ class LmlInfo(ctypes.Structure):
                 ("ms_total", ctypes.c_float), ("launches", ctypes.c_int64), ("spmm_launches", ctypes.c_int64),
                 ("spmm_bytes", ctypes.c_double), ("ms_spmm", ctypes.c_float), ("reserved_f", ctypes.c_float),
                 ("bj_block", ctypes.c_int32), ("spmm_seg_tiles", ctypes.c_int32),
-                ("pattern_reused", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("pattern_reused", ctypes.c_int32), ("batch_config", ctypes.c_int32)]
 
 
 class PosteriorInfo(ctypes.Structure):
@@ -190,6 +190,8 @@ class Hyper:
     def nparams(self) -> int:
         if self.family == KERNEL_WENDCONV:
             return self.L * (2 * self.d + 2) + self.d + 3
+        if self.family == KERNEL_FARFIELD:
+            return self.L * (self.d + 2) + 4
         return self.L * (self.d + 2) + 2
 
     def theta(self) -> np.ndarray:
@@ -199,6 +201,8 @@ class Hyper:
                 np.asarray(self.amps, np.float64)]
         if self.family == KERNEL_WENDCONV:
             head += [np.asarray(self.G, np.float64).ravel(), np.asarray(self.ell, np.float64), [self.w0]]
+        if self.family == KERNEL_FARFIELD:
+            head += [[float(np.asarray(self.ell, np.float64).ravel()[0]), self.w0]]
         return np.concatenate(head + [[self.r, self.sigma2]])
 
     def with_theta(self, th) -> "Hyper":
@@ -211,13 +215,16 @@ class Hyper:
             o = L * d + 2 * L
             kw.update(G=th[o:o + L * d].reshape(L, d).copy(), ell=th[o + L * d:o + L * d + d].copy(),
                       w0=float(th[o + L * d + d]))
+        if self.family == KERNEL_FARFIELD:
+            o = L * d + 2 * L
+            kw.update(ell=np.array([th[o]]), w0=float(th[o + 1]))
         return Hyper(**kw)
 
     def c(self) -> _Hyper:
         c = np.ascontiguousarray(np.asarray(self.centers, np.float64).reshape(self.L, self.d))
         r = np.ascontiguousarray(np.asarray(self.radii, np.float64))
         a = np.ascontiguousarray(np.asarray(self.amps, np.float64))
-        e = np.ascontiguousarray(np.asarray(self.ell if self.ell is not None else np.ones(self.d), np.float64))
+        e = np.ascontiguousarray(np.asarray(self.ell if self.ell is not None else np.ones(self.d), np.float64).ravel())
         g = np.ascontiguousarray(np.asarray(self.G if self.G is not None else np.zeros((self.L, self.d)),
                                             np.float64).reshape(self.L, self.d))
         self._keep = [c, r, a, e, g]

@@ -61,12 +61,16 @@ __device__ __forceinline__ double warp_sum_adj(double v)
 template <class T>
 __device__ __forceinline__ float to_f(T v) { return (float)v; }
 
-// sum_s (xa_s z_b,s + xb_s z_a,s) over the m probes (z as sign bits).
+// sum_s (xa_s z_b,s + xb_s z_a,s) over the m probes (z as sign bits), accumulated in the vectors'
+// precision (FP32 in MIXED, FP64 in the FP64 form).
+template <class T>
+__device__ __forceinline__ T flip_t(T x, uint32_t bit) { return bit ? -x : x; }
+
 template <class T, int M>
-__device__ __forceinline__ float probe_cross(const T *__restrict__ xa, const uint32_t *__restrict__ za,
-                                             const T *__restrict__ xb, const uint32_t *__restrict__ zb)
+__device__ __forceinline__ T probe_cross(const T *__restrict__ xa, const uint32_t *__restrict__ za,
+                                         const T *__restrict__ xb, const uint32_t *__restrict__ zb)
 {
-    float acc = 0.0f;
+    T acc = T(0);
 #pragma unroll
     for (int w = 0; w < (M + 31) / 32; ++w) {
         const uint32_t ba = za[w], bb = zb[w];
@@ -75,7 +79,7 @@ __device__ __forceinline__ float probe_cross(const T *__restrict__ xa, const uin
         for (int b = 0; b < NB; ++b) {
             const int s = w * 32 + b;
             if (s >= M) break;
-            acc += flip(to_f(xa[s]), (bb >> b) & 1u) + flip(to_f(xb[s]), (ba >> b) & 1u);
+            acc += flip_t<T>(xa[s], (bb >> b) & 1u) + flip_t<T>(xb[s], (ba >> b) & 1u);
         }
     }
     return acc;
@@ -106,7 +110,11 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
     constexpr int WZ = M > 0 ? (M + 31) / 32 : 1;
     const float inv_r = (float)kp.inv_r;
     const float inv2m = M > 0 ? 0.5f / (float)M : 0.0f;
-    double gr = 0.0, gs = 0.0;
+    // far-field kernel (family 2): kappa = exp(-q / (2 lc^2)) weights the bump term, w0 the taper
+    const bool ff = kp.family == 2;
+    const float lc = ff ? (float)kp.ell[0] : 1.0f;
+    const float inv2lc2 = 0.5f / (lc * lc);
+    double gr = 0.0, gs = 0.0, glc = 0.0, gw0 = 0.0;
     for (int64_t i = w0; i < g.n; i += nw) {
         const float4 hi_i = g.Xhi[i], lo_i = g.Xlo[i];
         const float ai = (float)g.a[i];
@@ -117,7 +125,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
         for (int w = 0; w < WZ; ++w) zi[w] = M > 0 ? g.zbits[i * WZ + w] : 0u;
         float Hacc[kMaxBumps];
         for (int l = 0; l < L; ++l) Hacc[l] = 0.0f;
-        float grr = 0.0f, gss = 0.0f;
+        float grr = 0.0f, gss = 0.0f, glcr = 0.0f, gw0r = 0.0f;
         const int p1 = g.rowptr[i + 1];
         for (int p = g.rowptr[i] + lane; p < p1; p += 32) {
             const int j = g.col[p];
@@ -128,7 +136,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
                 uint32_t zj[WZ];
 #pragma unroll
                 for (int w = 0; w < WZ; ++w) zj[w] = g.zbits[(int64_t)j * WZ + w];
-                tr = probe_cross<T, M>(Ui, zi, U + (int64_t)j * M, zj);
+                tr = (float)probe_cross<T, M>(Ui, zi, U + (int64_t)j * M, zj);
             }
             const float W = ai * aj - si * sj * tr * inv2m;
             if (j == i) {
@@ -148,13 +156,20 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
             const float phi = wendland<float>(kp.kind, D, t);
             const float dphi_dr = -wendland_dt<float>(kp.kind, D, t) * t * inv_r;
             float S = 0.0f;
-            const float pw = phi * W;
+            const float kap = ff ? expf(-q * inv2lc2) : 1.0f;
+            const float pw = (ff ? kap : phi) * W;
             for (int l = 0; l < L; ++l) {
                 const float bj = g.B32[(int64_t)j * L + l];
                 S = fmaf(g.B32[i * L + l], bj, S);
                 Hacc[l] = fmaf(pw, bj, Hacc[l]);
             }
-            grr += (S + (float)kp.w0) * dphi_dr * W;
+            if (ff) {
+                grr += (float)kp.w0 * dphi_dr * W;
+                glcr += S * kap * q / (lc * lc * lc) * W;
+                gw0r += phi * W;
+            } else {
+                grr += (S + (float)kp.w0) * dphi_dr * W;
+            }
         }
         // reduce the row's H over the warp
         for (int l = 0; l < L; ++l) {
@@ -165,27 +180,27 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
         }
         gr += (double)grr;
         gs += (double)gss;
+        glc += (double)glcr;
+        gw0 += (double)gw0r;
     }
-    // block reduction of g_r and g_s2 partial sums
-    __shared__ double sh[2][8];
+    // block reduction of the g_r, g_s2 (and far-field g_lc, g_w0) partial sums
+    __shared__ double sh[4][8];
+    double v4[4] = {gr, gs, glc, gw0};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        gr += __shfl_xor_sync(0xffffffffu, gr, o);
-        gs += __shfl_xor_sync(0xffffffffu, gs, o);
-    }
-    if (lane == 0) {
-        sh[0][threadIdx.x >> 5] = gr;
-        sh[1][threadIdx.x >> 5] = gs;
+    for (int k = 0; k < 4; ++k) {
+        v4[k] = warp_sum_adj(v4[k]);
+        if (lane == 0) sh[k][threadIdx.x >> 5] = v4[k];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[0][w]; b += sh[1][w]; }
-        g.part[blockIdx.x * 2 + 0] = a;
-        g.part[blockIdx.x * 2 + 1] = b;
+    if (threadIdx.x < 4) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += sh[threadIdx.x][w];
+        g.part[blockIdx.x * 4 + threadIdx.x] = a;
     }
 }
 
+// (The far-field kernel (family 2) takes the same pass with kappa in place of phi in H and the
+// extra sums g_lc = 1/2 sum W_ij S_ij dkappa/dlc and g_w0 = 1/2 sum W_ij phi_ij.)
 // g_{l,p} = sum_i d b_l(x_i) / d theta_{l,p} * H_il (FP64), per-block partials of the
 // L (d + 2) bump parameters: [centers (L x d), radii (L), amps (L)].
 // Thread t of a block handles bump l = t % L for points i = t / L, t / L + R, ... (R = threads / L
@@ -501,7 +516,8 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
     const Assembled &A = c->A;
     const int64_t n = A.n;
     const int d = A.d, L = A.L;
-    const int P = L * (d + 2) + 2;
+    const bool ff = A.kp.family == 2;
+    const int P = ff ? L * (d + 2) + 4 : L * (d + 2) + 2;
     if (!c->have_solution) return set_err(c, GP2S_ENOTREADY, "gradient needs the solve");
     if (m > 0 && !c->have_probes) return set_err(c, GP2S_ENOTREADY, "gradient needs the probe solves");
     const bool mixed = A.precision == GP2S_PREC_MIXED;
@@ -510,9 +526,9 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
     GP2S_TRY(ensure(c, c->H, sizeof(float) * (size_t)n * (L > 0 ? L : 1) + 64));
     const int nb = 152 * 8;
     const int nbf = 152 * 2;
-    GP2S_TRY(ensure(c, c->gpart, sizeof(double) * ((size_t)nb * 2 + (size_t)nbf * P + 64)));
+    GP2S_TRY(ensure(c, c->gpart, sizeof(double) * ((size_t)nb * 4 + (size_t)nbf * P + 64)));
     double *part = c->gpart.as<double>();
-    double *bpart = part + (size_t)nb * 2;
+    double *bpart = part + (size_t)nb * 4;
     if (m > 0) {
         unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * W, 256), 152 * 8);
         k_probe_bits<<<gb, 256, 0, c->stream>>>(c->perm.as<int32_t>(), n, m, A.opts.seed, c->Z.as<uint32_t>());
@@ -548,8 +564,8 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
         }
         GP2S_LAUNCH(c);
     }
-    std::vector<double> hp((size_t)nb * 2), hb((size_t)nbf * (Pb > 0 ? Pb : 1));
-    GP2S_CUDA(c, cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb * 2, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<double> hp((size_t)nb * 4), hb((size_t)nbf * (Pb > 0 ? Pb : 1));
+    GP2S_CUDA(c, cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb * 4, cudaMemcpyDeviceToHost, c->stream));
     if (Pb > 0)
         GP2S_CUDA(c, cudaMemcpyAsync(hb.data(), bpart, sizeof(double) * (size_t)nbf * Pb, cudaMemcpyDeviceToHost, c->stream));
     GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -557,8 +573,17 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
     for (int p = 0; p < P; ++p) grad_host[p] = 0.0;
     for (int b = 0; b < nbf && Pb > 0; ++b)
         for (int p = 0; p < Pb; ++p) grad_host[p] += hb[(size_t)b * Pb + p];
-    double gr = 0.0, gs = 0.0;
-    for (int b = 0; b < nb; ++b) { gr += hp[2 * b]; gs += hp[2 * b + 1]; }
+    double gr = 0.0, gs = 0.0, glc = 0.0, gw0 = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        gr += hp[4 * b];
+        gs += hp[4 * b + 1];
+        glc += hp[4 * b + 2];
+        gw0 += hp[4 * b + 3];
+    }
+    if (ff) {
+        grad_host[P - 4] = 0.5 * glc;
+        grad_host[P - 3] = 0.5 * gw0;
+    }
     grad_host[P - 2] = 0.5 * gr;
     grad_host[P - 1] = 0.5 * gs;
     return GP2S_OK;

@@ -10,6 +10,7 @@
 // counts (count pass) and the ordered, compacted column/value writes (fill pass): candidates are
 // visited in ascending sorted index, so columns come out ascending.
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -313,7 +314,7 @@ template <int D>
 __global__ void k_bumps(const double4_16a *__restrict__ X64, int64_t n, KernelParams kp,
                         double *__restrict__ B64, float *__restrict__ B32, double *__restrict__ D64,
                         double *__restrict__ s64, float *__restrict__ s32, int *__restrict__ bad,
-                        double4_16a *__restrict__ Lam, double *__restrict__ Sig)
+                        double4_16a *__restrict__ Lam, double *__restrict__ Sig, uint32_t *__restrict__ ffmask)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -344,22 +345,27 @@ __global__ void k_bumps(const double4_16a *__restrict__ X64, int64_t n, KernelPa
             continue;
         }
         double S = 0.0;
+        uint32_t mask = 0;
         for (int l = 0; l < kp.L; ++l) {
             double q = 0.0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                double dk = x[k] - kp.centers[l * D + k];
-                q = q + dk * dk;
+                double dk = __dsub_rn(x[k], kp.centers[l * D + k]);
+                q = __dadd_rn(q, __dmul_rn(dk, dk));
             }
             double rho = kp.radii[l];
-            double s = q / (rho * rho);
+            double s = __ddiv_rn(q, __dmul_rn(rho, rho));
             double e = 0.0;
-            if (s < 1.0) e = exp(kp.beta * (1.0 - 1.0 / (1.0 - s)));
+            if (s < 1.0) {
+                e = exp(kp.beta * (1.0 - 1.0 / (1.0 - s)));
+                mask |= 1u << l;   // inside bump l (the far-field kernel's pattern)
+            }
             double b = kp.amps[l] * e;
             B64[i * kp.L + l] = b;
             B32[i * kp.L + l] = (float)b;
             S = S + b * b;
         }
+        if (ffmask) ffmask[i] = mask;
         double Dii = (S + kp.w0) + kp.sigma2;
         D64[i] = Dii;
         if (!(Dii > 0.0) || !isfinite(Dii)) {
@@ -395,6 +401,21 @@ k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowp
             double v;
             if (j == i) {
                 v = 1.0;
+            } else if (kp.family == 2) {
+                // Sec. 4.5: w0 phi(|D| / r) inside the ball + kappa(|D|) sum_l b_l(x_i) b_l(x_j)
+                const double4_16a xj = X64[j];
+                const double a[4] = {xi.x, xi.y, xi.z, xi.w}, b[4] = {xj.x, xj.y, xj.z, xj.w};
+                double q = 0.0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    double dk = __dsub_rn(a[k], b[k]);
+                    q = __dadd_rn(q, __dmul_rn(dk, dk));
+                }
+                double S = 0.0;
+                for (int l = 0; l < L; ++l) S = fma(B64[i * L + l], B64[(int64_t)j * L + l], S);
+                const double loc = q < kp.r * kp.r ? kp.w0 * wendland<double>(kp.kind, D, sqrt(q) * kp.inv_r) : 0.0;
+                const double kap = exp(-q / (2.0 * kp.ell[0] * kp.ell[0]));
+                v = (loc + kap * S) * (si * s64[j]);
             } else if (kp.family == 1) {
                 // Eq. 6: s_i s_j prod_k (l_ik l_jk)^(1/4) / ((l_ik + l_jk) / 2)^(1/2) phi(sqrt(Q) / r)
                 const double4_16a li = Lam[i], lj = Lam[j];
@@ -424,6 +445,112 @@ k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowp
             if (val32) val32[p] = (float)v;   // the FP32 copy is the FP64 value rounded once
         }
     }
+}
+
+// Far-field kernel: bump l's members (points strictly inside it, ascending sorted index).
+__global__ void k_ff_flags(const uint32_t *__restrict__ mask, int64_t n, int l, int32_t *__restrict__ flag)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = (int32_t)((mask[i] >> l) & 1u);
+}
+
+__global__ void k_ff_members(const int32_t *__restrict__ flag, const int32_t *__restrict__ pos, int64_t n,
+                             int32_t *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) out[pos[i]] = (int32_t)i;
+}
+
+// Row i of the far-field pattern: the union of its Euclidean row and the member lists of the bumps
+// it lies in, by a warp merge with the list heads in lanes (lane 0: the Euclidean row, lane 1 + l:
+// bump l).  COUNT writes the union's length, FILL its columns (ascending, each once).
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+k_ff_union(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, const uint32_t *__restrict__ mask,
+           const int32_t *__restrict__ mptr, const int32_t *__restrict__ mcol, int64_t n,
+           const int32_t *__restrict__ uptr, int32_t *__restrict__ ucnt, int32_t *__restrict__ ucol)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < n; i += nw) {
+        const uint32_t mi = mask[i];
+        int pos = 0, end = 0;
+        if (lane == 0) {
+            pos = rowptr[i];
+            end = rowptr[i + 1];
+        } else if (lane <= 31 && ((mi >> (lane - 1)) & 1u)) {
+            pos = mptr[lane - 1];
+            end = mptr[lane];
+        }
+        const int *src = lane == 0 ? col : mcol;
+        int head = pos < end ? src[pos] : INT_MAX;
+        int64_t out = FILL ? uptr[i] : 0;
+        int emitted = 0;
+        for (;;) {
+            int mn = head;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            if (mn == INT_MAX) break;
+            if (FILL && lane == 0) ucol[out + emitted] = mn;
+            ++emitted;
+            if (head == mn) {
+                ++pos;
+                head = pos < end ? src[pos] : INT_MAX;
+            }
+        }
+        if (!FILL && lane == 0) ucnt[i] = emitted;
+    }
+}
+
+// Replace the Euclidean CSR by its union with the bumps' member blocks (far-field kernel).
+static gp2s_status far_field_union(gp2s_ctx *c, int64_t n, int L, int64_t *nnz)
+{
+    const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+    // member lists: one scan per bump
+    GP2S_TRY(ensure(c, c->ff_flag, sizeof(int32_t) * (size_t)(n + 1) * 2));
+    int32_t *flag = c->ff_flag.as<int32_t>(), *pos = flag + n + 1;
+    std::vector<int32_t> hptr(L + 1, 0);
+    std::vector<int64_t> cnt(L, 0);
+    for (int l = 0; l < L; ++l) {
+        k_ff_flags<<<gb, 256, 0, c->stream>>>(c->ff_mask.as<uint32_t>(), n, l, flag);
+        GP2S_LAUNCH(c);
+        GP2S_TRY(scan_counts_i32(c, flag, pos, n, &cnt[l]));
+        hptr[l + 1] = hptr[l] + (int32_t)cnt[l];
+    }
+    GP2S_TRY(ensure(c, c->ff_mptr, sizeof(int32_t) * (size_t)(L + 1)));
+    GP2S_TRY(ensure(c, c->ff_mcol, sizeof(int32_t) * (size_t)(hptr[L] > 0 ? hptr[L] : 1)));
+    GP2S_CUDA(c, cudaMemcpyAsync(c->ff_mptr.p, hptr.data(), sizeof(int32_t) * (L + 1), cudaMemcpyHostToDevice, c->stream));
+    for (int l = 0; l < L; ++l) {
+        if (cnt[l] == 0) continue;
+        k_ff_flags<<<gb, 256, 0, c->stream>>>(c->ff_mask.as<uint32_t>(), n, l, flag);
+        GP2S_LAUNCH(c);
+        int64_t t = 0;
+        GP2S_TRY(scan_counts_i32(c, flag, pos, n, &t));
+        k_ff_members<<<gb, 256, 0, c->stream>>>(flag, pos, n, c->ff_mcol.as<int32_t>() + hptr[l]);
+        GP2S_LAUNCH(c);
+    }
+    // union count -> scan -> fill
+    const unsigned gw = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 32);
+    GP2S_TRY(ensure(c, c->ff_ucnt, sizeof(int32_t) * (size_t)(n + 1)));
+    GP2S_TRY(ensure(c, c->ff_uptr, sizeof(int32_t) * (size_t)(n + 1)));
+    k_ff_union<false><<<gw, 256, 0, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->ff_mask.as<uint32_t>(),
+                                                 c->ff_mptr.as<int32_t>(), c->ff_mcol.as<int32_t>(), n, nullptr,
+                                                 c->ff_ucnt.as<int32_t>(), nullptr);
+    GP2S_LAUNCH(c);
+    int64_t unnz = 0;
+    GP2S_TRY(scan_counts_i32(c, c->ff_ucnt.as<int32_t>(), c->ff_uptr.as<int32_t>(), n, &unnz));
+    if (unnz > (int64_t)INT32_MAX - 1) return set_err(c, GP2S_EOVERFLOW, "far-field pattern exceeds int32 entries");
+    GP2S_TRY(ensure(c, c->ff_ucol, sizeof(int32_t) * (size_t)(unnz > 0 ? unnz : 1)));
+    k_ff_union<true><<<gw, 256, 0, c->stream>>>(c->rowptr.as<int32_t>(), c->col.as<int32_t>(), c->ff_mask.as<uint32_t>(),
+                                                c->ff_mptr.as<int32_t>(), c->ff_mcol.as<int32_t>(), n,
+                                                c->ff_uptr.as<int32_t>(), nullptr, c->ff_ucol.as<int32_t>());
+    GP2S_LAUNCH(c);
+    std::swap(c->rowptr, c->ff_uptr);
+    std::swap(c->col, c->ff_ucol);
+    std::swap(c->rowcnt, c->ff_ucnt);
+    *nnz = unnz;
+    return GP2S_OK;
 }
 
 __global__ void k_rowcnt_minmax(const int32_t *__restrict__ cnt, int64_t n, int *__restrict__ mm)
@@ -493,8 +620,13 @@ gp2s_status validate_hyper(gp2s_ctx *c, const gp2s_hyper *h)
     if (h->kind != GP2S_WENDLAND_C2 && h->kind != GP2S_WENDLAND_C6_PAPER) return set_err(c, GP2S_EINVAL, "unknown Wendland kind");
     if (h->kind == GP2S_WENDLAND_C6_PAPER && h->d > 3) return set_err(c, GP2S_EINVAL, "Eq. 3 C6 form is positive definite only for d <= 3");
     if (h->L > 0 && (!h->centers || !h->radii || !h->amps)) return set_err(c, GP2S_EINVAL, "bump arrays are NULL");
-    if (h->family != GP2S_KERNEL_PRODUCT && h->family != GP2S_KERNEL_WENDCONV)
+    if (h->family != GP2S_KERNEL_PRODUCT && h->family != GP2S_KERNEL_WENDCONV && h->family != GP2S_KERNEL_FARFIELD)
         return set_err(c, GP2S_EINVAL, "unknown kernel family");
+    if (h->family == GP2S_KERNEL_FARFIELD) {
+        if (!h->ell || !(h->ell[0] > 0.0) || !std::isfinite(h->ell[0]))
+            return set_err(c, GP2S_EINVAL, "the far-field core length ell[0] must be finite and > 0");
+        if (h->L > 31) return set_err(c, GP2S_EINVAL, "the far-field kernel takes at most 31 bumps");
+    }
     if (h->family == GP2S_KERNEL_WENDCONV) {
         if (!h->ell || (h->L > 0 && !h->G)) return set_err(c, GP2S_EINVAL, "ell / G arrays are NULL");
         for (int k = 0; k < h->d; ++k)
@@ -533,6 +665,7 @@ KernelParams make_kernel_params(const gp2s_hyper *h)
         for (int k = 0; k < h->d; ++k) kp.ell[k] = h->ell[k];
         for (int e = 0; e < h->L * h->d; ++e) kp.G[e] = h->G[e];
     }
+    if (h->family == GP2S_KERNEL_FARFIELD) kp.ell[0] = h->ell[0];
     return kp;
 }
 
@@ -618,7 +751,8 @@ static void launch_bumps(gp2s_ctx *c, int64_t n, const KernelParams &kp, int *db
     const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
     k_bumps<D><<<gb, 256, 0, c->stream>>>(c->Xs64.as<double4_16a>(), n, kp, c->B64.as<double>(), c->B32.as<float>(),
                                           c->D64.as<double>(), c->s64.as<double>(), c->s32.as<float>(), dbad,
-                                          c->wc_lam.as<double4_16a>(), c->wc_sig.as<double>());
+                                          c->wc_lam.as<double4_16a>(), c->wc_sig.as<double>(),
+                                          kp.family == 2 ? c->ff_mask.as<uint32_t>() : nullptr);
 }
 
 template <int D>
@@ -792,6 +926,7 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     const int L = h->L;
     GP2S_TRY(ensure(c, c->B64, sizeof(double) * (size_t)n * (L > 0 ? L : 1)));
     GP2S_TRY(ensure(c, c->B32, sizeof(float) * (size_t)n * (L > 0 ? L : 1)));
+    if (h->family == GP2S_KERNEL_FARFIELD) GP2S_TRY(ensure(c, c->ff_mask, sizeof(uint32_t) * (size_t)n));
     GP2S_TRY(ensure(c, c->D64, sizeof(double) * n));
     GP2S_TRY(ensure(c, c->s64, sizeof(double) * n));
     GP2S_TRY(ensure(c, c->s32, sizeof(float) * n));
@@ -837,6 +972,11 @@ gp2s_status assemble_problem(gp2s_ctx *c, int64_t n, const double *X_dev, const 
     a.rowptr = c->rowptr.as<int32_t>();
     a.col = c->col.as<int32_t>();
     if (nitems > 0) GP2S_TRY(dispatch_assemble<true>(c, d, a, g, sp, kp, nitems));
+    if (h->family == GP2S_KERNEL_FARFIELD) {
+        GP2S_TRY(far_field_union(c, n, L, &nnz));
+        if (mixed) GP2S_TRY(ensure(c, c->val32, sizeof(float) * (size_t)(nnz > 0 ? nnz : 1)));
+        GP2S_TRY(ensure(c, c->val64, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1)));
+    }
     GP2S_CUDA(c, cudaEventRecord(ev[3], c->stream));
 
     // ---- values: every stored pair in FP64 (and its FP32 rounding in MIXED precision) ----

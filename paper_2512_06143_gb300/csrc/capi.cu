@@ -252,7 +252,9 @@ int32_t gp2s_num_params(int32_t d, int32_t L) { return L * (d + 2) + 2; }
 
 int32_t gp2s_num_params_family(int32_t d, int32_t L, int32_t family)
 {
-    return family == GP2S_KERNEL_WENDCONV ? L * (2 * d + 2) + d + 3 : L * (d + 2) + 2;
+    if (family == GP2S_KERNEL_WENDCONV) return L * (2 * d + 2) + d + 3;
+    if (family == GP2S_KERNEL_FARFIELD) return L * (d + 2) + 4;
+    return L * (d + 2) + 2;
 }
 
 gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
@@ -276,6 +278,8 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (lim) c->mem_limit = (size_t)std::strtoull(lim, nullptr, 10);
     const char *gr = std::getenv("GP2S_GRAPHS");
     if (gr && std::strcmp(gr, "0") == 0) c->use_graphs = false;
+    const char *sp = std::getenv("GP2S_SPMM_PIPE");
+    if (sp) c->spmm_pipe = std::strcmp(sp, "0") != 0;
     const char *pa = std::getenv("GP2S_PC_ASYNC");
     if (pa && std::strcmp(pa, "0") == 0) c->pc_async = false;
     *ctx = c;
@@ -295,7 +299,8 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->Z, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
                       &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_tpart, &c->rb_seg,
                       &c->bj_Minv, &c->bj_ld, &c->bj_Minv_y, &c->post_X, &c->post_B, &c->post_cnt,
-                      &c->post_part, &c->mr_vec, &c->mc_X, &c->mc_y, &c->wc_lam, &c->wc_sig};
+                      &c->post_part, &c->mr_vec, &c->mc_X, &c->mc_y, &c->wc_lam, &c->wc_sig, &c->ff_mask,
+                      &c->ff_flag, &c->ff_mptr, &c->ff_mcol, &c->ff_ucnt, &c->ff_uptr, &c->ff_ucol};
     for (DevBuf *b : bufs) free_buf(*b);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     for (gp2s_ctx *w : c->workers) gp2s_destroy(w);
@@ -488,6 +493,7 @@ static gp2s_status lml_impl(gp2s_ctx *c, int64_t n, const double *X, const doubl
         info->bj_block = (A.precision == GP2S_PREC_MIXED && A.opts.precond == 2 && c->bj_valid) ? c->bj_size : 0;
         info->spmm_seg_tiles = c->spmm_seg_tiles;
         info->pattern_reused = A.info.pattern_reused;
+        info->batch_config = -1;
     }
     c->profile = false;
     return GP2S_OK;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -97,6 +99,8 @@ struct gp2s_ctx {
     gp2s::DevBuf B64, B32, D64, s64, s32;
     // Wendland convolution: length-scale field (double4 per point) and signal field
     gp2s::DevBuf wc_lam, wc_sig;
+    // far-field kernel: bump membership masks, member lists and the union pattern's buffers
+    gp2s::DevBuf ff_mask, ff_flag, ff_mptr, ff_mcol, ff_ucnt, ff_uptr, ff_ucol;
     // CSR
     gp2s::DevBuf rowcnt, rowptr, col, val32, val64, counters;
     // Krylov
@@ -113,6 +117,7 @@ struct gp2s_ctx {
     double bj_logdet = 0.0;
     bool probes_for_grad = false;   // the probe solves feed the Hutchinson gradient
     bool use_graphs = true;         // replay runs of CG iterations as CUDA graphs (GP2S_GRAPHS=0: off)
+    bool spmm_pipe = false;         // RB8 SpMM with double-buffered gathers (GP2S_SPMM_PIPE=1)
     bool pc_async = true;           // probe-group PCG step on the bulk-copy pipelined kernel
                                     // (GP2S_PC_ASYNC=0: the staged kernel)
     cudaStream_t capture_stream = nullptr;   // private stream the graphs are captured on
@@ -120,6 +125,14 @@ struct gp2s_ctx {
     std::vector<gp2s_ctx *> workers;
     std::vector<cudaStream_t> worker_streams;
     int batch_workers_max = 16;
+    // batched autotuner: per shape class, the summed score (seconds per point) and the number of
+    // problems each launch configuration ran, and which configurations were handed out
+    struct TuneState {
+        std::vector<double> score;
+        std::vector<int> count, issued;
+    };
+    std::map<int, TuneState> tune;
+    std::mutex tune_mu;
     // dense
     gp2s::DevBuf dense;
     // adjoint

@@ -873,7 +873,7 @@ struct RBWork {
     unsigned int pad;
 };
 
-template <int KH, bool HAS_Y>
+template <int KH, bool HAS_Y, bool PIPE>
 __global__ void __launch_bounds__(RBCfg<KH>::threads, 1)
 k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, const float *__restrict__ uval,
           int64_t n, const float *__restrict__ py, const float *__restrict__ pz, float *__restrict__ qy,
@@ -885,7 +885,8 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
     // alternate union entries of the same row block: one shared-memory broadcast of an entry's
     // column and 8 values then feeds 8 x KH products per lane (twice the products per staged entry
     // of a lane-per-column layout), and every lane keeps D independent 4 KH-byte gathers in flight.
-    constexpr int D = KH >= 6 ? 4 : 8;
+    // PD gathers per group: 8 in one batch, or 4 with the next group's 4 in flight (PIPE)
+    constexpr int PD = PIPE ? 4 : (KH >= 6 ? 4 : 8);
     constexpr int W = RBCfg<KH>::warps;
     extern __shared__ __align__(16) unsigned char rb_sh[];
     int *s_col = reinterpret_cast<int *>(rb_sh);                                    // W x 32
@@ -965,16 +966,9 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             const int npair = (cnt + 1) >> 1;
             const int *scol = s_col + wid * kWarp + half;
             const float4 *sval = s_val + (wid * kWarp + half) * 2;
-#pragma unroll 1
-            for (int u0 = 0; u0 < npair; u0 += D) {
-                int jj[D];
+            auto fma_group = [&](int u0, const float (&pv)[PD][KH]) {
 #pragma unroll
-                for (int d = 0; d < D; ++d) jj[d] = scol[2 * (u0 + d)];
-                float pv[D][KH];
-#pragma unroll
-                for (int d = 0; d < D; ++d) load_k<float, KH>(pz + (int64_t)jj[d] * M + hl * KH, pv[d]);
-#pragma unroll
-                for (int d = 0; d < D; ++d) {
+                for (int d = 0; d < PD; ++d) {
                     const float4 a0 = sval[4 * (u0 + d)], a1 = sval[4 * (u0 + d) + 1];
                     const float2 vp[kRB / 2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
                                                 make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
@@ -984,6 +978,35 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
 #pragma unroll
                         for (int rp = 0; rp < kRB / 2; ++rp) acc[rp][k] = __ffma2_rn(vp[rp], pk, acc[rp][k]);
                     }
+                }
+            };
+            auto load_group = [&](int u0, float (&pv)[PD][KH]) {
+                int jj[PD];
+#pragma unroll
+                for (int d = 0; d < PD; ++d) jj[d] = scol[2 * (u0 + d)];
+#pragma unroll
+                for (int d = 0; d < PD; ++d) load_k<float, KH>(pz + (int64_t)jj[d] * M + hl * KH, pv[d]);
+            };
+            if (PIPE) {
+                // two register buffers: the gathers of group g + 1 are in flight while group g's
+                // products run (a batch holds at most 16 / PD groups)
+                float pa[PD][KH], pb[PD][KH];
+                load_group(0, pa);
+#pragma unroll
+                for (int g = 0; g < 16 / PD; g += 2) {
+                    if (g * PD >= npair) break;
+                    if ((g + 1) * PD < npair) load_group((g + 1) * PD, pb);
+                    fma_group(g * PD, pa);
+                    if ((g + 1) * PD >= npair) break;
+                    if ((g + 2) * PD < npair) load_group((g + 2) * PD, pa);
+                    fma_group((g + 1) * PD, pb);
+                }
+            } else {
+#pragma unroll 1
+                for (int u0 = 0; u0 < npair; u0 += PD) {
+                    float pv[PD][KH];
+                    load_group(u0, pv);
+                    fma_group(u0, pv);
                 }
             }
             __syncwarp();
@@ -1140,7 +1163,8 @@ template <int KH>
 gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts)
 {
     const size_t smem = rb_smem<KH>();
-    auto kern = k_spmm_rb<KH, true>;
+    // the double-buffered form needs registers the wide column counts (KH >= 6) do not have
+    auto kern = (c->spmm_pipe && KH <= 4) ? k_spmm_rb<KH, true, (KH <= 4)> : k_spmm_rb<KH, true, false>;
     GP2S_TRY(smem_attr(c, (const void *)kern, smem));
     const RBTiles tl = rb_tiles(ceil_div(c->A.n, kRB), nb);
     GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (16 * KH + 1)));
@@ -1923,11 +1947,11 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         if (bjy == 128) GP2S_PCY_BJ(MODE, 128);                                                                     \
         else GP2S_PCY_BJ(MODE, 64);                                                                                 \
     } while (0)
-    // the probe group's UPDATE step on the bulk-copy pipelined kernel (FP32, m <= 64, 128-row
-    // blocks): one CTA per SM, x updated by the direction kernel.  With 64-row blocks the staged
+    // the probe group's UPDATE step on the bulk-copy pipelined kernel (FP32, m = 32 or 64 (the
+    // instantiated widths), 128-row blocks): one CTA per SM, x updated by the direction kernel.  With 64-row blocks the staged
     // kernel at several CTAs per SM measured faster (sphere_4d at N = 10M: 2.60 against 2.72 s per
     // evaluation), with 128-row blocks this one (clusters_3d at N = 1M: 1.78 against 1.85 s).
-    const bool pc_async = pc_avail && c->pc_async && m > 0 && m <= 64 && bjz == 128;
+    const bool pc_async = pc_avail && c->pc_async && (m == 32 || m == 64) && bjz == 128;
     const int pga = (int)std::min<int64_t>(c->num_sms, nblkz);
     int *dev_err = flags + 3;
     if (pc_async) {

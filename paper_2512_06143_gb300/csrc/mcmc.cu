@@ -61,6 +61,10 @@ gp2s_hyper hyper_from(const gp2s_hyper &h0, const std::vector<double> &th)
         h.ell = th.data() + 2 * L * d + 2 * L;
         h.w0 = th[2 * L * d + 2 * L + d];
     }
+    if (h0.family == GP2S_KERNEL_FARFIELD) {
+        h.ell = th.data() + L * d + 2 * L;
+        h.w0 = th[L * d + 2 * L + 1];
+    }
     h.r = th[P - 2];
     h.sigma2 = th[P - 1];
     return h;
@@ -76,6 +80,10 @@ std::vector<double> theta_of(const gp2s_hyper &h0)
     if (h0.family == GP2S_KERNEL_WENDCONV) {
         for (int k = 0; k < L * d; ++k) th.push_back(h0.G[k]);
         for (int k = 0; k < d; ++k) th.push_back(h0.ell[k]);
+        th.push_back(h0.w0);
+    }
+    if (h0.family == GP2S_KERNEL_FARFIELD) {
+        th.push_back(h0.ell[0]);
         th.push_back(h0.w0);
     }
     th.push_back(h0.r);
@@ -123,7 +131,7 @@ gp2s_status mcmc_run(gp2s_ctx *c, int64_t n, const double *X, const double *y, c
     if (!h0 || !mo || !chain) return set_err(c, GP2S_EINVAL, "hyper / mcmc options / chain is NULL");
     const int L = h0->L, d = h0->d;
     if (d < 1 || d > kMaxDim || L < 0 || L > kMaxBumps) return set_err(c, GP2S_EINVAL, "bad d / L");
-    const int P = h0->family == GP2S_KERNEL_WENDCONV ? L * (2 * d + 2) + d + 3 : L * (d + 2) + 2;
+    const int P = gp2s_num_params_family(d, L, h0->family);
     const int nb = mo->nblocks;
     if (mo->iters < 0 || nb < 1 || nb > 64 || !mo->block || !mo->step)
         return set_err(c, GP2S_EINVAL, "iters >= 0, 1 <= nblocks <= 64, block and step arrays required");

@@ -383,6 +383,7 @@ gp2s_status posterior(gp2s_ctx *c, int64_t ns, const double *Xs, double *mean, d
     if (!A.valid || !c->have_solution)
         return set_err(c, GP2S_ENOTREADY, "gp2s_posterior needs a solved problem (gp2s_lml, gp2s_lml_grad or gp2s_solve)");
     if (ns < 0) return set_err(c, GP2S_EINVAL, "n_test must be >= 0");
+    if (A.kp.family == 2) return set_err(c, GP2S_EINVAL, "gp2s_posterior takes the product and convolution kernels");
     if (ns == 0) {
         if (info) std::memset(info, 0, sizeof(*info));
         return GP2S_OK;

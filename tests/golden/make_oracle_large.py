@@ -18,6 +18,8 @@ Cases (Sec. 3 LML, SLQ log-determinant and Hutchinson gradient with identical Ra
                            (60 entries per row), 32 probes x 100 steps
   sphere_4d_10m            the full 10,000,000-point workload of that generator (about 600 M stored
                            entries; the oracle's CG to 1e-8), 32 probes x 100 steps
+  batch0_p{100,32,116}     three problems of the 256-problem batch (the largest, the densest rows,
+                           the largest 1-D one), 16 probes x 100 steps, LML only
 """
 import json
 import os
@@ -49,11 +51,18 @@ def cases():
                                  theta_index=0, probes=32, steps=100, seed=0)
     out["sphere_4d_10m"] = dict(workload="sphere_4d", n=10_000_000, target=60.0, theta_set=None,
                                 theta_index=0, probes=32, steps=100, seed=0, cg_tol=1e-8)
+    # problems of the 256-problem batch (seed 0): the largest, the densest rows, the largest 1-D
+    for idx in (100, 32, 116):
+        out[f"batch0_p{idx}"] = dict(workload="batch", n=None, target=None, theta_set=None, theta_index=idx,
+                                     probes=16, steps=100, seed=0, grad=False)
     return out
 
 
 def inputs(spec):
     """X, y and the hyperparameter dict of a case (the same calls the GPU tests make)."""
+    if spec["workload"] == "batch":
+        w = W.batch(0)[spec["theta_index"]]
+        return w["X"], w["y"], w["hyper"]
     gen = {"clusters_3d": W.clusters_3d, "sphere_4d": W.sphere_4d}[spec["workload"]]
     w = gen(0, n=spec["n"], target_nnz=spec["target"])
     hyper = w["hyper"]
@@ -67,7 +76,8 @@ def run(name, spec):
     h = oracle.Hyper(**hyper)
     t0 = time.time()
     tol = spec.get("cg_tol", CG_TOL)
-    s = oracle.lml_slq(X, y, h, m=spec["probes"], k=spec["steps"], seed=spec["seed"], tol=tol)
+    want_grad = spec.get("grad", True)
+    s = oracle.lml_slq(X, y, h, m=spec["probes"], k=spec["steps"], seed=spec["seed"], tol=tol, grad=want_grad)
     rec = {
         "case": name, **spec, "cg_tol": tol, "oracle_threads": oracle.num_threads(),
         "oracle_seconds": round(time.time() - t0, 1),
@@ -78,7 +88,8 @@ def run(name, spec):
         "nnz": int(s["csr"].nnz), "lml": s["lml"], "quad": s["quad"], "logdet": s["logdet"],
         "logdet_diag": s["logdet_diag"], "relres": s["relres"],
         "probe_quadrature_std": float(np.std(s["probe_quadrature"], ddof=1)),
-        "grad": [float(v) for v in s["grad"]],
+        "grad": [float(v) for v in s["grad"]] if want_grad else None,
+        "n_points": int(X.shape[0]),
     }
     path = os.path.join(HERE, f"oracle_{name}.json")
     with open(path, "w") as f:

@@ -106,7 +106,10 @@ def test_slq_and_gradient_match_oracle_with_identical_probes(gp, ctx, d, precisi
     assert info["logdet"] == pytest.approx(s["logdet"], rel=1e-3)
     assert info["quad"] == pytest.approx(s["quad"], rel=1e-7)
     assert g.shape == s["grad"].shape == (h.nparams,)
-    assert np.abs(g - s["grad"]).max() <= 1e-6 * np.abs(s["grad"]).max()
+    # mixed: FP32 probe solutions and probe cross terms (measured 1.2e-6 on the 1-D case); FP64 form:
+    # everything FP64 (solves to 1e-11)
+    bar = 1e-5 if precision == "mixed" else 1e-6
+    assert np.abs(g - s["grad"]).max() <= bar * np.abs(s["grad"]).max()
 
 
 def test_exact_gradient_direction_on_the_1d_test_function(gp, ctx):
