@@ -278,8 +278,6 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (lim) c->mem_limit = (size_t)std::strtoull(lim, nullptr, 10);
     const char *gr = std::getenv("GP2S_GRAPHS");
     if (gr && std::strcmp(gr, "0") == 0) c->use_graphs = false;
-    const char *sp = std::getenv("GP2S_SPMM_PIPE");
-    if (sp) c->spmm_pipe = std::strcmp(sp, "0") != 0;
     const char *pa = std::getenv("GP2S_PC_ASYNC");
     if (pa && std::strcmp(pa, "0") == 0) c->pc_async = false;
     *ctx = c;

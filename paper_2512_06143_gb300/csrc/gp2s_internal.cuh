@@ -117,7 +117,6 @@ struct gp2s_ctx {
     double bj_logdet = 0.0;
     bool probes_for_grad = false;   // the probe solves feed the Hutchinson gradient
     bool use_graphs = true;         // replay runs of CG iterations as CUDA graphs (GP2S_GRAPHS=0: off)
-    bool spmm_pipe = false;         // RB8 SpMM with double-buffered gathers (GP2S_SPMM_PIPE=1)
     bool pc_async = true;           // probe-group PCG step on the bulk-copy pipelined kernel
                                     // (GP2S_PC_ASYNC=0: the staged kernel)
     cudaStream_t capture_stream = nullptr;   // private stream the graphs are captured on

@@ -873,7 +873,7 @@ struct RBWork {
     unsigned int pad;
 };
 
-template <int KH, bool HAS_Y, bool PIPE>
+template <int KH, bool HAS_Y>
 __global__ void __launch_bounds__(RBCfg<KH>::threads, 1)
 k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, const float *__restrict__ uval,
           int64_t n, const float *__restrict__ py, const float *__restrict__ pz, float *__restrict__ qy,
@@ -885,8 +885,9 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
     // alternate union entries of the same row block: one shared-memory broadcast of an entry's
     // column and 8 values then feeds 8 x KH products per lane (twice the products per staged entry
     // of a lane-per-column layout), and every lane keeps D independent 4 KH-byte gathers in flight.
-    // PD gathers per group: 8 in one batch, or 4 with the next group's 4 in flight (PIPE)
-    constexpr int PD = PIPE ? 4 : (KH >= 6 ? 4 : 8);
+    // PD gathers in flight per lane (a double-buffered form with 4 + 4 spilled registers at
+    // KH = 4 and measured slower: 1.03 against 0.90 ms per launch at N = 1M)
+    constexpr int PD = KH >= 6 ? 4 : 8;
     constexpr int W = RBCfg<KH>::warps;
     extern __shared__ __align__(16) unsigned char rb_sh[];
     int *s_col = reinterpret_cast<int *>(rb_sh);                                    // W x 32
@@ -966,7 +967,14 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             const int npair = (cnt + 1) >> 1;
             const int *scol = s_col + wid * kWarp + half;
             const float4 *sval = s_val + (wid * kWarp + half) * 2;
-            auto fma_group = [&](int u0, const float (&pv)[PD][KH]) {
+#pragma unroll 1
+            for (int u0 = 0; u0 < npair; u0 += PD) {
+                int jj[PD];
+#pragma unroll
+                for (int d = 0; d < PD; ++d) jj[d] = scol[2 * (u0 + d)];
+                float pv[PD][KH];
+#pragma unroll
+                for (int d = 0; d < PD; ++d) load_k<float, KH>(pz + (int64_t)jj[d] * M + hl * KH, pv[d]);
 #pragma unroll
                 for (int d = 0; d < PD; ++d) {
                     const float4 a0 = sval[4 * (u0 + d)], a1 = sval[4 * (u0 + d) + 1];
@@ -978,35 +986,6 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
 #pragma unroll
                         for (int rp = 0; rp < kRB / 2; ++rp) acc[rp][k] = __ffma2_rn(vp[rp], pk, acc[rp][k]);
                     }
-                }
-            };
-            auto load_group = [&](int u0, float (&pv)[PD][KH]) {
-                int jj[PD];
-#pragma unroll
-                for (int d = 0; d < PD; ++d) jj[d] = scol[2 * (u0 + d)];
-#pragma unroll
-                for (int d = 0; d < PD; ++d) load_k<float, KH>(pz + (int64_t)jj[d] * M + hl * KH, pv[d]);
-            };
-            if (PIPE) {
-                // two register buffers: the gathers of group g + 1 are in flight while group g's
-                // products run (a batch holds at most 16 / PD groups)
-                float pa[PD][KH], pb[PD][KH];
-                load_group(0, pa);
-#pragma unroll
-                for (int g = 0; g < 16 / PD; g += 2) {
-                    if (g * PD >= npair) break;
-                    if ((g + 1) * PD < npair) load_group((g + 1) * PD, pb);
-                    fma_group(g * PD, pa);
-                    if ((g + 1) * PD >= npair) break;
-                    if ((g + 2) * PD < npair) load_group((g + 2) * PD, pa);
-                    fma_group((g + 1) * PD, pb);
-                }
-            } else {
-#pragma unroll 1
-                for (int u0 = 0; u0 < npair; u0 += PD) {
-                    float pv[PD][KH];
-                    load_group(u0, pv);
-                    fma_group(u0, pv);
                 }
             }
             __syncwarp();
@@ -1163,8 +1142,7 @@ template <int KH>
 gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts)
 {
     const size_t smem = rb_smem<KH>();
-    // the double-buffered form needs registers the wide column counts (KH >= 6) do not have
-    auto kern = (c->spmm_pipe && KH <= 4) ? k_spmm_rb<KH, true, (KH <= 4)> : k_spmm_rb<KH, true, false>;
+    auto kern = k_spmm_rb<KH, true>;
     GP2S_TRY(smem_attr(c, (const void *)kern, smem));
     const RBTiles tl = rb_tiles(ceil_div(c->A.n, kRB), nb);
     GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (16 * KH + 1)));
@@ -1551,20 +1529,27 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
            const float *__restrict__ qz, float *__restrict__ zz, const double *__restrict__ sc,
            double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride, int *__restrict__ err)
 {
+    // Warp-specialised: warps 8..15 (producers) turn the staged r of block k into r - alpha q and
+    // hand the stage over through named barrier 1 + (k & 1); warps 0..7 (consumers) take it, form
+    // z = M^{-1} r with 8 x 4 register tiles (one tile per thread), then release the stage, and
+    // thread 0 refills it with block k + 2.  The producers' elementwise work of block k + 1
+    // overlaps the consumers' product of block k.
+    constexpr int NT = kPPThreads / 2;         // threads per role
     constexpr int CG = M / 4;                  // column groups of four
     constexpr int NF4 = BJ * M / 4;            // float4 per residual block
-    constexpr int PER = NF4 / kPPThreads;      // float4 per thread
-    static_assert(NF4 % kPPThreads == 0 && kPPThreads % CG == 0, "block shape");
+    constexpr int PER = NF4 / NT;              // float4 per producer thread
+    constexpr int TR = 8;                      // tile rows per consumer thread
+    constexpr int NTILE = (BJ / TR) * CG;      // consumer tiles (<= NT; the rest of the consumers idle)
+    static_assert(NF4 % NT == 0 && NT % CG == 0 && NTILE <= NT, "block shape");
     extern __shared__ __align__(128) unsigned char pp_sh[];
     float *stage0 = reinterpret_cast<float *>(pp_sh);
     float *stage1 = stage0 + BJ * BJ + BJ * M;
     uint64_t *bar = reinterpret_cast<uint64_t *>(stage1 + BJ * BJ + BJ * M);
     const int tid = threadIdx.x;
-    const int cg = tid % CG;                   // this thread's four columns, in every phase
-    float a4[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) a4[q] = (float)sc[(cg * 4 + q + 1) * kScal + S_ALPHA];
-    double drz[4] = {0.0, 0.0, 0.0, 0.0}, drr[4] = {0.0, 0.0, 0.0, 0.0};
+    const bool producer = tid >= NT;
+    const int t = producer ? tid - NT : tid;
+    const int cg = t % CG;                     // this thread's four columns, in either role
+    double dacc[4] = {0.0, 0.0, 0.0, 0.0};     // r^T r (producers) or r^T z (consumers)
     const int64_t nmine = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     auto issue = [&](int64_t k) {
@@ -1577,14 +1562,6 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
         bulk_copy_g2s(st, Minv32 + b * BJ * BJ, mb, &bar[k & 1]);
         bulk_copy_g2s(st + BJ * BJ, rz + i0 * M, rb, &bar[k & 1]);
     };
-    auto load_q = [&](int64_t k, float4 (&q4)[PER]) {
-        const int64_t i0 = (blockIdx.x + k * gridDim.x) * BJ;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int e = tid + j * kPPThreads;
-            q4[j] = i0 + e / CG < n ? reinterpret_cast<const float4 *>(qz + i0 * M)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -1596,90 +1573,125 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
         if (nmine > 0) issue(0);
         if (nmine > 1) issue(1);
     }
-    float4 qn[PER];
-    if (nmine > 0) load_q(0, qn);
-    bool ok = true;
-    for (int64_t k = 0; k < nmine; ++k) {
-        float *MT = (k & 1) ? stage1 : stage0;
-        float *R = MT + BJ * BJ;
-        const int64_t i0 = (blockIdx.x + k * gridDim.x) * BJ;
-        const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
-        float4 qc[PER];
+    if (producer) {
+        float a4[4];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) qc[j] = qn[j];
-        if (k + 1 < nmine) load_q(k + 1, qn);
-        if (!mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1))) {
-            ok = false;
-            break;
-        }
-        // r -= alpha q: in the stage, and back to the probe block; rows past the matrix are zero
-        float srr[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < 4; ++q) a4[q] = (float)sc[(cg * 4 + q + 1) * kScal + S_ALPHA];
+        bool ok = true;
+        for (int64_t k = 0; k < nmine; ++k) {
+            float *R = ((k & 1) ? stage1 : stage0) + BJ * BJ;
+            const int64_t i0 = (blockIdx.x + k * gridDim.x) * BJ;
+            const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
+            float4 q4[PER];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int e = tid + j * kPPThreads;
-            float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (e / CG < nb) {
-                r4 = reinterpret_cast<const float4 *>(R)[e];
-                r4.x = r4.x - a4[0] * qc[j].x;
-                r4.y = r4.y - a4[1] * qc[j].y;
-                r4.z = r4.z - a4[2] * qc[j].z;
-                r4.w = r4.w - a4[3] * qc[j].w;
-                reinterpret_cast<float4 *>(rz + i0 * M)[e] = r4;
-                srr[0] = fmaf(r4.x, r4.x, srr[0]);
-                srr[1] = fmaf(r4.y, r4.y, srr[1]);
-                srr[2] = fmaf(r4.z, r4.z, srr[2]);
-                srr[3] = fmaf(r4.w, r4.w, srr[3]);
+            for (int j = 0; j < PER; ++j) {
+                const int e = t + j * NT;
+                q4[j] = e / CG < nb ? reinterpret_cast<const float4 *>(qz + i0 * M)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            reinterpret_cast<float4 *>(R)[e] = r4;
-        }
-        __syncthreads();
-        // z = M^{-1} r (symmetric M^{-1}: its rows are its columns), written with r^T z
-        float srz[4] = {0.f, 0.f, 0.f, 0.f};
-        bj_tile_mm<BJ>(MT, R, M, [&](int it, int c0, float (&acc)[4][4]) {
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                if (it + a >= nb) continue;
-                *reinterpret_cast<float4 *>(zz + (i0 + it + a) * M + c0) =
-                    make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) srz[q] = fmaf(R[(it + a) * M + c0 + q], acc[a][q], srz[q]);
+            // a copy that never lands is reported; the stage is handed over all the same so that
+            // the consumers never wait on a barrier nobody arrives at
+            if (ok && !mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1))) {
+                ok = false;
+                atomicExch(err, 1);
             }
-        });
+            float srr[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            drz[q] += (double)srz[q];
-            drr[q] += (double)srr[q];
+            for (int j = 0; j < PER; ++j) {
+                const int e = t + j * NT;
+                float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e / CG < nb) {
+                    r4 = reinterpret_cast<const float4 *>(R)[e];
+                    r4.x = r4.x - a4[0] * q4[j].x;
+                    r4.y = r4.y - a4[1] * q4[j].y;
+                    r4.z = r4.z - a4[2] * q4[j].z;
+                    r4.w = r4.w - a4[3] * q4[j].w;
+                    reinterpret_cast<float4 *>(rz + i0 * M)[e] = r4;
+                    srr[0] = fmaf(r4.x, r4.x, srr[0]);
+                    srr[1] = fmaf(r4.y, r4.y, srr[1]);
+                    srr[2] = fmaf(r4.z, r4.z, srr[2]);
+                    srr[3] = fmaf(r4.w, r4.w, srr[3]);
+                }
+                reinterpret_cast<float4 *>(R)[e] = r4;   // rows past the matrix are zero
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dacc[q] += (double)srr[q];
+            asm volatile("bar.arrive %0, %1;" ::"r"(1 + (int)(k & 1)), "r"(kPPThreads) : "memory");
         }
-        __syncthreads();   // the stage is free: refill it with block k + 2
-        if (tid == 0 && k + 2 < nmine) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(k + 2);
+        if (!ok && t == 0) {
+            // give copies still in flight a bounded chance to land before the CTA leaves
+            for (int b = 0; b < 2; ++b)
+                for (uint32_t par = 0; par < 2; ++par) mbar_wait_bounded(&bar[b], par);
+        }
+    } else {
+        const int rg = t / CG;                 // rows TR rg .. TR rg + TR - 1, columns 4 cg .. 4 cg + 3
+        const int i0t = rg * TR, c0 = cg * 4;
+        const bool has_tile = t < NTILE;
+        for (int64_t k = 0; k < nmine; ++k) {
+            const float *MT = (k & 1) ? stage1 : stage0;
+            const float *R = MT + BJ * BJ;
+            const int64_t i0 = (blockIdx.x + k * gridDim.x) * BJ;
+            const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(k & 1)), "r"(kPPThreads) : "memory");
+            if (has_tile) {
+            // z = M^{-1} r (symmetric M^{-1}: row kk of the stage is column kk), rows in pairs with
+            // packed FP32x2 FMAs (each half rounds like fmaf)
+            float2 acc[TR / 2][4];
+#pragma unroll
+            for (int a = 0; a < TR / 2; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int kk = 0; kk < BJ; ++kk) {
+                const float4 m0 = *reinterpret_cast<const float4 *>(MT + kk * BJ + i0t);
+                const float4 m1 = *reinterpret_cast<const float4 *>(MT + kk * BJ + i0t + 4);
+                const float4 rv = *reinterpret_cast<const float4 *>(R + kk * M + c0);
+                const float2 mp[4] = {make_float2(m0.x, m0.y), make_float2(m0.z, m0.w), make_float2(m1.x, m1.y),
+                                      make_float2(m1.z, m1.w)};
+                const float ra[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 rq = make_float2(ra[q], ra[q]);
+#pragma unroll
+                    for (int a = 0; a < TR / 2; ++a) acc[a][q] = __ffma2_rn(mp[a], rq, acc[a][q]);
+                }
+            }
+            float srz[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < TR; ++a) {
+                const int i = i0t + a;
+                if (i >= nb) continue;
+                const float z[4] = {(a & 1) ? acc[a / 2][0].y : acc[a / 2][0].x, (a & 1) ? acc[a / 2][1].y : acc[a / 2][1].x,
+                                    (a & 1) ? acc[a / 2][2].y : acc[a / 2][2].x, (a & 1) ? acc[a / 2][3].y : acc[a / 2][3].x};
+                *reinterpret_cast<float4 *>(zz + (i0 + i) * M + c0) = make_float4(z[0], z[1], z[2], z[3]);
+                const float4 rv = *reinterpret_cast<const float4 *>(R + i * M + c0);
+                srz[0] = fmaf(rv.x, z[0], srz[0]);
+                srz[1] = fmaf(rv.y, z[1], srz[1]);
+                srz[2] = fmaf(rv.z, z[2], srz[2]);
+                srz[3] = fmaf(rv.w, z[3], srz[3]);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dacc[q] += (double)srz[q];
+            }
+            // every consumer is done with the stage: refill it with block k + 2
+            asm volatile("bar.sync 3, %0;" ::"r"(NT) : "memory");
+            if (t == 0 && k + 2 < nmine) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(k + 2);
+            }
         }
     }
-    if (!ok) {
-        // a copy never completed: report, give the other stage's copy a bounded chance to land
-        // so that no copy still targets this CTA's shared memory, and leave
-        if (tid == 0) {
-            atomicExch(err, 1);
-            mbar_wait_bounded(&bar[0], 0);
-            mbar_wait_bounded(&bar[1], 0);
-        }
-        return;
-    }
-    // per-column partials of this CTA, summed in thread order
+    __syncthreads();
+    // per-column partials of this CTA in thread order: r^T z from the consumers, r^T r from the producers
     double *red = reinterpret_cast<double *>(stage0);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        red[(size_t)tid * 8 + q] = drz[q];
-        red[(size_t)tid * 8 + 4 + q] = drr[q];
-    }
+    for (int q = 0; q < 4; ++q) red[(size_t)tid * 4 + q] = dacc[q];
     __syncthreads();
     if (tid < M) {
         const int g = tid / 4, q = tid % 4;
         double s1 = 0.0, s2 = 0.0;
-        for (int t = g; t < kPPThreads; t += CG) {
-            s1 += red[(size_t)t * 8 + q];
-            s2 += red[(size_t)t * 8 + 4 + q];
+        for (int u = g; u < NT; u += CG) {
+            s1 += red[(size_t)u * 4 + q];
+            s2 += red[(size_t)(NT + u) * 4 + q];
         }
         part_rz[(int64_t)(tid + 1) * pstride + blockIdx.x] = s1;
         part_rr[(int64_t)(tid + 1) * pstride + blockIdx.x] = s2;
@@ -1955,13 +1967,8 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     const int pga = (int)std::min<int64_t>(c->num_sms, nblkz);
     int *dev_err = flags + 3;
     if (pc_async) {
-        if (bjz == 128) {
-            GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64>, pp_smem<128, 64>()));
-            GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32>, pp_smem<128, 32>()));
-        } else {
-            GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<64, 64>, pp_smem<64, 64>()));
-            GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<64, 32>, pp_smem<64, 32>()));
-        }
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64>, pp_smem<128, 64>()));
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32>, pp_smem<128, 32>()));
     }
     auto launch_pc_probe = [&](int mm) -> gp2s_status {
         float *rzp = (float *)B.rz, *zzp = (float *)B.zz;
@@ -1969,10 +1976,8 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
 #define GP2S_PP(BJ_, M_)                                                                                     \
     k_pc_probe<BJ_, M_><<<pga, kPPThreads, pp_smem<BJ_, M_>(), c->stream>>>(n, nblkz, Minvz, rzp, qzp, zzp, sc, \
                                                                            part, part_rr, pstride, dev_err)
-        if (bjz == 128 && mm == 64) GP2S_PP(128, 64);
-        else if (bjz == 128) GP2S_PP(128, 32);
-        else if (mm == 64) GP2S_PP(64, 64);
-        else GP2S_PP(64, 32);
+        if (mm == 64) GP2S_PP(128, 64);
+        else GP2S_PP(128, 32);
 #undef GP2S_PP
         return GP2S_OK;
     };
