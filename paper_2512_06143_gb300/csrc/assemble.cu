@@ -381,12 +381,17 @@ __global__ void k_bumps(const double4_16a *__restrict__ X64, int64_t n, KernelPa
 }
 
 // FP64 values of Ah on the assembled pattern: one warp per row, lanes over the row's entries.
+// Every kernel here is symmetric bit for bit in its FP64 evaluation (squared differences, products
+// of the two points' factors, the product s_i s_j of the Jacobi scales), and so is the pattern: row
+// i evaluates only its pairs j >= i and writes each value also into row j, at the position of
+// column i that a binary search of row j's ascending columns finds.  Half the FP64 evaluations,
+// the same matrix.  A row j without column i (never, for a symmetric pattern) sets bit 0 of *bad.
 template <int D>
 __global__ void __launch_bounds__(256)
 k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowptr,
            const int32_t *__restrict__ col, int64_t n, KernelParams kp, const double *__restrict__ B64,
            const double *__restrict__ s64, double *__restrict__ val64, float *__restrict__ val32,
-           const double4_16a *__restrict__ Lam, const double *__restrict__ Sig)
+           const double4_16a *__restrict__ Lam, const double *__restrict__ Sig, int *__restrict__ bad)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -396,7 +401,13 @@ k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowp
         const double4_16a xi = X64[i];
         const double si = s64[i];
         const int p0 = rowptr[i], p1 = rowptr[i + 1];
-        for (int p = p0 + lane; p < p1; p += kWarp) {
+        // first entry with column >= i (the diagonal is stored): a search over the row's columns
+        int lo = p0, hi = p1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (col[mid] < (int32_t)i) lo = mid + 1; else hi = mid;
+        }
+        for (int p = lo + lane; p < p1; p += kWarp) {
             const int j = col[p];
             double v;
             if (j == i) {
@@ -443,6 +454,19 @@ k_values64(const double4_16a *__restrict__ X64, const int32_t *__restrict__ rowp
             }
             val64[p] = v;
             if (val32) val32[p] = (float)v;   // the FP32 copy is the FP64 value rounded once
+            if (j != i) {
+                int a = rowptr[j], e = rowptr[j + 1];
+                while (a < e) {
+                    const int mid = (a + e) >> 1;
+                    if (col[mid] < (int32_t)i) a = mid + 1; else e = mid;
+                }
+                if (a < rowptr[j + 1] && col[a] == (int32_t)i) {
+                    val64[a] = v;
+                    if (val32) val32[a] = (float)v;
+                } else {
+                    atomicOr(bad, 1);
+                }
+            }
         }
     }
 }
@@ -756,13 +780,13 @@ static void launch_bumps(gp2s_ctx *c, int64_t n, const KernelParams &kp, int *db
 }
 
 template <int D>
-static void launch_values(gp2s_ctx *c, int64_t n, const KernelParams &kp, bool mixed)
+static void launch_values(gp2s_ctx *c, int64_t n, const KernelParams &kp, bool mixed, int *vbad)
 {
     const unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * 32, 256), 152 * 32);
     k_values64<D><<<gb, 256, 0, c->stream>>>(c->Xs64.as<double4_16a>(), c->rowptr.as<int32_t>(), c->col.as<int32_t>(), n,
                                              kp, c->B64.as<double>(), c->s64.as<double>(), c->val64.as<double>(),
                                              mixed ? c->val32.as<float>() : nullptr, c->wc_lam.as<double4_16a>(),
-                                             c->wc_sig.as<double>());
+                                             c->wc_sig.as<double>(), vbad);
 }
 
 // Bump tables (FP64 and FP32), the diagonal and the Jacobi scales of the current points.
@@ -778,16 +802,24 @@ static gp2s_status bumps_and_checks(gp2s_ctx *c, int64_t n, int d, const KernelP
     return GP2S_OK;
 }
 
-// The values of every stored pair of the current pattern.
+// The values of every stored pair of the current pattern (synchronises the stream: the mirror
+// check is read back).
 static gp2s_status values_pass(gp2s_ctx *c, int64_t n, int d, const KernelParams &kp, bool mixed)
 {
+    GP2S_TRY(ensure(c, c->counters, 256));
+    int *vbad = reinterpret_cast<int *>(c->counters.as<char>() + 32);
+    GP2S_CUDA(c, cudaMemsetAsync(vbad, 0, sizeof(int), c->stream));
     switch (d) {
-    case 1: launch_values<1>(c, n, kp, mixed); break;
-    case 2: launch_values<2>(c, n, kp, mixed); break;
-    case 3: launch_values<3>(c, n, kp, mixed); break;
-    default: launch_values<4>(c, n, kp, mixed); break;
+    case 1: launch_values<1>(c, n, kp, mixed, vbad); break;
+    case 2: launch_values<2>(c, n, kp, mixed, vbad); break;
+    case 3: launch_values<3>(c, n, kp, mixed, vbad); break;
+    default: launch_values<4>(c, n, kp, mixed, vbad); break;
     }
     GP2S_LAUNCH(c);
+    int hv = 0;
+    GP2S_CUDA(c, cudaMemcpyAsync(&hv, vbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (hv) return set_err(c, GP2S_EINVAL, "internal: the assembled pattern is not symmetric");
     return GP2S_OK;
 }
 

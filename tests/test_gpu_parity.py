@@ -88,6 +88,14 @@ def _check_assembly(gp, ctx, w, exact_support=0, precision=None, method="auto"):
     v64 = c["val64"].cpu().numpy()
     rows = np.repeat(np.arange(n), np.diff(rp))
     assert np.all(v64[rows == col] == 1.0)
+    # Ah is symmetric bit for bit, in FP64 and in its FP32 copy (each pair is evaluated once and
+    # mirrored; the kernels are symmetric in their arithmetic anyway)
+    import scipy.sparse as sp
+    for v in (v64, None if c.get("val32") is None else c["val32"].cpu().numpy()):
+        if v is None:
+            continue
+        S = sp.csr_matrix((v, col, rp), shape=(n, n))
+        assert (S != S.T).nnz == 0
     return info
 
 
