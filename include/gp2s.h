@@ -298,8 +298,10 @@ gp2s_status gp2s_lml_grad(gp2s_ctx *ctx, int64_t n, const double *X, const doubl
  * or GP2S_BATCH_WORKERS), largest problems first; the call first synchronises ctx's stream so
  * that device inputs produced there are complete.  In MIXED precision with precond = 2 and
  * bj_block = 0 an autotuner picks, per shape class (family, d, floor(log2 n)), the block-Jacobi
- * block size and CUDA-graph replay from timings of the class's first problems (kept in ctx for
- * later calls; GP2S_BATCH_TUNE=0 turns it off).  Each problem's result equals that of a single
+ * block size and CUDA-graph replay from timings of the class's first problems: each of the four
+ * configurations runs one problem, and once all four have been timed the fastest (mean time per
+ * point) is fixed for the class, in this call and later ones on ctx (GP2S_BATCH_TUNE=0 turns the
+ * autotuner off).  Each problem's result equals that of a single
  * gp2s_lml call with the same options and opts.bj_block = info.bj_block, bit for bit.
  * lml_host: B doubles (NaN for a failed problem).
  * info_host: optional, B entries.  On failure the status and message are those of the first

@@ -107,18 +107,24 @@ gp2s_status batched_lml(gp2s_ctx *c, int32_t B, const int64_t *n, const double *
             t.score.assign(kNumBatchConfigs, 0.0);
             t.issued.assign(kNumBatchConfigs, 0);
         }
+        if (t.chosen >= 0) return t.chosen;
         for (int k = 0; k < kNumBatchConfigs; ++k)
             if (t.issued[k] == 0) {       // every configuration gets one problem first
                 t.issued[k] = 1;
                 return k;
             }
-        int best = 0;
+        // the best mean time per point so far; final once every configuration has been measured
+        int best = 0, measured = 0;
         double bs = 1e300;
         for (int k = 0; k < kNumBatchConfigs; ++k)
-            if (t.count[k] > 0 && t.score[k] / t.count[k] < bs) {
-                bs = t.score[k] / t.count[k];
-                best = k;
+            if (t.count[k] > 0) {
+                ++measured;
+                if (t.score[k] / t.count[k] < bs) {
+                    bs = t.score[k] / t.count[k];
+                    best = k;
+                }
             }
+        if (measured == kNumBatchConfigs) t.chosen = best;
         return best;
     };
     auto record = [&](int cls, int k, double sec_per_point) {

@@ -280,6 +280,10 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (gr && std::strcmp(gr, "0") == 0) c->use_graphs = false;
     const char *pa = std::getenv("GP2S_PC_ASYNC");
     if (pa && std::strcmp(pa, "0") == 0) c->pc_async = false;
+    const char *fy = std::getenv("GP2S_PC_FUSE_Y");
+    if (fy && std::strcmp(fy, "0") == 0) c->pc_fuse_y = false;
+    const char *sh = std::getenv("GP2S_SPMM_HALF");
+    if (sh && std::strcmp(sh, "1") == 0) c->spmm_half = true;
     *ctx = c;
     return GP2S_OK;
 }

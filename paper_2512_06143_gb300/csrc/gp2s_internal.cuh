@@ -118,6 +118,8 @@ struct gp2s_ctx {
     bool probes_for_grad = false;   // the probe solves feed the Hutchinson gradient
     bool use_graphs = true;         // replay runs of CG iterations as CUDA graphs (GP2S_GRAPHS=0: off)
     bool pc_async = true;           // probe-group PCG step on the bulk-copy pipelined kernel
+    bool spmm_half = false;         // 16 and 32 columns on half-warp entry groups (KH = 1, 2)
+    bool pc_fuse_y = true;          // the y column's PCG update inside the probe kernel
                                     // (GP2S_PC_ASYNC=0: the staged kernel)
     cudaStream_t capture_stream = nullptr;   // private stream the graphs are captured on
     // batched form: worker contexts (own stream and workspace each), created on first use
@@ -129,6 +131,7 @@ struct gp2s_ctx {
     struct TuneState {
         std::vector<double> score;
         std::vector<int> count, issued;
+        int chosen = -1;   // fixed once every configuration has a measurement
     };
     std::map<int, TuneState> tune;
     std::mutex tune_mu;

@@ -624,7 +624,7 @@ struct CGBuffers {
     void *zz, *zy;   // preconditioned residuals (block-Jacobi PCG)
 };
 
-template <int KH>
+template <int KH, int NG>
 gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts);
 
 // y-only SpMV (the y column after every probe column has stopped, and the refinement solves):
@@ -739,12 +739,20 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
     }
     if (rb_launch<T>(c, m, has_y)) {
         switch (m) {
-        case 16: GP2S_TRY(launch_rb<1>(c, B, part, pstride, nb, nparts)); break;
-        case 32: GP2S_TRY(launch_rb<2>(c, B, part, pstride, nb, nparts)); break;
-        case 48: GP2S_TRY(launch_rb<3>(c, B, part, pstride, nb, nparts)); break;
-        case 64: GP2S_TRY(launch_rb<4>(c, B, part, pstride, nb, nparts)); break;
-        case 96: GP2S_TRY(launch_rb<6>(c, B, part, pstride, nb, nparts)); break;
-        default: GP2S_TRY(launch_rb<8>(c, B, part, pstride, nb, nparts)); break;
+        // every lane covers KH = 4 columns where the column count allows (groups of 4, 8 or 16
+        // lanes per entry); 48 and 96 columns take half-warps with KH = 3 and 6
+        case 16:
+            GP2S_TRY((c->spmm_half ? launch_rb<1, 2>(c, B, part, pstride, nb, nparts)
+                                   : launch_rb<4, 8>(c, B, part, pstride, nb, nparts)));
+            break;
+        case 32:
+            GP2S_TRY((c->spmm_half ? launch_rb<2, 2>(c, B, part, pstride, nb, nparts)
+                                   : launch_rb<4, 4>(c, B, part, pstride, nb, nparts)));
+            break;
+        case 48: GP2S_TRY((launch_rb<3, 2>(c, B, part, pstride, nb, nparts))); break;
+        case 64: GP2S_TRY((launch_rb<4, 2>(c, B, part, pstride, nb, nparts))); break;
+        case 96: GP2S_TRY((launch_rb<6, 2>(c, B, part, pstride, nb, nparts))); break;
+        default: GP2S_TRY((launch_rb<8, 2>(c, B, part, pstride, nb, nparts))); break;
         }
         if (ev_b) GP2S_CUDA(c, cudaEventRecord(ev_b, c->stream));
         return GP2S_OK;
@@ -873,27 +881,33 @@ struct RBWork {
     unsigned int pad;
 };
 
-template <int KH, bool HAS_Y>
+template <int KH, int NG, bool HAS_Y>
 __global__ void __launch_bounds__(RBCfg<KH>::threads, 1)
 k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, const float *__restrict__ uval,
           int64_t n, const float *__restrict__ py, const float *__restrict__ pz, float *__restrict__ qy,
           float *__restrict__ qz, double *__restrict__ part, int pstride, RBWork *__restrict__ work,
           int tile_blocks, int ntiles, double *__restrict__ tpart, int *__restrict__ seg_cnt, int seg_tiles)
 {
-    constexpr int M = 16 * KH;
-    // Each half-warp covers all M probe columns (KH = M / 16 per lane) and the two halves take
-    // alternate union entries of the same row block: one shared-memory broadcast of an entry's
-    // column and 8 values then feeds 8 x KH products per lane (twice the products per staged entry
-    // of a lane-per-column layout), and every lane keeps D independent 4 KH-byte gathers in flight.
-    // PD gathers in flight per lane (a double-buffered form with 4 + 4 spilled registers at
-    // KH = 4 and measured slower: 1.03 against 0.90 ms per launch at N = 1M)
-    constexpr int PD = KH >= 6 ? 4 : 8;
+    // The warp splits into NG groups of LG = 32 / NG lanes.  Each group covers all M = LG KH probe
+    // columns (KH per lane) and the groups take interleaved union entries of the same row block:
+    // one shared-memory broadcast of an entry's column and 8 values feeds 8 x KH products per
+    // lane, and every lane keeps PD independent 4 KH-byte gathers in flight.  NG = 2 (half-warps)
+    // for M >= 48; M = 32 and M = 16 take NG = 4 and 8 with KH = 4, so that every lane does the
+    // same 16 packed FMAs per gathered entry whatever the column count.
+    // (A double-buffered form with 4 + 4 gathers spilled registers at KH = 4 and measured slower:
+    // 1.03 against 0.90 ms per launch at N = 1M.)
+    constexpr int LG = kWarp / NG;
+    constexpr int M = LG * KH;
+    // runs of PD entries per group, at most the 32 / NG entries of a staged batch
+    constexpr int PD = (KH >= 6 ? 4 : 8) < kWarp / NG ? (KH >= 6 ? 4 : 8) : kWarp / NG;
     constexpr int W = RBCfg<KH>::warps;
+    static_assert(NG == 2 || NG == 4 || NG == 8, "entry groups of 16, 8 or 4 lanes");
+    static_assert((kWarp / NG) % PD == 0, "runs tile the staged batch");
     extern __shared__ __align__(16) unsigned char rb_sh[];
     int *s_col = reinterpret_cast<int *>(rb_sh);                                    // W x 32
     float4 *s_val = reinterpret_cast<float4 *>(rb_sh + sizeof(int) * W * kWarp);  // W x 32 x 2
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int half = lane >> 4, hl = lane & 15;
+    const int grp = lane / LG, gl = lane % LG;
     const int64_t nblk = (n + kRB - 1) / kRB;
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(&work->next, 1ull);
@@ -962,22 +976,22 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             s_val[(wid * kWarp + lane) * 2] = v0;
             s_val[(wid * kWarp + lane) * 2 + 1] = v1;
             __syncwarp();
-            // half h takes entries 2u + h, u < ceil(cnt / 2), in groups of D (the staged entries
-            // past cnt are zeros, so a group may run past cnt)
-            const int npair = (cnt + 1) >> 1;
-            const int *scol = s_col + wid * kWarp + half;
-            const float4 *sval = s_val + (wid * kWarp + half) * 2;
+            // group g takes entries NG u + g, u < ceil(cnt / NG), in runs of PD (the staged entries
+            // past cnt are zeros, so a run may pass cnt)
+            const int nrun = (cnt + NG - 1) / NG;
+            const int *scol = s_col + wid * kWarp + grp;
+            const float4 *sval = s_val + (wid * kWarp + grp) * 2;
 #pragma unroll 1
-            for (int u0 = 0; u0 < npair; u0 += PD) {
+            for (int u0 = 0; u0 < nrun; u0 += PD) {
                 int jj[PD];
 #pragma unroll
-                for (int d = 0; d < PD; ++d) jj[d] = scol[2 * (u0 + d)];
+                for (int d = 0; d < PD; ++d) jj[d] = scol[NG * (u0 + d)];
                 float pv[PD][KH];
 #pragma unroll
-                for (int d = 0; d < PD; ++d) load_k<float, KH>(pz + (int64_t)jj[d] * M + hl * KH, pv[d]);
+                for (int d = 0; d < PD; ++d) load_k<float, KH>(pz + (int64_t)jj[d] * M + gl * KH, pv[d]);
 #pragma unroll
                 for (int d = 0; d < PD; ++d) {
-                    const float4 a0 = sval[4 * (u0 + d)], a1 = sval[4 * (u0 + d) + 1];
+                    const float4 a0 = sval[2 * NG * (u0 + d)], a1 = sval[2 * NG * (u0 + d) + 1];
                     const float2 vp[kRB / 2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w),
                                                 make_float2(a1.x, a1.y), make_float2(a1.z, a1.w)};
 #pragma unroll
@@ -990,35 +1004,84 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             }
             __syncwarp();
             if (block_end) {
-                // row block bcur is complete: half h adds its partner's sums of rows 4h .. 4h + 3
-                // to its own, stores those rows and folds them into the tile's dots
+                // row block bcur is complete: a butterfly over the groups (lane masks 16, 8, 4)
+                // leaves each group the full sums of 8 / NG rows, which it stores and folds into
+                // the tile's dots
                 const int64_t r0 = bcur * kRB;
                 const int nrows = (int)(n - r0 < kRB ? n - r0 : kRB);
-                float2 mine[2][KH];
+                const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1;
+                float2 h2[2][KH];   // rows 4 b16 + 2q, 4 b16 + 2q + 1
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
 #pragma unroll
                     for (int k = 0; k < KH; ++k) {
-                        const float2 keep = half ? acc[2 + q][k] : acc[q][k];
-                        const float2 send = half ? acc[q][k] : acc[2 + q][k];
+                        const float2 keep = b16 ? acc[2 + q][k] : acc[q][k];
+                        const float2 send = b16 ? acc[q][k] : acc[2 + q][k];
                         float2 got;
                         got.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
                         got.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
-                        mine[q][k] = make_float2(keep.x + got.x, keep.y + got.y);
+                        h2[q][k] = make_float2(keep.x + got.x, keep.y + got.y);
                     }
+                if constexpr (NG == 2) {
 #pragma unroll
-                for (int rr = 0; rr < kRB / 2; ++rr) {
-                    const int r = 4 * half + rr;
-                    if (r < nrows) {
-                        const int64_t i = r0 + r;
-                        float qr[KH];
+                    for (int rr = 0; rr < kRB / 2; ++rr) {
+                        const int r = 4 * b16 + rr;
+                        if (r < nrows) {
+                            const int64_t i = r0 + r;
+                            float qr[KH];
 #pragma unroll
-                        for (int k = 0; k < KH; ++k) qr[k] = (rr & 1) ? mine[rr / 2][k].y : mine[rr / 2][k].x;
-                        store_k<float, KH>(qz + i * M + hl * KH, qr);
-                        float pi[KH];
-                        load_k<float, KH>(pz + i * M + hl * KH, pi);
+                            for (int k = 0; k < KH; ++k) qr[k] = (rr & 1) ? h2[rr / 2][k].y : h2[rr / 2][k].x;
+                            store_k<float, KH>(qz + i * M + gl * KH, qr);
+                            float pi[KH];
+                            load_k<float, KH>(pz + i * M + gl * KH, pi);
 #pragma unroll
-                        for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
+                            for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
+                        }
+                    }
+                } else {
+                    float2 h1[KH];   // rows 4 b16 + 2 b8, + 1
+#pragma unroll
+                    for (int k = 0; k < KH; ++k) {
+                        const float2 keep = b8 ? h2[1][k] : h2[0][k];
+                        const float2 send = b8 ? h2[0][k] : h2[1][k];
+                        float2 got;
+                        got.x = __shfl_xor_sync(0xffffffffu, send.x, 8);
+                        got.y = __shfl_xor_sync(0xffffffffu, send.y, 8);
+                        h1[k] = make_float2(keep.x + got.x, keep.y + got.y);
+                    }
+                    if constexpr (NG == 4) {
+#pragma unroll
+                        for (int rr = 0; rr < 2; ++rr) {
+                            const int r = 4 * b16 + 2 * b8 + rr;
+                            if (r < nrows) {
+                                const int64_t i = r0 + r;
+                                float qr[KH];
+#pragma unroll
+                                for (int k = 0; k < KH; ++k) qr[k] = rr ? h1[k].y : h1[k].x;
+                                store_k<float, KH>(qz + i * M + gl * KH, qr);
+                                float pi[KH];
+                                load_k<float, KH>(pz + i * M + gl * KH, pi);
+#pragma unroll
+                                for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
+                            }
+                        }
+                    } else {
+                        float qr[KH];   // row 4 b16 + 2 b8 + b4
+#pragma unroll
+                        for (int k = 0; k < KH; ++k) {
+                            const float keep = b4 ? h1[k].y : h1[k].x;
+                            const float send = b4 ? h1[k].x : h1[k].y;
+                            qr[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+                        }
+                        const int r = 4 * b16 + 2 * b8 + b4;
+                        if (r < nrows) {
+                            const int64_t i = r0 + r;
+                            store_k<float, KH>(qz + i * M + gl * KH, qr);
+                            float pi[KH];
+                            load_k<float, KH>(pz + i * M + gl * KH, pi);
+#pragma unroll
+                            for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
+                        }
                     }
                 }
 #pragma unroll
@@ -1040,20 +1103,24 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
                 }
             }
         }
-        // the tile's dot of each probe column: rows 0-3 of every block (half 0) plus rows 4-7
-        // (half 1), in that order
+        // the tile's dot of each probe column: the groups' rows combined in a fixed order (lane
+        // masks 16, then 8, then 4, the lower group first)
         double dzt[KH];
 #pragma unroll
         for (int k = 0; k < KH; ++k) {
-            const double v = dz[k].value();
-            const double o = __shfl_xor_sync(0xffffffffu, v, 16);
-            dzt[k] = half ? o + v : v + o;
+            double v = dz[k].value();
+#pragma unroll
+            for (int o = 16; o >= LG; o >>= 1) {
+                const double w = __shfl_xor_sync(0xffffffffu, v, o);
+                v = (lane & o) ? w + v : v + w;
+            }
+            dzt[k] = v;
         }
         if (seg_tiles == 1) {
             // every tile is a segment of its own: its partial dots go straight to part
-            if (half == 0) {
+            if (grp == 0) {
 #pragma unroll
-                for (int k = 0; k < KH; ++k) part[(int64_t)(1 + hl * KH + k) * pstride + (int64_t)t] = dzt[k];
+                for (int k = 0; k < KH; ++k) part[(int64_t)(1 + gl * KH + k) * pstride + (int64_t)t] = dzt[k];
             }
             if (lane == 0) part[(int64_t)t] = HAS_Y ? dy.value() : 0.0;
             t = __shfl_sync(0xffffffffu, tn, 0);
@@ -1061,9 +1128,9 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
         }
         // the tile's partial dots, then the segment count; the segment's last tile reduces it
         double *tp = tpart + (int64_t)t * (M + 1);
-        if (half == 0) {
+        if (grp == 0) {
 #pragma unroll
-            for (int k = 0; k < KH; ++k) tp[1 + hl * KH + k] = dzt[k];
+            for (int k = 0; k < KH; ++k) tp[1 + gl * KH + k] = dzt[k];
         }
         if (lane == 0) tp[0] = HAS_Y ? dy.value() : 0.0;
         __threadfence();
@@ -1138,14 +1205,15 @@ inline RBTiles rb_tiles(int64_t nblk, int nb)
     return t;
 }
 
-template <int KH>
+template <int KH, int NG>
 gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts)
 {
+    constexpr int M = kWarp / NG * KH;
     const size_t smem = rb_smem<KH>();
-    auto kern = k_spmm_rb<KH, true>;
+    auto kern = k_spmm_rb<KH, NG, true>;
     GP2S_TRY(smem_attr(c, (const void *)kern, smem));
     const RBTiles tl = rb_tiles(ceil_div(c->A.n, kRB), nb);
-    GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (16 * KH + 1)));
+    GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (M + 1)));
     RBWork *work = reinterpret_cast<RBWork *>(c->counters.as<char>() + kRBWorkOffset);
     kern<<<tl.ctas, RBCfg<KH>::threads, smem, c->stream>>>(c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
                                                      c->rb_val.as<float>(), c->A.n, (const float *)B.py,
@@ -1517,17 +1585,25 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
                  : "memory");
 }
 
+// two stages of (M^{-1} block, residual block), the y column's two staged residual blocks and its
+// split products (WY), the two mbarriers
 template <int BJ, int M>
 size_t pp_smem()
 {
-    return sizeof(float) * 2 * ((size_t)BJ * BJ + (size_t)BJ * M) + 64;
+    return sizeof(float) * (2 * ((size_t)BJ * BJ + (size_t)BJ * M) + 2 * (size_t)BJ + 4 * (size_t)BJ) + 64;
 }
 
-template <int BJ, int M>
+// WY: the y column's PCG update rides along on the same staged M^{-1} blocks (when it uses the
+// probes' factors): x_y += alpha_y p_y, r_y -= alpha_y q_y by the producers, z_y = M^{-1} r_y by the
+// consumers (each half of them sums half of the block's columns), partial dots in column 0 of
+// part_rz / part_rr.  This saves the y column's own pass over all of M^{-1} per iteration.
+template <int BJ, int M, bool WY>
 __global__ void __launch_bounds__(kPPThreads, 1)
 k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__restrict__ rz,
            const float *__restrict__ qz, float *__restrict__ zz, const double *__restrict__ sc,
-           double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride, int *__restrict__ err)
+           double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride, int *__restrict__ err,
+           float *__restrict__ xy, float *__restrict__ ry, const float *__restrict__ py, const float *__restrict__ qy,
+           float *__restrict__ zy)
 {
     // Warp-specialised: warps 8..15 (producers) turn the staged r of block k into r - alpha q and
     // hand the stage over through named barrier 1 + (k & 1); warps 0..7 (consumers) take it, form
@@ -1541,15 +1617,19 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
     constexpr int TR = 8;                      // tile rows per consumer thread
     constexpr int NTILE = (BJ / TR) * CG;      // consumer tiles (<= NT; the rest of the consumers idle)
     static_assert(NF4 % NT == 0 && NT % CG == 0 && NTILE <= NT, "block shape");
+    static_assert(!WY || NT == 2 * BJ, "the y product splits each block's columns over two halves of the consumers");
     extern __shared__ __align__(128) unsigned char pp_sh[];
     float *stage0 = reinterpret_cast<float *>(pp_sh);
     float *stage1 = stage0 + BJ * BJ + BJ * M;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(stage1 + BJ * BJ + BJ * M);
+    float *ys = stage1 + BJ * BJ + BJ * M;     // 2 x BJ: the y column's residual blocks
+    float *yp = ys + 2 * BJ;                   // 2 x 2 x BJ: halves of z_y = M^{-1} r_y
+    uint64_t *bar = reinterpret_cast<uint64_t *>(yp + 4 * BJ);
     const int tid = threadIdx.x;
     const bool producer = tid >= NT;
     const int t = producer ? tid - NT : tid;
     const int cg = t % CG;                     // this thread's four columns, in either role
     double dacc[4] = {0.0, 0.0, 0.0, 0.0};     // r^T r (producers) or r^T z (consumers)
+    double ydacc = 0.0;                        // the y column's r^T r (producers) or r^T z (consumers)
     const int64_t nmine = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     auto issue = [&](int64_t k) {
@@ -1577,6 +1657,8 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
         float a4[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) a4[q] = (float)sc[(cg * 4 + q + 1) * kScal + S_ALPHA];
+        const double alpha_y = WY ? sc[S_ALPHA] : 0.0;
+        const float ay = (float)alpha_y;
         bool ok = true;
         for (int64_t k = 0; k < nmine; ++k) {
             float *R = ((k & 1) ? stage1 : stage0) + BJ * BJ;
@@ -1587,6 +1669,17 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
             for (int j = 0; j < PER; ++j) {
                 const int e = t + j * NT;
                 q4[j] = e / CG < nb ? reinterpret_cast<const float4 *>(qz + i0 * M)[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            // the y column's row i0 + t (the same arithmetic as the y column's own PCG step)
+            float yr = 0.0f, yq = 0.0f, yx = 0.0f, ypv = 0.0f;
+            const bool yrow = WY && t < nb;
+            if (yrow) {
+                yr = ry[i0 + t];
+                if (alpha_y != 0.0) {
+                    yq = qy[i0 + t];
+                    yx = xy[i0 + t];
+                    ypv = py[i0 + t];
+                }
             }
             // a copy that never lands is reported; the stage is handed over all the same so that
             // the consumers never wait on a barrier nobody arrives at
@@ -1615,6 +1708,16 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) dacc[q] += (double)srr[q];
+            if (WY && t < BJ) {
+                // after the stage's wait: the consumers are done with the block two back
+                if (yrow && alpha_y != 0.0) {
+                    xy[i0 + t] = yx + ay * ypv;
+                    yr = yr - ay * yq;
+                    ry[i0 + t] = yr;
+                }
+                if (yrow) ydacc = fma((double)yr, (double)yr, ydacc);
+                ys[(k & 1) * BJ + t] = yr;
+            }
             asm volatile("bar.arrive %0, %1;" ::"r"(1 + (int)(k & 1)), "r"(kPPThreads) : "memory");
         }
         if (!ok && t == 0) {
@@ -1672,11 +1775,27 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
 #pragma unroll
             for (int q = 0; q < 4; ++q) dacc[q] += (double)srz[q];
             }
+            float yri = 0.0f;
+            if (WY) {
+                // half h = t / BJ of z_y[i] = sum_kk M^{-1}[kk][i] r_y[kk], kk in [h BJ/2, (h+1) BJ/2)
+                const int i = t % BJ, h = t / BJ;
+                const float *yrs = ys + (k & 1) * BJ;
+                float zp = 0.0f;
+#pragma unroll 8
+                for (int kk = h * (BJ / 2); kk < (h + 1) * (BJ / 2); ++kk) zp = fmaf(MT[kk * BJ + i], yrs[kk], zp);
+                yp[((k & 1) * 2 + h) * BJ + i] = zp;
+                if (t < BJ) yri = yrs[t];
+            }
             // every consumer is done with the stage: refill it with block k + 2
             asm volatile("bar.sync 3, %0;" ::"r"(NT) : "memory");
             if (t == 0 && k + 2 < nmine) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 issue(k + 2);
+            }
+            if (WY && t < nb) {
+                const float z = yp[((k & 1) * 2) * BJ + t] + yp[((k & 1) * 2 + 1) * BJ + t];
+                zy[i0 + t] = z;
+                ydacc = fma((double)yri, (double)z, ydacc);
             }
         }
     }
@@ -1695,6 +1814,21 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
         }
         part_rz[(int64_t)(tid + 1) * pstride + blockIdx.x] = s1;
         part_rr[(int64_t)(tid + 1) * pstride + blockIdx.x] = s2;
+    }
+    if (WY) {
+        // the y column's partials: consumers' r^T z, then producers' r^T r, each in thread order
+        __syncthreads();
+        red[tid] = ydacc;
+        __syncthreads();
+        if (tid == 0) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int u = 0; u < NT; ++u) {
+                s1 += red[u];
+                s2 += red[NT + u];
+            }
+            part_rz[blockIdx.x] = s1;
+            part_rr[blockIdx.x] = s2;
+        }
     }
 }
 
@@ -1966,18 +2100,28 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     const bool pc_async = pc_avail && c->pc_async && (m == 32 || m == 64) && bjz == 128;
     const int pga = (int)std::min<int64_t>(c->num_sms, nblkz);
     int *dev_err = flags + 3;
+    // the y column's PCG update joins the probe kernel when both use the same factors
+    const bool pc_fuse_y = pc_async && pcy && bjy == bjz && c->pc_fuse_y;
     if (pc_async) {
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64>, pp_smem<128, 64>()));
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32>, pp_smem<128, 32>()));
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64, false>, pp_smem<128, 64>()));
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32, false>, pp_smem<128, 32>()));
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64, true>, pp_smem<128, 64>()));
+        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32, true>, pp_smem<128, 32>()));
     }
-    auto launch_pc_probe = [&](int mm) -> gp2s_status {
+    auto launch_pc_probe = [&](int mm, bool wy) -> gp2s_status {
         float *rzp = (float *)B.rz, *zzp = (float *)B.zz;
         const float *qzp = (const float *)B.qz;
-#define GP2S_PP(BJ_, M_)                                                                                     \
-    k_pc_probe<BJ_, M_><<<pga, kPPThreads, pp_smem<BJ_, M_>(), c->stream>>>(n, nblkz, Minvz, rzp, qzp, zzp, sc, \
-                                                                           part, part_rr, pstride, dev_err)
-        if (mm == 64) GP2S_PP(128, 64);
-        else GP2S_PP(128, 32);
+#define GP2S_PP(BJ_, M_, WY_)                                                                                \
+    k_pc_probe<BJ_, M_, WY_><<<pga, kPPThreads, pp_smem<BJ_, M_>(), c->stream>>>(                           \
+        n, nblkz, Minvz, rzp, qzp, zzp, sc, part, part_rr, pstride, dev_err, (float *)B.xy, (float *)B.ry, \
+        (const float *)B.py, (const float *)B.qy, (float *)B.zy)
+        if (mm == 64) {
+            if (wy) GP2S_PP(128, 64, true);
+            else GP2S_PP(128, 64, false);
+        } else {
+            if (wy) GP2S_PP(128, 32, true);
+            else GP2S_PP(128, 32, false);
+        }
 #undef GP2S_PP
         return GP2S_OK;
     };
@@ -2011,20 +2155,23 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         k_scal_alpha<<<kc, 256, 0, c->stream>>>(part, pstride, np, sc, active, flags, rec, ksteps, lucky);
         GP2S_LAUNCH(c);
         GP2S_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int) * 2, c->stream));
+        const bool fused_y = mc > 0 && pcz && pc_fuse_y;
         if (mc > 0) {
-            if (pcz && pc_async) GP2S_TRY(launch_pc_probe(mc));
+            if (pcz && pc_async) GP2S_TRY(launch_pc_probe(mc, fused_y));
             else if (pcz) GP2S_PCZ(PC_UPDATE, mc);
             else k_update<T><<<nbz, ut, 0, c->stream>>>(n, m, (T *)B.xz, (T *)B.rz, (const T *)B.pz, (const T *)B.qz,
                                                          (T *)B.xy, (T *)B.ry, (const T *)B.py, (const T *)B.qy, sc,
                                                          part, pstride, nbz);
             GP2S_LAUNCH(c);
         }
-        if (pcy) GP2S_PCY(PC_UPDATE);
-        else k_update<T><<<nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, (T *)B.xz, (T *)B.rz, (const T *)B.pz,
-                                                     (const T *)B.qz, (T *)B.xy, (T *)B.ry, (const T *)B.py,
-                                                     (const T *)B.qy, sc, part, pstride, 0);
-        GP2S_LAUNCH(c);
-        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, part_rr, pstride, pcy ? pgy : nby,
+        if (!fused_y) {
+            if (pcy) GP2S_PCY(PC_UPDATE);
+            else k_update<T><<<nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, (T *)B.xz, (T *)B.rz, (const T *)B.pz,
+                                                         (const T *)B.qz, (T *)B.xy, (T *)B.ry, (const T *)B.py,
+                                                         (const T *)B.qy, sc, part, pstride, 0);
+            GP2S_LAUNCH(c);
+        }
+        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, part_rr, pstride, fused_y ? pga : pcy ? pgy : nby,
                                                pcz ? (pc_async ? pga : pgz) : nbz, sc, active, flags + 1, rec, ksteps,
                                                kmin_probe, pcy, pcz, lucky);
         GP2S_LAUNCH(c);
