@@ -1370,7 +1370,7 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
           float *__restrict__ rz, float *__restrict__ pz, const float *__restrict__ qz, float *__restrict__ zz,
           float *__restrict__ xy, float *__restrict__ ry, float *__restrict__ py, const float *__restrict__ qy,
           float *__restrict__ zy, const double *__restrict__ rhs_y, const double *__restrict__ sc,
-          double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride)
+          double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride, int wy)
 {
     constexpr bool SETP = MODE != PC_UPDATE;   // p = z (INIT, RESTART)
     extern __shared__ __align__(16) float pc_sh[];
@@ -1378,6 +1378,13 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
         float *MT = pc_sh;                       // M^{-1} (symmetric, so no transpose)
         float *R = pc_sh + BJ * BJ;              // BJ x m residual block
         float *Pd = R + BJ * m;                  // (BJ / 4) x m partial dot rows (r^T z)
+        // wy (UPDATE only): the y column's update rides along on the staged M^{-1} block, its
+        // residual block staged after Pd; threads [0, BJ) own its rows in the elementwise phase and
+        // the last BJ threads form z_y = M^{-1} r_y beside the probes' product
+        float *Ry = Pd + (BJ / 4) * m;
+        double yrr = 0.0, yrz = 0.0;
+        const double alpha_y = (MODE == PC_UPDATE && wy) ? sc[S_ALPHA] : 0.0;
+        const int yu = (int)threadIdx.x - ((int)blockDim.x - BJ);
         double acc_rz = 0.0, acc_rr = 0.0;       // thread c < m: this CTA's column sums
         // elementwise phase: thread t owns the 4 columns 4 (t % cgs) .. +3 of rows t / cgs + k rps
         const int cgs = m / 4;
@@ -1419,6 +1426,22 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
                     *reinterpret_cast<float4 *>(R + i * m + ecg * 4) = make_float4(r4[0], r4[1], r4[2], r4[3]);
                 }
             }
+            if (MODE == PC_UPDATE && wy && (int)threadIdx.x < BJ) {
+                const int i = threadIdx.x;
+                float r = 0.0f;
+                if (i < nb) {
+                    const int64_t e = i0 + i;
+                    r = ry[e];
+                    if (alpha_y != 0.0) {
+                        const float a = (float)alpha_y;
+                        xy[e] = xy[e] + a * py[e];
+                        r = r - a * qy[e];
+                        ry[e] = r;
+                    }
+                    yrr = fma((double)r, (double)r, yrr);
+                }
+                Ry[i] = r;
+            }
             __syncthreads();
             // z = M^{-1} r, written with the partial dots of this block
             bj_tile_mm<BJ>(MT, R, m, [&](int it, int c0, float (&acc)[4][4]) {
@@ -1436,6 +1459,16 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
 #pragma unroll
                 for (int q = 0; q < 4; ++q) Pd[(it / 4) * m + c0 + q] = drz[q];
             });
+            if (MODE == PC_UPDATE && wy && yu >= 0) {
+                // z_y[u] = sum_k M^{-1}[k][u] r_y[k] (the y column's own step sums the same way)
+                float z = 0.0f;
+#pragma unroll 8
+                for (int k = 0; k < BJ; ++k) z = fmaf(MT[k * BJ + yu], Ry[k], z);
+                if (yu < nb) {
+                    zy[i0 + yu] = z;
+                    yrz = fma((double)Ry[yu], (double)z, yrz);
+                }
+            }
             __syncthreads();
             if ((int)threadIdx.x < m) {
                 float srz = 0.0f, srr = 0.0f;
@@ -1452,6 +1485,27 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
         if ((int)threadIdx.x < m) {
             part_rz[(int64_t)(threadIdx.x + 1) * pstride + blockIdx.x] = acc_rz;
             part_rr[(int64_t)(threadIdx.x + 1) * pstride + blockIdx.x] = acc_rr;
+        }
+        if (MODE == PC_UPDATE && wy) {
+            // the y column's partials of this CTA: warp sums, then the warps in order
+            __shared__ double yred[2][kPCThreads / kWarp];
+            double v1 = yrz, v2 = yrr;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+                v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                yred[0][threadIdx.x >> 5] = v1;
+                yred[1][threadIdx.x >> 5] = v2;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double s1 = 0.0, s2 = 0.0;
+                for (int w = 0; w < (int)(blockDim.x / kWarp); ++w) { s1 += yred[0][w]; s2 += yred[1][w]; }
+                part_rz[blockIdx.x] = s1;
+                part_rr[blockIdx.x] = s2;
+            }
         }
     } else {
         // y column: the CTA's BJ-thread groups each take one block; thread i of a group owns
@@ -1837,7 +1891,7 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
 // residuals (kPCThreads / BJ blocks of BJ rows).  The launch covers both.
 size_t pc_smem(int m, int bj)
 {
-    const size_t z = m > 0 ? (size_t)bj * bj + (size_t)bj * m + (size_t)(bj / 4) * m : 0;
+    const size_t z = m > 0 ? (size_t)bj * bj + (size_t)bj * m + (size_t)(bj / 4) * m + bj : 0;
     const size_t y = (size_t)kPCThreads;
     return sizeof(float) * (z > y ? z : y) + 64;
 }
@@ -2073,21 +2127,22 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         }
     }
     // probe group (bjz-row blocks) and y column (bjy-row blocks) launches
-#define GP2S_PCZ_BJ(MODE, BJ, MM)                                                                                   \
+#define GP2S_PCZ_BJ(MODE, BJ, MM, WY)                                                                               \
     k_pc_step<MODE, BJ><<<pgz, kPCThreads, pc_smem(MM, BJ), c->stream>>>(                                          \
         n, MM, nblkz, pgz, Minvz, (float *)B.xz, (float *)B.rz, (float *)B.pz, (const float *)B.qz, (float *)B.zz, \
         (float *)B.xy, (float *)B.ry, (float *)B.py, (const float *)B.qy, (float *)B.zy, rhs_y, sc, part, part_rr,  \
-        pstride)
-#define GP2S_PCZ(MODE, MM)                                                                                          \
+        pstride, WY)
+#define GP2S_PCZ_WY(MODE, MM, WY)                                                                                   \
     do {                                                                                                            \
-        if (bjz == 128) GP2S_PCZ_BJ(MODE, 128, MM);                                                                 \
-        else GP2S_PCZ_BJ(MODE, 64, MM);                                                                             \
+        if (bjz == 128) GP2S_PCZ_BJ(MODE, 128, MM, WY);                                                             \
+        else GP2S_PCZ_BJ(MODE, 64, MM, WY);                                                                         \
     } while (0)
+#define GP2S_PCZ(MODE, MM) GP2S_PCZ_WY(MODE, MM, 0)
 #define GP2S_PCY_BJ(MODE, BJ)                                                                                       \
     k_pc_step<MODE, BJ><<<pgy, kPCThreads, pc_smem(0, BJ), c->stream>>>(                                           \
         n, 0, nblky, 0, Minvy, (float *)B.xz, (float *)B.rz, (float *)B.pz, (const float *)B.qz, (float *)B.zz,    \
         (float *)B.xy, (float *)B.ry, (float *)B.py, (const float *)B.qy, (float *)B.zy, rhs_y, sc, part, part_rr, \
-        pstride)
+        pstride, 0)
 #define GP2S_PCY(MODE)                                                                                              \
     do {                                                                                                            \
         if (bjy == 128) GP2S_PCY_BJ(MODE, 128);                                                                     \
@@ -2100,8 +2155,8 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     const bool pc_async = pc_avail && c->pc_async && (m == 32 || m == 64) && bjz == 128;
     const int pga = (int)std::min<int64_t>(c->num_sms, nblkz);
     int *dev_err = flags + 3;
-    // the y column's PCG update joins the probe kernel when both use the same factors
-    const bool pc_fuse_y = pc_async && pcy && bjy == bjz && c->pc_fuse_y;
+    // the y column's PCG update joins the probe group's step when both use the same factors
+    const bool pc_fuse_y = pcy && bjy == bjz && c->pc_fuse_y;
     if (pc_async) {
         GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64, false>, pp_smem<128, 64>()));
         GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32, false>, pp_smem<128, 32>()));
@@ -2158,7 +2213,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         const bool fused_y = mc > 0 && pcz && pc_fuse_y;
         if (mc > 0) {
             if (pcz && pc_async) GP2S_TRY(launch_pc_probe(mc, fused_y));
-            else if (pcz) GP2S_PCZ(PC_UPDATE, mc);
+            else if (pcz) GP2S_PCZ_WY(PC_UPDATE, mc, fused_y ? 1 : 0);
             else k_update<T><<<nbz, ut, 0, c->stream>>>(n, m, (T *)B.xz, (T *)B.rz, (const T *)B.pz, (const T *)B.qz,
                                                          (T *)B.xy, (T *)B.ry, (const T *)B.py, (const T *)B.qy, sc,
                                                          part, pstride, nbz);
@@ -2171,7 +2226,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
                                                          (const T *)B.qy, sc, part, pstride, 0);
             GP2S_LAUNCH(c);
         }
-        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, part_rr, pstride, fused_y ? pga : pcy ? pgy : nby,
+        k_scal_beta<<<kc, 256, 0, c->stream>>>(part, part_rr, pstride, fused_y ? (pc_async ? pga : pgz) : pcy ? pgy : nby,
                                                pcz ? (pc_async ? pga : pgz) : nbz, sc, active, flags + 1, rec, ksteps,
                                                kmin_probe, pcy, pcz, lucky);
         GP2S_LAUNCH(c);
