@@ -125,8 +125,11 @@ typedef struct {
                                 default 64 */
     int32_t lanczos_steps;   /* SLQ steps k per probe, default 100 */
     int32_t max_iter;        /* iteration cap per CG solve, default 20000 */
-    double tol_inner;        /* FP32 inner CG relative residual of the first y solve, default 1e-6
-                                (about the FP32 floor: one refinement step then reaches tol_refine) */
+    double tol_inner;        /* relative residual at which an FP32 y solve without reliable updates
+                                stops before an FP64 refinement step (the MIXED y column with the
+                                block-Jacobi preconditioner instead replaces its recursive residual
+                                by the true FP64 residual at every tenfold gain and stops at
+                                tol_refine), default 1e-6 */
     double tol_refine;       /* target |y - A a| / |y| of the y solve (FP64 residual), default 1e-8 */
     double tol_probe;        /* relative residual of the probe solves used by the gradient, default 1e-5 */
     uint64_t seed;           /* probe seed, default 0 */
@@ -136,7 +139,7 @@ typedef struct {
                                 Default 2. */
     int32_t exact_support;   /* 1 = skip the FP32 guard-band pre-test (every candidate pair is
                                 decided by the FP64 test); default 0 */
-    int32_t max_outer;       /* refinement steps cap, default 8 */
+    int32_t max_outer;       /* refinement steps (restarted FP64-residual solves) cap, default 8 */
     int32_t profile;         /* 1 = time every SpMM launch with CUDA events (gp2s_lml_info.ms_spmm); default 0 */
     int32_t bj_block;        /* rows per block-Jacobi block (precond = 2): 64, 128, or 0 =
                                 automatic (128 when A has at least 64 stored entries per row and
@@ -145,7 +148,8 @@ typedef struct {
                                 r, exact_support and precision are unchanged: only the bump
                                 tables and values are recomputed; 1 = always rebuild; default 0 */
     int32_t solver;          /* solver of the y column: GP2S_SOLVER_CG (default; multi-RHS with the
-                                probes, FP32 in MIXED precision with FP64 refinement) or
+                                probes, FP32 in MIXED precision with FP64 reliable updates and
+                                refinement) or
                                 GP2S_SOLVER_MINRES (App. B.6's solver: FP64 MINRES on
                                 D^{-1/2} A D^{-1/2}, restarted on the FP64 residual until
                                 tol_refine); the probe columns always run CG */
@@ -167,7 +171,7 @@ typedef struct {
 
 typedef struct {
     int32_t iters;           /* FP32 (or FP64) CG iterations of the y column, all refinement steps */
-    int32_t outer;           /* refinement steps */
+    int32_t outer;           /* refinement steps (0 when the reliable updates met tol_refine) */
     double relres;           /* final |y - A a| / |y|, FP64 residual */
     float ms;
 } gp2s_solve_info;

@@ -280,6 +280,10 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (gr && std::strcmp(gr, "0") == 0) c->use_graphs = false;
     const char *pa = std::getenv("GP2S_PC_ASYNC");
     if (pa && std::strcmp(pa, "0") == 0) c->pc_async = false;
+    const char *ry = std::getenv("GP2S_RELIABLE_Y");
+    if (ry && std::strcmp(ry, "0") == 0) c->reliable_y = false;
+    const char *rd = std::getenv("GP2S_RELIABLE_DELTA");
+    if (rd && std::atof(rd) > 0.0 && std::atof(rd) < 1.0) c->reliable_delta = std::atof(rd);
     const char *fy = std::getenv("GP2S_PC_FUSE_Y");
     if (fy && std::strcmp(fy, "0") == 0) c->pc_fuse_y = false;
     const char *sh = std::getenv("GP2S_SPMM_HALF");

@@ -18,6 +18,12 @@ constexpr int kMaxDim = 4;
 constexpr int kMaxBumps = 32;
 constexpr int kWarp = 32;
 
+// The CG scalar block: kScal doubles per column c (y = 0, probes 1..m) at sc + c kScal:
+// [rho, alpha, beta, b2, pq, rr, steps, tol2b2, rho of the previous step, why an active column
+// stopped (1: in the beta kernel, its direction update still pending; 2: in the alpha kernel)]
+constexpr int kScal = 10;
+enum { S_RHO = 0, S_ALPHA, S_BETA, S_B2, S_PQ, S_RR, S_STEPS, S_TOL, S_RHO_PREV, S_STOP };
+
 // ------------------------------------------------------------------------------------------
 // Kernel hyperparameters passed by value to kernels (Eq. 3, Eq. 7, Sec. 4.3).
 // ------------------------------------------------------------------------------------------
@@ -120,6 +126,8 @@ struct gp2s_ctx {
     bool pc_async = true;           // probe-group PCG step on the bulk-copy pipelined kernel
     bool spmm_half = false;         // 16 and 32 columns on half-warp entry groups (KH = 1, 2)
     bool pc_fuse_y = true;          // the y column's PCG update inside the probe kernel
+    bool reliable_y = true;         // reliable updates of the y column instead of restarted refinement
+    double reliable_delta = 0.1;    // residual replacement at every gain of this factor
                                     // (GP2S_PC_ASYNC=0: the staged kernel)
     cudaStream_t capture_stream = nullptr;   // private stream the graphs are captured on
     // batched form: worker contexts (own stream and workspace each), created on first use

@@ -27,11 +27,7 @@ constexpr int kSpmmThreads = 1024;
 constexpr int kSpmmWarps = kSpmmThreads / kWarp;
 constexpr int kMaxPartBlocks = 152 * 8;
 constexpr int kRBWorkOffset = 224;   // byte offset of the RB8 SpMM's tile counter in c->counters
-constexpr int kScal = 8;   // doubles per column in the scalar block
 constexpr int kMaxCols = 129;   // y + up to 128 probes
-
-// scalar block layout per column c: [rho, alpha, beta, b2, pq, rr, steps, tol2b2]
-enum { S_RHO = 0, S_ALPHA, S_BETA, S_B2, S_PQ, S_RR, S_STEPS, S_TOL };
 
 // ---------------------------------------------------------------------------------------------
 // SplitMix64 Rademacher probes (same definition as the oracle's, written independently):
@@ -323,6 +319,8 @@ __global__ void k_scal_init(const double *__restrict__ part, const double *__res
         q[S_BETA] = 0.0;
         q[S_STEPS] = 0.0;
         q[S_RR] = s2;
+        q[S_RHO_PREV] = 0.0;
+        q[S_STOP] = 0.0;
         active[c] = s > 0.0 ? 1 : 0;
     }
 }
@@ -347,6 +345,7 @@ __global__ void k_scal_alpha(const double *__restrict__ part, int pstride, int n
         if (!(s > 0.0)) {
             active[c] = 0;
             q[S_ALPHA] = 0.0;
+            q[S_STOP] = 2.0;
             if (!(q[S_RR] <= lucky * q[S_B2])) atomicOr(&flags[0], 1);   // breakdown
             return;
         }
@@ -381,6 +380,7 @@ __global__ void k_scal_beta(const double *__restrict__ part, const double *__res
         int st = (int)q[S_STEPS];
         if (c > 0 && rec && st < ksteps) rec[((int64_t)(c - 1) * ksteps + st) * 2 + 1] = b;
         q[S_BETA] = b;
+        q[S_RHO_PREV] = q[S_RHO];
         q[S_RHO] = s;
         q[S_STEPS] = (double)(st + 1);
         bool conv = s2 <= q[S_TOL];
@@ -390,6 +390,7 @@ __global__ void k_scal_beta(const double *__restrict__ part, const double *__res
         const bool exhausted = s2 <= lucky * q[S_B2];
         if ((conv && st + 1 >= kmin) || exhausted || !(s == s)) {
             active[c] = 0;
+            q[S_STOP] = 1.0;
             // p is not updated for inactive columns (beta unused)
         } else {
             atomicAdd(count, 1);
@@ -405,6 +406,33 @@ __global__ void k_scal_restart(const double *__restrict__ part, int pstride, int
     const int c = blockIdx.x + 1;
     double s = block_sum(part + (int64_t)c * pstride, nparts);
     if (threadIdx.x == 0 && active[c]) sc[c * kScal + S_RHO] = s;
+}
+
+// Reliable update of the y column (column 0) after its residual was replaced by the true one.
+// The column stopped in the beta kernel of some step j, before that step's direction update: the
+// recurrence continues there with the replaced residual, rho' = r'^T z', beta = rho' / rho_j
+// (p = z' + beta p follows in the direction kernel).  A column that stopped in the alpha kernel
+// (p^T A p at the rounding level) restarts its direction, beta = 0.  The new |r|^2 becomes the
+// reference of the rounding-level rule (b2) and the column stops again once |r| has fallen by
+// the factor delta.
+__global__ void k_scal_replace(const double *__restrict__ part, const double *__restrict__ part_rr, int nparts,
+                               double *__restrict__ sc, int *__restrict__ active, double delta)
+{
+    double s = block_sum(part, nparts);
+    __syncthreads();
+    double s2 = block_sum(part_rr, nparts);
+    if (threadIdx.x == 0) {
+        const bool cont = sc[S_STOP] == 1.0 && sc[S_RHO_PREV] > 0.0;
+        sc[S_BETA] = cont ? s / sc[S_RHO_PREV] : 0.0;
+        sc[S_RHO_PREV] = sc[S_RHO];
+        sc[S_RHO] = s;
+        sc[S_RR] = s2;
+        sc[S_B2] = s2;
+        sc[S_TOL] = delta * delta * s2;
+        sc[S_ALPHA] = 0.0;
+        sc[S_STOP] = 0.0;
+        active[0] = s > 0.0 ? 1 : 0;
+    }
 }
 
 // x += alpha p ; r -= alpha q ; partial r^T r.  Probe group: thread t owns column t % m.
@@ -1363,7 +1391,9 @@ __device__ __forceinline__ void bj_tile_mm(const float *__restrict__ MT, const f
 // x += alpha p, r -= alpha q, z = M^{-1} r.  RESTART (a CG column switching to PCG): x and r kept,
 // z = M^{-1} r, p = z.  All emit per-CTA partial dots r^T z and r^T r per column.
 // CTAs [0, gz) work on the probe group (n x m), CTAs [gz, gridDim) on the y column.
-enum { PC_INIT = 0, PC_UPDATE = 1, PC_RESTART = 2 };
+// REPLACE (y column only): r = rhs (the true residual), x = 0, z = M^{-1} r; p is kept (a reliable
+// update of the y column's recursion).
+enum { PC_INIT = 0, PC_UPDATE = 1, PC_RESTART = 2, PC_REPLACE = 3 };
 template <int MODE, int BJ>
 __global__ void __launch_bounds__(kPCThreads, 3)
 k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv32, float *__restrict__ xz,
@@ -1372,7 +1402,7 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
           float *__restrict__ zy, const double *__restrict__ rhs_y, const double *__restrict__ sc,
           double *__restrict__ part_rz, double *__restrict__ part_rr, int pstride, int wy)
 {
-    constexpr bool SETP = MODE != PC_UPDATE;   // p = z (INIT, RESTART)
+    constexpr bool SETP = MODE == PC_INIT || MODE == PC_RESTART;   // p = z
     extern __shared__ __align__(16) float pc_sh[];
     if ((int)blockIdx.x < gz) {
         float *MT = pc_sh;                       // M^{-1} (symmetric, so no transpose)
@@ -1529,7 +1559,7 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
                 float r = 0.0f;
                 if (i < nb) {
                     const int64_t e = i0 + i;
-                    if (MODE == PC_INIT) {
+                    if (MODE == PC_INIT || MODE == PC_REPLACE) {
                         r = (float)rhs_y[e];
                         ry[e] = r;
                         xy[e] = 0.0f;
@@ -2066,11 +2096,30 @@ struct GraphRun {
     }
 };
 
+// Reliable updates of the y column (FP32 block-Jacobi PCG): its recursive FP32 residual drifts
+// from the true one at about 1e-5 relative, so instead of a restarted FP64 refinement solve the
+// column's x is folded into the FP64 accumulator xh and its residual replaced by the true FP64
+// residual b - Ah xh each time the recursion has gained the factor delta (the column stops on the
+// device, the host replaces at the next convergence check).  The search direction p is kept, so
+// the column goes on from its Krylov space and reaches tol_refine while the probe columns still
+// run (Sleijpen & van der Vorst's reliable-update scheme).
+}  // namespace
+gp2s_status y_residual(gp2s_ctx *c, const double *y_sorted_dev, double *relres);
+namespace {
+
+struct ReliableY {
+    const double *y_sorted;   // original-order y, sorted (for the original-space residual)
+    double tol_refine, delta;
+    bool done = false;        // the true residual met tol_refine
+    double relres = 0.0;
+    int replacements = 0;
+};
+
 // One CG run (x0 = 0) on columns [y | probes]; the probe right-hand sides must already be in rz.
 template <class T, class V>
 gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const double *rhs_y, double tol_y,
                    double tol_z, int kmin_probe, int ksteps, double *rec, int max_iter, int *iters_y,
-                   int *iters_z, bool *breakdown)
+                   int *iters_z, bool *breakdown, ReliableY *ru = nullptr)
 {
     const Assembled &A = c->A;
     const int64_t n = A.n;
@@ -2191,8 +2240,10 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     else k_cg_init<T><<<nby, ut, 0, c->stream>>>(n, m > 0 ? m : 1, rhs_y, (T *)B.xz, (T *)B.rz, (T *)B.pz,
                                                   (T *)B.xy, (T *)B.ry, (T *)B.py, part, pstride, 0);
     GP2S_LAUNCH(c);
-    k_scal_init<<<k, 256, 0, c->stream>>>(part, part_rr, pstride, pcy ? pgy : nby, pcz ? pgz : nbz, sc, active, tol_y,
-                                          tol_z, pcy, pcz);
+    // reliable updates need the y column's block-Jacobi step (REPLACE mode)
+    ReliableY *rel = (ru && pcy) ? ru : nullptr;
+    k_scal_init<<<k, 256, 0, c->stream>>>(part, part_rr, pstride, pcy ? pgy : nby, pcz ? pgz : nbz, sc, active,
+                                          rel ? rel->delta : tol_y, tol_z, pcy, pcz);
     GP2S_LAUNCH(c);
 
     // squared relative residual at the rounding level of the vector precision
@@ -2244,6 +2295,44 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         }
         return GP2S_OK;
     };
+    // The y column has stopped (its recursion gained the factor delta, or reached its rounding
+    // level): fold x_y into xh, form the true residual in FP64; done at tol_refine, else restart the
+    // recursion from the true residual with p kept.
+    auto replace_y = [&]() -> gp2s_status {
+        double *b64v = c->vec64.as<double>();
+        double *xh = b64v + n, *r64 = b64v + 2 * n;
+        const unsigned gbn = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 8);
+        k_accum64<float><<<gbn, 256, 0, c->stream>>>(n, (const float *)B.xy, xh);
+        GP2S_LAUNCH(c);
+        GP2S_CUDA(c, cudaMemsetAsync(B.xy, 0, sizeof(float) * (size_t)n, c->stream));
+        double relres = 0.0;
+        GP2S_TRY(y_residual(c, rel->y_sorted, &relres));
+        rel->relres = relres;
+        ++rel->replacements;
+        if (!(relres > rel->tol_refine)) {
+            rel->done = true;
+            return GP2S_OK;
+        }
+        if (bjy == 128)
+            k_pc_step<PC_REPLACE, 128><<<pgy, kPCThreads, pc_smem(0, 128), c->stream>>>(
+                n, 0, nblky, 0, Minvy, (float *)B.xz, (float *)B.rz, (float *)B.pz, (const float *)B.qz,
+                (float *)B.zz, (float *)B.xy, (float *)B.ry, (float *)B.py, (const float *)B.qy, (float *)B.zy, r64,
+                sc, part, part_rr, pstride, 0);
+        else
+            k_pc_step<PC_REPLACE, 64><<<pgy, kPCThreads, pc_smem(0, 64), c->stream>>>(
+                n, 0, nblky, 0, Minvy, (float *)B.xz, (float *)B.rz, (float *)B.pz, (const float *)B.qz,
+                (float *)B.zz, (float *)B.xy, (float *)B.ry, (float *)B.py, (const float *)B.qy, (float *)B.zy, r64,
+                sc, part, part_rr, pstride, 0);
+        GP2S_LAUNCH(c);
+        k_scal_replace<<<1, 256, 0, c->stream>>>(part, part_rr, pgy, sc, active, rel->delta);
+        GP2S_LAUNCH(c);
+        // the step's pending direction update, p = z' + beta p (y column only)
+        const int dgy = (int)std::min<int64_t>(152 * 2, ceil_div(n, 256));
+        k_direction<float><<<dgy, 256, 0, c->stream>>>(n, 0, (const float *)B.zz, (float *)B.pz, (const float *)B.zy,
+                                                       (float *)B.py, sc, active, 0, (float *)B.xz, 0);
+        GP2S_LAUNCH(c);
+        return GP2S_OK;
+    };
     // Runs of check_every iterations between two convergence checks are captured once into a CUDA
     // graph and replayed while the column set (mc, pcz) stays the same: one launch instead of
     // about seven per iteration.  The first run (it allocates the per-launch scratch), the run
@@ -2270,10 +2359,16 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
             }
         }
         GP2S_CUDA(c, cudaMemcpyAsync(hcount, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream));
+        if (rel) GP2S_CUDA(c, cudaMemcpyAsync(hcount + 4, active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
         GP2S_TRY(flush_profile(c));
         if (hcount[3]) return set_err(c, GP2S_ETIMEOUT, "a block-Jacobi stage copy did not complete (bounded wait gave up)");
-        if (hcount[1] == 0) break;
+        bool y_back = false;
+        if (rel && !rel->done && hcount[4] == 0 && !hcount[0]) {
+            GP2S_TRY(replace_y());
+            y_back = !rel->done;
+        }
+        if (hcount[1] == 0 && !y_back) break;
         if (mc > 0 && hcount[2] == 0) mc = 0;   // only the y column is left: y-only kernels
     }
 #undef GP2S_PCZ
@@ -2460,9 +2555,15 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
         }
         return GP2S_OK;
     }
+    // xhat accumulates the y solution in FP64 (the reliable updates fold x_y into it during the run)
+    GP2S_CUDA(c, cudaMemsetAsync(xh, 0, sizeof(double) * n, c->stream));
+    ReliableY ru;
+    ru.y_sorted = y_sorted_dev;
+    ru.tol_refine = o.tol_refine;
+    ru.delta = c->reliable_delta;
     if (mixed)
         GP2S_TRY((cg_run<float, float>(c, mm, c->val32.as<float>(), B, b64, tol_first, tol_z, mm > 0 ? ksteps : 0,
-                                       ksteps, rec, o.max_iter, &iy, &iz, &brk)));
+                                       ksteps, rec, o.max_iter, &iy, &iz, &brk, c->reliable_y ? &ru : nullptr)));
     else
         GP2S_TRY((cg_run<double, double>(c, mm, c->val64.as<double>(), B, b64, tol_first, tol_z,
                                          mm > 0 ? ksteps : 0, ksteps, rec, o.max_iter, &iy, &iz, &brk)));
@@ -2472,8 +2573,7 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
         res->status = GP2S_EBREAKDOWN;
         return set_err(c, GP2S_EBREAKDOWN, "CG breakdown (p^T A p <= 0 or NaN)");
     }
-    // xhat = x_y (FP64 accumulate)
-    GP2S_CUDA(c, cudaMemsetAsync(xh, 0, sizeof(double) * n, c->stream));
+    // xhat += x_y (FP64 accumulate)
     if (mixed) k_accum64<float><<<gbn, 256, 0, c->stream>>>(n, (const float *)B.xy, xh);
     else k_accum64<double><<<gbn, 256, 0, c->stream>>>(n, (const double *)B.xy, xh);
     GP2S_LAUNCH(c);

@@ -95,7 +95,7 @@ __global__ void k_slq(const double *__restrict__ rec, const double *__restrict__
     double *b = a + ksteps;
     double *q = b + ksteps;
     // number of recorded steps for this probe column (column s + 1 of the CG scalar block)
-    int steps = (int)sc[(s + 1) * 8 + 6];
+    int steps = (int)sc[(s + 1) * kScal + S_STEPS];
     int k = steps < ksteps ? steps : ksteps;
     if (k <= 0) { out[s] = 0.0; atomicOr(bad, 1); return; }
     const double *al = rec + (int64_t)s * ksteps * 2;

@@ -131,8 +131,10 @@ def test_posterior_matches_oracle(gp, ctx):
     import oracle
     w = W.random_wendconv(970, 3000, 2, L=3, sigma2=1e-3)
     h = gp.Hyper(**w["hyper"])
+    # the y solve to 1e-12: a solve stopped at relative residual tol leaves up to tol |y| / sigma^2
+    # in A^{-1} y, which at the default 1e-8 can reach the mean's 1e-8 bar
     ctx.lml(torch.tensor(w["X"], device="cuda"), torch.tensor(w["y"], device="cuda"), h,
-            gp.default_opts(logdet=gp.LOGDET_SLQ, probes=32, lanczos_steps=30, tol_probe=1e-7))
+            gp.default_opts(logdet=gp.LOGDET_SLQ, probes=32, lanczos_steps=30, tol_probe=1e-7, tol_refine=1e-12))
     rng = np.random.default_rng(2)
     Xs = np.vstack([rng.random((80, 2)), w["X"][:20], rng.random((20, 2)) * 3 - 1])
     mean, var, info = ctx.posterior(Xs)
