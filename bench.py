@@ -133,22 +133,35 @@ def make_workload(name: str, seed: int, n: int | None = None):
 
 
 FP32_INSTR_PEAK = 152 * 128 * 2.07e9   # FP32 lanes x SMs x maximum SM clock (instructions/s)
+# GB300's nominal FP64 rate (1.25 TFLOP/s), in FP64 instructions per second (a fused multiply-add
+# is two flops and one instruction)
+FP64_INSTR_PEAK = 1.25e12 / 2
 
 
-def assembly_roofline(n: int, d: int, L: int, nnz: int, ms: float, hbm_gbs: float) -> dict:
+def assembly_roofline(n: int, d: int, L: int, nnz: int, ms: float, hbm_gbs: float, mixed: bool = True) -> dict:
     """Whole assembly (sort, cell list, count, scan, fill, FP64 values) against its algorithmic
-    roofline: memory leg = the CSR written once (8 B per stored entry + 4 B per row pointer);
-    compute leg = one support test (2d FP32 instructions) and one value (2d + 8 + L instructions,
-    a fused multiply-add counted once) per unique pair, (nnz + n) / 2 pairs, at the FP32 issue
-    rate of 152 SMs x 128 lanes x 2.07 GHz."""
-    mem = 8.0 * nnz + 4.0 * (n + 1)
-    instr = 0.5 * (nnz + n) * (2 * d + 2 * d + 8 + L)
-    t_mem, t_alu = mem / (hbm_gbs * 1e9), instr / FP32_INSTR_PEAK
-    roof_ms = 1000.0 * max(t_mem, t_alu)
+    roofline, the slowest of three legs over the (nnz + n) / 2 unique pairs:
+      memory: the CSR written once, int32 columns + FP64 values (+ FP32 values in mixed
+              precision) per stored entry + 4 B per row pointer;
+      FP32:   one support test per unique pair, 2d instructions, at 152 SMs x 128 lanes x 2.07 GHz;
+      FP64:   one value per unique pair, 2d (differences, squares) + 1 (square root) + 7 (taper
+              polynomial) + L (bump products) + 3 (w0, the Jacobi scales) instructions, at the
+              nominal FP64 rate.  The values must be FP64: the refinement residual is formed with
+              them, against the FP64 matrix to 1e-8."""
+    mem = (16.0 if mixed else 12.0) * nnz + 4.0 * (n + 1)
+    pairs = 0.5 * (nnz + n)
+    instr32 = pairs * 2 * d
+    instr64 = pairs * (2 * d + 1 + 7 + L + 3)
+    t_mem, t_32, t_64 = mem / (hbm_gbs * 1e9), instr32 / FP32_INSTR_PEAK, instr64 / FP64_INSTR_PEAK
+    legs = {"hbm": t_mem, "alu_fp32": t_32, "alu_fp64": t_64}
+    bound = max(legs, key=legs.get)
+    roof_ms = 1000.0 * legs[bound]
     return {"ms": ms, "gnnz_per_s": nnz / (ms * 1e6) if ms > 0 else None,
-            "roofline": {"bound": "hbm" if t_mem >= t_alu else "alu", "bytes": mem, "fp32_instr": instr,
-                         "roof_ms": roof_ms, "frac": roof_ms / ms if ms > 0 else None,
-                         "alu_peak_instr_per_s": FP32_INSTR_PEAK}}
+            "roofline": {"bound": bound, "roof_ms": roof_ms, "frac": roof_ms / ms if ms > 0 else None,
+                         "legs_ms": {k: 1000.0 * v for k, v in legs.items()}, "bytes": mem,
+                         "fp32_instr": instr32, "fp64_instr": instr64,
+                         "alu_peak_instr_per_s": FP32_INSTR_PEAK, "fp64_peak_instr_per_s": FP64_INSTR_PEAK,
+                         "fp64_peak_source": "nominal GB300 FP64 rate, 1.25 TFLOP/s"}}
 
 
 def replica_throughput(ws: int, steps: int, total_ms: float, e2e_ms: float, device: str):

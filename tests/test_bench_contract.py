@@ -32,13 +32,21 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
-def test_assembly_roofline_is_the_larger_leg():
-    r = bench.assembly_roofline(1_000_000, 3, 8, 100_000_000, 10.0, 6789.6)["roofline"]
-    mem_s = (8.0 * 100_000_000 + 4.0 * 1_000_001) / 6789.6e9
-    alu_s = 0.5 * (100_000_000 + 1_000_000) * (3 * 4 + 8 + 8) / bench.FP32_INSTR_PEAK
-    assert r["bound"] == ("hbm" if mem_s >= alu_s else "alu")
-    assert r["roof_ms"] == pytest.approx(1000.0 * max(mem_s, alu_s))
+def test_assembly_roofline_is_the_largest_leg():
+    n, nnz, d, L = 1_000_000, 100_000_000, 3, 8
+    r = bench.assembly_roofline(n, d, L, nnz, 10.0, 6789.6)["roofline"]
+    pairs = 0.5 * (nnz + n)
+    legs = {"hbm": (16.0 * nnz + 4.0 * (n + 1)) / 6789.6e9,
+            "alu_fp32": pairs * 2 * d / bench.FP32_INSTR_PEAK,
+            "alu_fp64": pairs * (2 * d + 1 + 7 + L + 3) / bench.FP64_INSTR_PEAK}
+    assert r["bound"] == max(legs, key=legs.get)
+    assert r["roof_ms"] == pytest.approx(1000.0 * max(legs.values()))
     assert r["frac"] == pytest.approx(r["roof_ms"] / 10.0)
+    for k, v in legs.items():
+        assert r["legs_ms"][k] == pytest.approx(1000.0 * v)
+    # FP64 precision stores no FP32 copy
+    r64 = bench.assembly_roofline(n, d, L, nnz, 10.0, 6789.6, mixed=False)["roofline"]
+    assert r64["bytes"] == 12.0 * nnz + 4.0 * (n + 1)
 
 
 def test_profile_traffic_reads_the_committed_summaries():
