@@ -270,8 +270,23 @@ k_residual64(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = w0; i < n; i += nw) {
+        const int p1 = rowptr[i + 1];
         double s = 0.0;
-        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += kWarp) s = fma(val[p], x[col[p]], s);
+        // four independent entries per lane in flight (rows of up to 128 entries in one pass)
+        for (int p = rowptr[i] + lane; p < p1; p += 4 * kWarp) {
+            double v[4], g[4];
+            int cj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int q = p + u * kWarp;
+                v[u] = q < p1 ? val[q] : 0.0;
+                cj[u] = q < p1 ? col[q] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g[u] = x[cj[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s = fma(v[u], g[u], s);
+        }
         s = warp_sum(s);
         if (lane == 0) out[i] = b[i] - s;
     }
@@ -432,6 +447,48 @@ __global__ void k_scal_replace(const double *__restrict__ part, const double *__
         sc[S_ALPHA] = 0.0;
         sc[S_STOP] = 0.0;
         active[0] = s > 0.0 ? 1 : 0;
+    }
+}
+
+// Plain-CG step of the FP32 probe group, four columns per thread: r -= alpha q and the partial
+// r^T r of each column (x += alpha p is left to the direction kernel, which reads p anyway).
+// Thread t owns columns 4 (t % (m/4)) .. +3 and strides over rows; per column the CTA's partial
+// sums the threads in thread order.
+__global__ void __launch_bounds__(256)
+k_update_z4(int64_t n, int m, float *__restrict__ rz, const float *__restrict__ qz, const double *__restrict__ sc,
+            double *__restrict__ part, int pstride)
+{
+    __shared__ double red[256 * 4];
+    const int cgs = m / 4;
+    const int rps = blockDim.x / cgs;
+    const bool on = (int)threadIdx.x < cgs * rps;
+    const int cg = threadIdx.x % cgs, r0 = threadIdx.x / cgs;
+    float a4[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a4[q] = (float)sc[(cg * 4 + q + 1) * kScal + S_ALPHA];
+    Acc32 acc[4];
+    if (on) {
+        for (int64_t i = (int64_t)blockIdx.x * rps + r0; i < n; i += (int64_t)gridDim.x * rps) {
+            const int64_t e = i * m + cg * 4;
+            float r4[4], q4[4];
+            load_k<float, 4>(rz + e, r4);
+            load_k<float, 4>(qz + e, q4);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (a4[q] != 0.0f) r4[q] = r4[q] - a4[q] * q4[q];
+                acc[q].fma2(r4[q], r4[q]);
+            }
+            store_k<float, 4>(rz + e, r4);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[threadIdx.x * 4 + q] = on ? acc[q].value() : 0.0;
+    __syncthreads();
+    if ((int)threadIdx.x < m) {
+        const int g = threadIdx.x / 4, q = threadIdx.x % 4;
+        double t = 0.0;
+        for (int u = g; u < cgs * rps; u += cgs) t += red[u * 4 + q];
+        part[(int64_t)(threadIdx.x + 1) * pstride + blockIdx.x] = t;
     }
 }
 
@@ -2206,6 +2263,8 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     int *dev_err = flags + 3;
     // the y column's PCG update joins the probe group's step when both use the same factors
     const bool pc_fuse_y = pcy && bjy == bjz && c->pc_fuse_y;
+    // the probe group's plain-CG steps on the vectorised update (x += alpha p in the direction kernel)
+    const bool upd4 = std::is_same<T, float>::value && m % 4 == 0 && m > 0;
     if (pc_async) {
         GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64, false>, pp_smem<128, 64>()));
         GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32, false>, pp_smem<128, 32>()));
@@ -2265,6 +2324,8 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         if (mc > 0) {
             if (pcz && pc_async) GP2S_TRY(launch_pc_probe(mc, fused_y));
             else if (pcz) GP2S_PCZ_WY(PC_UPDATE, mc, fused_y ? 1 : 0);
+            else if (upd4) k_update_z4<<<nbz, 256, 0, c->stream>>>(n, m, (float *)B.rz, (const float *)B.qz, sc,
+                                                                    part, pstride);
             else k_update<T><<<nbz, ut, 0, c->stream>>>(n, m, (T *)B.xz, (T *)B.rz, (const T *)B.pz, (const T *)B.qz,
                                                          (T *)B.xy, (T *)B.ry, (const T *)B.py, (const T *)B.qy, sc,
                                                          part, pstride, nbz);
@@ -2290,7 +2351,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
             const T *zzp = pcz ? (const T *)B.zz : (const T *)B.rz;
             const T *zyp = pcy ? (const T *)B.zy : (const T *)B.ry;
             k_direction<T><<<dgz + dgy, dthreads, 0, c->stream>>>(n, mc, zzp, (T *)B.pz, zyp, (T *)B.py, sc, active,
-                                                                 dgz, (T *)B.xz, (pcz && pc_async) ? 1 : 0);
+                                                                 dgz, (T *)B.xz, ((pcz && pc_async) || (!pcz && upd4)) ? 1 : 0);
             GP2S_LAUNCH(c);
         }
         return GP2S_OK;
