@@ -270,23 +270,8 @@ k_residual64(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = w0; i < n; i += nw) {
-        const int p1 = rowptr[i + 1];
         double s = 0.0;
-        // four independent entries per lane in flight (rows of up to 128 entries in one pass)
-        for (int p = rowptr[i] + lane; p < p1; p += 4 * kWarp) {
-            double v[4], g[4];
-            int cj[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int q = p + u * kWarp;
-                v[u] = q < p1 ? val[q] : 0.0;
-                cj[u] = q < p1 ? col[q] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) g[u] = x[cj[u]];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) s = fma(v[u], g[u], s);
-        }
+        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += kWarp) s = fma(val[p], x[col[p]], s);
         s = warp_sum(s);
         if (lane == 0) out[i] = b[i] - s;
     }
@@ -1445,7 +1430,8 @@ __device__ __forceinline__ void bj_tile_mm(const float *__restrict__ MT, const f
 }
 
 // Fused PCG step on BJ-row blocks.  INIT: x = 0, r = rhs, z = M^{-1} r, p = z.  UPDATE:
-// x += alpha p, r -= alpha q, z = M^{-1} r.  RESTART (a CG column switching to PCG): x and r kept,
+// r -= alpha q, z = M^{-1} r (the probe group's x += alpha p is done by the direction kernel; the
+// y column's here).  RESTART (a CG column switching to PCG): x and r kept,
 // z = M^{-1} r, p = z.  All emit per-CTA partial dots r^T z and r^T r per column.
 // CTAs [0, gz) work on the probe group (n x m), CTAs [gz, gridDim) on the y column.
 // REPLACE (y column only): r = rhs (the true residual), x = 0, z = M^{-1} r; p is kept (a reliable
@@ -1497,16 +1483,12 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
                             const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
                             store_k<float, 4>(xz + e, zero4);   // the right-hand side was written into r
                         } else if (MODE == PC_UPDATE) {
-                            float x4[4], p4[4], q4[4];
-                            load_k<float, 4>(xz + e, x4);
-                            load_k<float, 4>(pz + e, p4);
+                            // r -= alpha q (x += alpha p is left to the direction kernel, which
+                            // reads p anyway)
+                            float q4[4];
                             load_k<float, 4>(qz + e, q4);
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                x4[q] = x4[q] + a4[q] * p4[q];
-                                r4[q] = r4[q] - a4[q] * q4[q];
-                            }
-                            store_k<float, 4>(xz + e, x4);
+                            for (int q = 0; q < 4; ++q) r4[q] = r4[q] - a4[q] * q4[q];
                             store_k<float, 4>(rz + e, r4);
                         }
                     }
@@ -2351,7 +2333,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
             const T *zzp = pcz ? (const T *)B.zz : (const T *)B.rz;
             const T *zyp = pcy ? (const T *)B.zy : (const T *)B.ry;
             k_direction<T><<<dgz + dgy, dthreads, 0, c->stream>>>(n, mc, zzp, (T *)B.pz, zyp, (T *)B.py, sc, active,
-                                                                 dgz, (T *)B.xz, ((pcz && pc_async) || (!pcz && upd4)) ? 1 : 0);
+                                                                 dgz, (T *)B.xz, ((pcz && pc_avail) || (!pcz && upd4)) ? 1 : 0);
             GP2S_LAUNCH(c);
         }
         return GP2S_OK;
