@@ -127,9 +127,9 @@ typedef struct {
     int32_t max_iter;        /* iteration cap per CG solve, default 20000 */
     double tol_inner;        /* relative residual at which an FP32 y solve without reliable updates
                                 stops before an FP64 refinement step (the MIXED y column with the
-                                block-Jacobi preconditioner instead replaces its recursive residual
-                                by the true FP64 residual at every tenfold gain and stops at
-                                tol_refine), default 1e-6 */
+                                block-Jacobi preconditioner and at least 2^18 rows instead replaces
+                                its recursive residual by the true FP64 residual at every gain of
+                                a factor 33 and stops at tol_refine), default 1e-6 */
     double tol_refine;       /* target |y - A a| / |y| of the y solve (FP64 residual), default 1e-8 */
     double tol_probe;        /* relative residual of the probe solves used by the gradient, default 1e-5 */
     uint64_t seed;           /* probe seed, default 0 */

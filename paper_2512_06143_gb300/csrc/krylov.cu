@@ -28,6 +28,7 @@ constexpr int kSpmmWarps = kSpmmThreads / kWarp;
 constexpr int kMaxPartBlocks = 152 * 8;
 constexpr int kRBWorkOffset = 224;   // byte offset of the RB8 SpMM's tile counter in c->counters
 constexpr int kMaxCols = 129;   // y + up to 128 probes
+constexpr int64_t kReliableMinRows = int64_t(1) << 18;   // reliable updates of the y column from here
 
 // ---------------------------------------------------------------------------------------------
 // SplitMix64 Rademacher probes (same definition as the oracle's, written independently):
@@ -2604,9 +2605,14 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
     ru.y_sorted = y_sorted_dev;
     ru.tol_refine = o.tol_refine;
     ru.delta = c->reliable_delta;
+    // Reliable updates pay where iterations are dear: each replacement costs a host synchronisation,
+    // about ten launches and up to one check interval of idle y iterations, which a small problem's
+    // cheap restarted refinement undercuts (the 256-problem batch, n <= 65,536: 21 problems/s with
+    // them against 29 without; at n = 1M and 10M they save 13 % and 10 %).
+    const bool reliable = c->reliable_y && n >= kReliableMinRows;
     if (mixed)
         GP2S_TRY((cg_run<float, float>(c, mm, c->val32.as<float>(), B, b64, tol_first, tol_z, mm > 0 ? ksteps : 0,
-                                       ksteps, rec, o.max_iter, &iy, &iz, &brk, c->reliable_y ? &ru : nullptr)));
+                                       ksteps, rec, o.max_iter, &iy, &iz, &brk, reliable ? &ru : nullptr)));
     else
         GP2S_TRY((cg_run<double, double>(c, mm, c->val64.as<double>(), B, b64, tol_first, tol_z,
                                          mm > 0 ? ksteps : 0, ksteps, rec, o.max_iter, &iy, &iz, &brk)));
