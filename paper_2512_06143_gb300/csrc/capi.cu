@@ -282,6 +282,8 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (pa && std::strcmp(pa, "0") == 0) c->pc_async = false;
     const char *ry = std::getenv("GP2S_RELIABLE_Y");
     if (ry && std::strcmp(ry, "0") == 0) c->reliable_y = false;
+    const char *rm = std::getenv("GP2S_RELIABLE_MIN_ROWS");
+    if (rm && std::atoll(rm) >= 0) c->reliable_min_rows = (int64_t)std::atoll(rm);
     const char *rd = std::getenv("GP2S_RELIABLE_DELTA");
     if (rd && std::atof(rd) > 0.0 && std::atof(rd) < 1.0) c->reliable_delta = std::atof(rd);
     const char *fy = std::getenv("GP2S_PC_FUSE_Y");

@@ -128,6 +128,7 @@ struct gp2s_ctx {
     bool pc_fuse_y = true;          // the y column's PCG update inside the probe kernel
     bool reliable_y = true;         // reliable updates of the y column instead of restarted refinement
     double reliable_delta = 0.03;   // residual replacement at every gain of this factor
+    int64_t reliable_min_rows = int64_t(1) << 18;   // reliable updates of the y column from here
                                     // (GP2S_PC_ASYNC=0: the staged kernel)
     cudaStream_t capture_stream = nullptr;   // private stream the graphs are captured on
     // batched form: worker contexts (own stream and workspace each), created on first use

@@ -28,7 +28,6 @@ constexpr int kSpmmWarps = kSpmmThreads / kWarp;
 constexpr int kMaxPartBlocks = 152 * 8;
 constexpr int kRBWorkOffset = 224;   // byte offset of the RB8 SpMM's tile counter in c->counters
 constexpr int kMaxCols = 129;   // y + up to 128 probes
-constexpr int64_t kReliableMinRows = int64_t(1) << 18;   // reliable updates of the y column from here
 
 // ---------------------------------------------------------------------------------------------
 // SplitMix64 Rademacher probes (same definition as the oracle's, written independently):
@@ -2609,7 +2608,7 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
     // about ten launches and up to one check interval of idle y iterations, which a small problem's
     // cheap restarted refinement undercuts (the 256-problem batch, n <= 65,536: 21 problems/s with
     // them against 29 without; at n = 1M and 10M they save 13 % and 10 %).
-    const bool reliable = c->reliable_y && n >= kReliableMinRows;
+    const bool reliable = c->reliable_y && n >= c->reliable_min_rows;
     if (mixed)
         GP2S_TRY((cg_run<float, float>(c, mm, c->val32.as<float>(), B, b64, tol_first, tol_z, mm > 0 ? ksteps : 0,
                                        ksteps, rec, o.max_iter, &iy, &iz, &brk, reliable ? &ru : nullptr)));

@@ -88,6 +88,18 @@ def test_clusters_3d_20k_gradient_at_random_theta(gp, ctx, t):
     _compare(gp, ctx, f"clusters_3d_20k_t{t}", logdet=gp.LOGDET_SLQ)
 
 
+def test_reliable_updates_of_the_y_column_match_oracle(gp, monkeypatch):
+    """The y column's reliable updates (on by default from 2^18 rows) forced on for the 150k-point
+    clustered case: the solve stops at its true FP64 residual with no restarted refinement step,
+    and log-det, quadratic term, LML and gradient meet the same bars against the oracle."""
+    monkeypatch.setenv("GP2S_RELIABLE_MIN_ROWS", "0")
+    info, err = _compare(gp, gp.Context(0), "clusters_3d_150k_t0")
+    assert info["outer"] == 0
+    monkeypatch.setenv("GP2S_RELIABLE_Y", "0")
+    info0, _ = _compare(gp, gp.Context(0), "clusters_3d_150k_t0")
+    assert info0["outer"] >= 1
+
+
 def test_sphere_4d_150k_default_options_match_oracle(gp, ctx):
     info, err = _compare(gp, ctx, "sphere_4d_150k")
     assert info["spmm_seg_tiles"] > 1
