@@ -271,7 +271,7 @@ k_residual64(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = w0; i < n; i += nw) {
         double s = 0.0;
-        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += kWarp) s = fma(val[p], x[col[p]], s);
+        for (int p = rowptr[i] + lane; p < rowptr[i + 1]; p += kWarp) s = fma(__ldcs(val + p), x[__ldcs(col + p)], s);
         s = warp_sum(s);
         if (lane == 0) out[i] = b[i] - s;
     }
@@ -723,8 +723,8 @@ k_spmv_y(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, co
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int q = p + u * kWarp;
-                v[u] = q < p1 ? val[q] : V(0);
-                cj[u] = q < p1 ? col[q] : 0;
+                v[u] = q < p1 ? __ldcs(val + q) : V(0);
+                cj[u] = q < p1 ? __ldcs(col + q) : 0;
             }
             T g[4];
 #pragma unroll
@@ -990,17 +990,19 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
         Acc32 dz[KH];
         Acc32 dy;
         // the tile's entries are contiguous: stream them in 32-entry batches that never straddle
-        // a block, the next batch's column and values loaded while the current one is consumed;
-        // lanes past the block's last entry stage a zero entry on the block's first row
+        // a block, the next batch's column and values loaded while the current one is consumed
+        // (evict-first: the matrix is read once per launch, the gathered P rows are what L2
+        // should keep; 4.67 -> 4.37 ms per launch at N = 10M); lanes past the block's last entry
+        // stage a zero entry on the block's first row
         int64_t b = bb;
         int e1 = bptr[b + 1];
         int eb = bptr[b];
         int cj_n = (int)(b * kRB);
         float4 v0_n = make_float4(0.f, 0.f, 0.f, 0.f), v1_n = v0_n;
         if (eb + lane < e1) {
-            cj_n = ucol[eb + lane];
-            v0_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2];
-            v1_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2 + 1];
+            cj_n = __ldcs(ucol + eb + lane);
+            v0_n = __ldcs(reinterpret_cast<const float4 *>(uval) + (int64_t)(eb + lane) * 2);
+            v1_n = __ldcs(reinterpret_cast<const float4 *>(uval) + (int64_t)(eb + lane) * 2 + 1);
         }
         // accumulators of row pairs (2p, 2p + 1) for each of the lane's columns: one packed FP32x2
         // FMA per pair (each half rounds exactly like a scalar fmaf)
@@ -1031,9 +1033,9 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
             v0_n = make_float4(0.f, 0.f, 0.f, 0.f);
             v1_n = v0_n;
             if (b < be && eb + lane < e1) {
-                cj_n = ucol[eb + lane];
-                v0_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2];
-                v1_n = reinterpret_cast<const float4 *>(uval)[(int64_t)(eb + lane) * 2 + 1];
+                cj_n = __ldcs(ucol + eb + lane);
+                v0_n = __ldcs(reinterpret_cast<const float4 *>(uval) + (int64_t)(eb + lane) * 2);
+                v1_n = __ldcs(reinterpret_cast<const float4 *>(uval) + (int64_t)(eb + lane) * 2 + 1);
             }
             if (HAS_Y) {
                 const float yj = py[cj];
@@ -1472,7 +1474,7 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
             const int64_t i0 = b * BJ;
             const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
             const float4 *Mg = reinterpret_cast<const float4 *>(Minv32 + b * BJ * BJ);
-            for (int t = threadIdx.x; t < BJ * BJ / 4; t += blockDim.x) reinterpret_cast<float4 *>(MT)[t] = Mg[t];
+            for (int t = threadIdx.x; t < BJ * BJ / 4; t += blockDim.x) reinterpret_cast<float4 *>(MT)[t] = __ldcs(Mg + t);
             if (eth) {
                 for (int i = er0; i < BJ; i += rps) {
                     float r4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1622,7 +1624,7 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
                 const float *Mb = Minv32 + b * BJ * BJ;
                 const float *Rb = R + sub * BJ;
 #pragma unroll 8
-                for (int k = 0; k < BJ; ++k) z = fmaf(Mb[k * BJ + i], Rb[k], z);
+                for (int k = 0; k < BJ; ++k) z = fmaf(__ldcs(Mb + k * BJ + i), Rb[k], z);
                 if (i < nb) {
                     zy[i0 + i] = z;
                     if (SETP) py[i0 + i] = z;
