@@ -282,6 +282,8 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (pa && std::strcmp(pa, "0") == 0) c->pc_async = false;
     const char *ry = std::getenv("GP2S_RELIABLE_Y");
     if (ry && std::strcmp(ry, "0") == 0) c->reliable_y = false;
+    const char *sa = std::getenv("GP2S_SLQ_ASYNC");
+    if (sa && std::strcmp(sa, "0") == 0) c->slq_async = false;
     const char *rm = std::getenv("GP2S_RELIABLE_MIN_ROWS");
     if (rm && std::atoll(rm) >= 0) c->reliable_min_rows = (int64_t)std::atoll(rm);
     const char *rd = std::getenv("GP2S_RELIABLE_DELTA");
@@ -314,6 +316,13 @@ void gp2s_destroy(gp2s_ctx *c)
     for (gp2s_ctx *w : c->workers) gp2s_destroy(w);
     for (cudaStream_t s : c->worker_streams) cudaStreamDestroy(s);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    if (c->side_stream) {
+        cudaStreamSynchronize(c->side_stream);
+        cudaStreamDestroy(c->side_stream);
+    }
+    if (c->slq_ev_rec) cudaEventDestroy(c->slq_ev_rec);
+    if (c->slq_ev_done) cudaEventDestroy(c->slq_ev_done);
+    free_buf(c->slq_work);
     if (c->hbuf.p) cudaFreeHost(c->hbuf.p);
     delete c;
 }

@@ -131,6 +131,14 @@ struct gp2s_ctx {
     int64_t reliable_min_rows = int64_t(1) << 18;   // reliable updates of the y column from here
                                     // (GP2S_PC_ASYNC=0: the staged kernel)
     cudaStream_t capture_stream = nullptr;   // private stream the graphs are captured on
+    // SLQ's tridiagonal quadratures run on a side stream once the probes' k steps are recorded,
+    // beside the rest of the probe solves (slq_start_async); slq_logdet waits for them
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t slq_ev_rec = nullptr, slq_ev_done = nullptr;
+    bool slq_pending = false;
+    bool slq_async = true;
+    int slq_m = 0, slq_k = 0;
+    gp2s::DevBuf slq_work;
     // batched form: worker contexts (own stream and workspace each), created on first use
     std::vector<gp2s_ctx *> workers;
     std::vector<cudaStream_t> worker_streams;
@@ -236,6 +244,11 @@ struct CGResult {
 gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_probes, int m,
                          int ksteps, CGResult *res);
 gp2s_status slq_logdet(gp2s_ctx *c, int m, int ksteps, double *logdet_hat, double *stderr_hat);
+// Start SLQ's quadratures on the side stream from the coefficients recorded so far (every probe
+// column has its k steps or has stopped); the stream order of c->stream is the dependency.
+gp2s_status slq_start_async(gp2s_ctx *c, int m, int ksteps);
+// c->stream waits for a pending SLQ launch (before its inputs are overwritten).
+gp2s_status slq_fence(gp2s_ctx *c);
 // FP64 MINRES on Ah (minres.cu): b (device, sorted order) -> x, until |b - Ah x| <= tol |b|.
 gp2s_status minres_solve(gp2s_ctx *c, const double *b, double *x, double tol, int maxit, int *steps);
 // Multi-RHS (P)CG on caller-supplied columns (no y column, no SLQ records): krylov_columns_buffers

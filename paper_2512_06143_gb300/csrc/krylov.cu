@@ -2393,7 +2393,9 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         } else {
             for (int r = 0; r < len; ++r, ++it) {
                 if (pc_avail && !pcz && mc > 0 && it == kmin_probe) {
-                    // the SLQ steps are recorded: restart the probe columns as PCG from their iterates
+                    // the SLQ steps are recorded: their quadratures go to the side stream, and the
+                    // probe columns restart as PCG from their iterates
+                    if (rec && c->slq_async) GP2S_TRY(slq_start_async(c, m, ksteps));
                     GP2S_PCZ(PC_RESTART, mc);
                     GP2S_LAUNCH(c);
                     k_scal_restart<<<mc, 256, 0, c->stream>>>(part, pstride, pgz, sc, active);
@@ -2533,6 +2535,9 @@ gp2s_status krylov_solve(gp2s_ctx *c, const double *y_sorted_dev, bool with_prob
     double *b64 = c->vec64.as<double>();
     double *xh = b64 + n, *r64 = b64 + 2 * n, *a64 = b64 + 3 * n;
     GP2S_TRY(ensure_host(c, c->hbuf, 4096));
+    // a pending SLQ launch of the previous solve still reads rec and the scalars
+    GP2S_TRY(slq_fence(c));
+    c->slq_pending = false;
     if (mm > 0) GP2S_TRY(ensure(c, c->rec, sizeof(double) * (size_t)mm * ksteps * 2 + 64));
     double *rec = mm > 0 ? c->rec.as<double>() : nullptr;
     if (rec) GP2S_CUDA(c, cudaMemsetAsync(rec, 0, sizeof(double) * (size_t)mm * ksteps * 2, c->stream));

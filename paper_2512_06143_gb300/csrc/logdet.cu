@@ -354,18 +354,72 @@ gp2s_status dot_f64(gp2s_ctx *c, const double *a, const double *b, int64_t n, do
     return reduce_parts(c, c->gpart.as<double>(), nb, out_host);
 }
 
+// SLQ scratch: per probe 3 k doubles of work, the m quadratures, the failure flag, and a snapshot
+// of the CG scalar block (the step counts k_slq reads) taken when the launch is queued.
+static double *slq_layout(gp2s_ctx *c, int m, int ksteps, double **out, int **bad, double **snap)
+{
+    double *work = c->slq_work.as<double>();
+    *out = work + (size_t)m * 3 * ksteps;
+    *bad = reinterpret_cast<int *>(*out + m);
+    *snap = *out + m + 8;
+    return work;
+}
+
+static gp2s_status slq_launch(gp2s_ctx *c, cudaStream_t wait_on, cudaStream_t run_on, int m, int ksteps)
+{
+    GP2S_TRY(ensure(c, c->slq_work, sizeof(double) * ((size_t)m * 3 * ksteps + m + 8 + (size_t)kScal * (m + 1)) + 64));
+    double *out, *snap;
+    int *bad;
+    double *work = slq_layout(c, m, ksteps, &out, &bad, &snap);
+    GP2S_CUDA(c, cudaMemcpyAsync(snap, c->scal.as<double>(), sizeof(double) * kScal * (m + 1), cudaMemcpyDeviceToDevice,
+                                 wait_on));
+    GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), wait_on));
+    if (run_on != wait_on) {
+        GP2S_CUDA(c, cudaEventRecord(c->slq_ev_rec, wait_on));
+        GP2S_CUDA(c, cudaStreamWaitEvent(run_on, c->slq_ev_rec, 0));
+    }
+    const size_t smem = sizeof(double) * 3 * (size_t)ksteps;
+    GP2S_TRY(smem_attr(c, (const void *)k_slq, smem));
+    k_slq<<<m, 32, smem, run_on>>>(c->rec.as<double>(), snap, m, ksteps, work, out, bad);
+    GP2S_LAUNCH(c);
+    return GP2S_OK;
+}
+
+gp2s_status slq_start_async(gp2s_ctx *c, int m, int ksteps)
+{
+    if (!c->side_stream) {
+        GP2S_CUDA(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        GP2S_CUDA(c, cudaEventCreateWithFlags(&c->slq_ev_rec, cudaEventDisableTiming));
+        GP2S_CUDA(c, cudaEventCreateWithFlags(&c->slq_ev_done, cudaEventDisableTiming));
+    }
+    GP2S_TRY(slq_fence(c));
+    GP2S_TRY(slq_launch(c, c->stream, c->side_stream, m, ksteps));
+    GP2S_CUDA(c, cudaEventRecord(c->slq_ev_done, c->side_stream));
+    c->slq_pending = true;
+    c->slq_m = m;
+    c->slq_k = ksteps;
+    return GP2S_OK;
+}
+
+gp2s_status slq_fence(gp2s_ctx *c)
+{
+    if (c->slq_pending) GP2S_CUDA(c, cudaStreamWaitEvent(c->stream, c->slq_ev_done, 0));
+    return GP2S_OK;
+}
+
 gp2s_status slq_logdet(gp2s_ctx *c, int m, int ksteps, double *logdet_hat, double *stderr_hat)
 {
     if (m <= 0 || !c->have_probes) return set_err(c, GP2S_ENOTREADY, "SLQ needs the probe CG run");
-    GP2S_TRY(ensure(c, c->dense, sizeof(double) * ((size_t)m * 3 * ksteps + m + 8)));
-    double *work = c->dense.as<double>();
-    double *out = work + (size_t)m * 3 * ksteps;
-    int *bad = reinterpret_cast<int *>(out + m);
-    GP2S_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-    const size_t smem = sizeof(double) * 3 * (size_t)ksteps;
-    GP2S_TRY(smem_attr(c, (const void *)k_slq, smem));
-    k_slq<<<m, 32, smem, c->stream>>>(c->rec.as<double>(), c->scal.as<double>(), m, ksteps, work, out, bad);
-    GP2S_LAUNCH(c);
+    if (c->slq_pending && c->slq_m == m && c->slq_k == ksteps) {
+        GP2S_TRY(slq_fence(c));   // queued beside the probe solves, from the same recorded steps
+    } else {
+        GP2S_TRY(slq_fence(c));
+        GP2S_TRY(slq_launch(c, c->stream, c->stream, m, ksteps));
+    }
+    c->slq_pending = false;
+    double *out, *snap;
+    int *bad;
+    slq_layout(c, m, ksteps, &out, &bad, &snap);
     std::vector<double> g(m);
     int hbad = 0;
     GP2S_CUDA(c, cudaMemcpyAsync(g.data(), out, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream));
