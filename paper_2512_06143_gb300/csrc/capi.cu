@@ -282,6 +282,8 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     if (pa && std::strcmp(pa, "0") == 0) c->pc_async = false;
     const char *ry = std::getenv("GP2S_RELIABLE_Y");
     if (ry && std::strcmp(ry, "0") == 0) c->reliable_y = false;
+    const char *p64 = std::getenv("GP2S_PC_ASYNC64");
+    if (p64 && std::strcmp(p64, "0") == 0) c->pc_async64 = false;
     const char *sa = std::getenv("GP2S_SLQ_ASYNC");
     if (sa && std::strcmp(sa, "0") == 0) c->slq_async = false;
     const char *rm = std::getenv("GP2S_RELIABLE_MIN_ROWS");

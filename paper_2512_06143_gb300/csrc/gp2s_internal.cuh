@@ -124,6 +124,7 @@ struct gp2s_ctx {
     bool probes_for_grad = false;   // the probe solves feed the Hutchinson gradient
     bool use_graphs = true;         // replay runs of CG iterations as CUDA graphs (GP2S_GRAPHS=0: off)
     bool pc_async = true;           // probe-group PCG step on the bulk-copy pipelined kernel
+    bool pc_async64 = true;         // ... also with 64-row block-Jacobi blocks (two per stage)
     bool spmm_half = false;         // 16 and 32 columns on half-warp entry groups (KH = 1, 2)
     bool pc_fuse_y = true;          // the y column's PCG update inside the probe kernel
     bool reliable_y = true;         // reliable updates of the y column instead of restarted refinement

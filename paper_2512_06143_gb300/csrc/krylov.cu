@@ -1712,17 +1712,20 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 
 // two stages of (M^{-1} block, residual block), the y column's two staged residual blocks and its
 // split products (WY), the two mbarriers
-template <int BJ, int M>
+template <int BJ, int SB, int M>
 size_t pp_smem()
 {
-    return sizeof(float) * (2 * ((size_t)BJ * BJ + (size_t)BJ * M) + 2 * (size_t)BJ + 4 * (size_t)BJ) + 64;
+    return sizeof(float) * (2 * ((size_t)BJ * SB + (size_t)BJ * M) + 2 * (size_t)BJ + 4 * (size_t)BJ) + 64;
 }
 
 // WY: the y column's PCG update rides along on the same staged M^{-1} blocks (when it uses the
 // probes' factors): x_y += alpha_y p_y, r_y -= alpha_y q_y by the producers, z_y = M^{-1} r_y by the
 // consumers (each half of them sums half of the block's columns), partial dots in column 0 of
 // part_rz / part_rr.  This saves the y column's own pass over all of M^{-1} per iteration.
-template <int BJ, int M, bool WY>
+// Stages of BJ = 128 rows; the block-Jacobi blocks are SB = 128 or 64 rows (a stage then holds two
+// consecutive 64 x 64 blocks of M^{-1}, contiguous in memory, and each tile multiplies within its
+// own block).
+template <int BJ, int SB, int M, bool WY>
 __global__ void __launch_bounds__(kPPThreads, 1)
 k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__restrict__ rz,
            const float *__restrict__ qz, float *__restrict__ zz, const double *__restrict__ sc,
@@ -1742,11 +1745,13 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
     constexpr int TR = 8;                      // tile rows per consumer thread
     constexpr int NTILE = (BJ / TR) * CG;      // consumer tiles (<= NT; the rest of the consumers idle)
     static_assert(NF4 % NT == 0 && NT % CG == 0 && NTILE <= NT, "block shape");
+    static_assert(BJ % SB == 0 && SB % TR == 0, "tiles within one block-Jacobi block");
     static_assert(!WY || NT == 2 * BJ, "the y product splits each block's columns over two halves of the consumers");
+    constexpr int MS = BJ * SB;                // floats of M^{-1} per stage (BJ / SB blocks of SB x SB)
     extern __shared__ __align__(128) unsigned char pp_sh[];
     float *stage0 = reinterpret_cast<float *>(pp_sh);
-    float *stage1 = stage0 + BJ * BJ + BJ * M;
-    float *ys = stage1 + BJ * BJ + BJ * M;     // 2 x BJ: the y column's residual blocks
+    float *stage1 = stage0 + MS + BJ * M;
+    float *ys = stage1 + MS + BJ * M;          // 2 x BJ: the y column's residual blocks
     float *yp = ys + 2 * BJ;                   // 2 x 2 x BJ: halves of z_y = M^{-1} r_y
     uint64_t *bar = reinterpret_cast<uint64_t *>(yp + 4 * BJ);
     const int tid = threadIdx.x;
@@ -1757,15 +1762,19 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
     double ydacc = 0.0;                        // the y column's r^T r (producers) or r^T z (consumers)
     const int64_t nmine = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
+    const int64_t nsub = (n + SB - 1) / SB;    // block-Jacobi blocks of the matrix
     auto issue = [&](int64_t k) {
         const int64_t b = blockIdx.x + k * gridDim.x;
         float *st = (k & 1) ? stage1 : stage0;
         const int64_t i0 = b * BJ;
         const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
-        const uint32_t mb = sizeof(float) * BJ * BJ, rb = sizeof(float) * (uint32_t)nb * M;
+        // the stage's blocks of M^{-1} that exist (the matrix's last stage may hold fewer)
+        const int64_t s0 = b * (BJ / SB);
+        const int ns = (int)(nsub - s0 < BJ / SB ? nsub - s0 : BJ / SB);
+        const uint32_t mb = sizeof(float) * SB * SB * (uint32_t)ns, rb = sizeof(float) * (uint32_t)nb * M;
         mbar_expect_tx(&bar[k & 1], mb + rb);
-        bulk_copy_g2s(st, Minv32 + b * BJ * BJ, mb, &bar[k & 1]);
-        bulk_copy_g2s(st + BJ * BJ, rz + i0 * M, rb, &bar[k & 1]);
+        bulk_copy_g2s(st, Minv32 + s0 * SB * SB, mb, &bar[k & 1]);
+        bulk_copy_g2s(st + MS, rz + i0 * M, rb, &bar[k & 1]);
     };
 
     if (tid == 0) {
@@ -1786,7 +1795,7 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
         const float ay = (float)alpha_y;
         bool ok = true;
         for (int64_t k = 0; k < nmine; ++k) {
-            float *R = ((k & 1) ? stage1 : stage0) + BJ * BJ;
+            float *R = ((k & 1) ? stage1 : stage0) + MS;
             const int64_t i0 = (blockIdx.x + k * gridDim.x) * BJ;
             const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
             float4 q4[PER];
@@ -1856,7 +1865,7 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
         const bool has_tile = t < NTILE;
         for (int64_t k = 0; k < nmine; ++k) {
             const float *MT = (k & 1) ? stage1 : stage0;
-            const float *R = MT + BJ * BJ;
+            const float *R = MT + MS;
             const int64_t i0 = (blockIdx.x + k * gridDim.x) * BJ;
             const int nb = (int)(n - i0 < BJ ? n - i0 : BJ);
             asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(k & 1)), "r"(kPPThreads) : "memory");
@@ -1868,11 +1877,16 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
             for (int a = 0; a < TR / 2; ++a)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
+            // the tile's rows lie in block sb of the stage: M^{-1}_sb (SB x SB, symmetric) times
+            // the block's SB residual rows
+            const int sb = i0t / SB;
+            const float *MB = MT + sb * SB * SB + (i0t - sb * SB);
+            const float *RB = R + sb * SB * M + c0;
 #pragma unroll 4
-            for (int kk = 0; kk < BJ; ++kk) {
-                const float4 m0 = *reinterpret_cast<const float4 *>(MT + kk * BJ + i0t);
-                const float4 m1 = *reinterpret_cast<const float4 *>(MT + kk * BJ + i0t + 4);
-                const float4 rv = *reinterpret_cast<const float4 *>(R + kk * M + c0);
+            for (int kk = 0; kk < SB; ++kk) {
+                const float4 m0 = *reinterpret_cast<const float4 *>(MB + kk * SB);
+                const float4 m1 = *reinterpret_cast<const float4 *>(MB + kk * SB + 4);
+                const float4 rv = *reinterpret_cast<const float4 *>(RB + kk * M);
                 const float2 mp[4] = {make_float2(m0.x, m0.y), make_float2(m0.z, m0.w), make_float2(m1.x, m1.y),
                                       make_float2(m1.z, m1.w)};
                 const float ra[4] = {rv.x, rv.y, rv.z, rv.w};
@@ -1902,14 +1916,17 @@ k_pc_probe(int64_t n, int64_t nblk, const float *__restrict__ Minv32, float *__r
             }
             float yri = 0.0f;
             if (WY) {
-                // half h = t / BJ of z_y[i] = sum_kk M^{-1}[kk][i] r_y[kk], kk in [h BJ/2, (h+1) BJ/2)
+                // half h = t / BJ of z_y[i] = sum_kk M^{-1}_sb[kk][i] r_y[kk] over row i's block sb,
+                // kk in [h SB/2, (h+1) SB/2)
                 const int i = t % BJ, h = t / BJ;
-                const float *yrs = ys + (k & 1) * BJ;
+                const int sb = i / SB, il = i - sb * SB;
+                const float *yrs = ys + (k & 1) * BJ + sb * SB;
+                const float *MB = MT + sb * SB * SB + il;
                 float zp = 0.0f;
 #pragma unroll 8
-                for (int kk = h * (BJ / 2); kk < (h + 1) * (BJ / 2); ++kk) zp = fmaf(MT[kk * BJ + i], yrs[kk], zp);
+                for (int kk = h * (SB / 2); kk < (h + 1) * (SB / 2); ++kk) zp = fmaf(MB[kk * SB], yrs[kk], zp);
                 yp[((k & 1) * 2 + h) * BJ + i] = zp;
-                if (t < BJ) yri = yrs[t];
+                if (t < BJ) yri = ys[(k & 1) * BJ + t];
             }
             // every consumer is done with the stage: refill it with block k + 2
             asm volatile("bar.sync 3, %0;" ::"r"(NT) : "memory");
@@ -2238,36 +2255,54 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         if (bjy == 128) GP2S_PCY_BJ(MODE, 128);                                                                     \
         else GP2S_PCY_BJ(MODE, 64);                                                                                 \
     } while (0)
-    // the probe group's UPDATE step on the bulk-copy pipelined kernel (FP32, m = 32 or 64 (the
-    // instantiated widths), 128-row blocks): one CTA per SM, x updated by the direction kernel.  With 64-row blocks the staged
-    // kernel at several CTAs per SM measured faster (sphere_4d at N = 10M: 2.60 against 2.72 s per
-    // evaluation), with 128-row blocks this one (clusters_3d at N = 1M: 1.78 against 1.85 s).
-    const bool pc_async = pc_avail && c->pc_async && (m == 32 || m == 64) && bjz == 128;
-    const int pga = (int)std::min<int64_t>(c->num_sms, nblkz);
+    // the probe group's UPDATE step on the warp-specialised bulk-copy kernel (FP32, m = 32 or 64, the
+    // instantiated widths; 128-row stages holding one 128-row or two 64-row block-Jacobi blocks):
+    // one CTA per SM, x updated by the direction kernel.  Against the staged kernel at several CTAs
+    // per SM: clusters_3d at N = 1M 1.66 against 1.84 s, sphere_4d at N = 10M 1.78 against 1.86 s.
+    const bool pc_async = pc_avail && c->pc_async && (m == 32 || m == 64) &&
+                          (bjz == 128 || (bjz == 64 && c->pc_async64));
+    const int64_t nstage = ceil_div(n, (int64_t)128);   // the bulk-copy kernel's 128-row stages
+    const int pga = (int)std::min<int64_t>(c->num_sms, nstage);
     int *dev_err = flags + 3;
     // the y column's PCG update joins the probe group's step when both use the same factors
     const bool pc_fuse_y = pcy && bjy == bjz && c->pc_fuse_y;
     // the probe group's plain-CG steps on the vectorised update (x += alpha p in the direction kernel)
     const bool upd4 = std::is_same<T, float>::value && m % 4 == 0 && m > 0;
+#define GP2S_PP_ATTR(SB_, M_, WY_) \
+    GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, SB_, M_, WY_>, pp_smem<128, SB_, M_>()))
     if (pc_async) {
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64, false>, pp_smem<128, 64>()));
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32, false>, pp_smem<128, 32>()));
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 64, true>, pp_smem<128, 64>()));
-        GP2S_TRY(smem_attr(c, (const void *)k_pc_probe<128, 32, true>, pp_smem<128, 32>()));
+        if (bjz == 128) {
+            GP2S_PP_ATTR(128, 64, false); GP2S_PP_ATTR(128, 32, false);
+            GP2S_PP_ATTR(128, 64, true); GP2S_PP_ATTR(128, 32, true);
+        } else {
+            GP2S_PP_ATTR(64, 64, false); GP2S_PP_ATTR(64, 32, false);
+            GP2S_PP_ATTR(64, 64, true); GP2S_PP_ATTR(64, 32, true);
+        }
     }
+#undef GP2S_PP_ATTR
     auto launch_pc_probe = [&](int mm, bool wy) -> gp2s_status {
         float *rzp = (float *)B.rz, *zzp = (float *)B.zz;
         const float *qzp = (const float *)B.qz;
-#define GP2S_PP(BJ_, M_, WY_)                                                                                \
-    k_pc_probe<BJ_, M_, WY_><<<pga, kPPThreads, pp_smem<BJ_, M_>(), c->stream>>>(                           \
-        n, nblkz, Minvz, rzp, qzp, zzp, sc, part, part_rr, pstride, dev_err, (float *)B.xy, (float *)B.ry, \
+#define GP2S_PP(SB_, M_, WY_)                                                                                \
+    k_pc_probe<128, SB_, M_, WY_><<<pga, kPPThreads, pp_smem<128, SB_, M_>(), c->stream>>>(                  \
+        n, nstage, Minvz, rzp, qzp, zzp, sc, part, part_rr, pstride, dev_err, (float *)B.xy, (float *)B.ry, \
         (const float *)B.py, (const float *)B.qy, (float *)B.zy)
-        if (mm == 64) {
-            if (wy) GP2S_PP(128, 64, true);
-            else GP2S_PP(128, 64, false);
+        if (bjz == 128) {
+            if (mm == 64) {
+                if (wy) GP2S_PP(128, 64, true);
+                else GP2S_PP(128, 64, false);
+            } else {
+                if (wy) GP2S_PP(128, 32, true);
+                else GP2S_PP(128, 32, false);
+            }
         } else {
-            if (wy) GP2S_PP(128, 32, true);
-            else GP2S_PP(128, 32, false);
+            if (mm == 64) {
+                if (wy) GP2S_PP(64, 64, true);
+                else GP2S_PP(64, 64, false);
+            } else {
+                if (wy) GP2S_PP(64, 32, true);
+                else GP2S_PP(64, 32, false);
+            }
         }
 #undef GP2S_PP
         return GP2S_OK;
