@@ -261,6 +261,8 @@ def run_reference(args):
 
 GOLDEN_DIR = os.path.join(ROOT, "tests", "golden")
 SAMPLE_CASES = {"clusters_3d": ("clusters_3d_150k_t0", 100.0), "sphere_4d": ("sphere_4d_150k", 60.0)}
+# the oracle's run over a whole workload, stored where it could be afforded (5.2 hours on 8 cores)
+FULL_CASES = {("sphere_4d", 10_000_000): "sphere_4d_10m"}
 
 
 def timed_evals(ctx, X, y, hyper, opts, steps, warmup, flush, stream, barrier):
@@ -393,10 +395,11 @@ def measure_workload(gp, ctx, workload, seed, n, steps, warmup, flush, stream, b
 def oracle_errors(gp, ctx, m: dict) -> dict:
     """Part of the oracle leg (after every timed region): each result's error against the FP64
     oracle.  (1) The full-size y solve: |y_i - A_i a| on sampled rows, the rows of A from the
-    oracle's brute force over all points, against |y|.  (2) The log-determinant, quadratic term,
-    LML and gradient on a 150,000-point sample of the same generator against the oracle's results
-    stored in tests/golden (written by tests/golden/make_oracle_large.py, which calls only the
-    oracle), with the bench's own default options."""
+    oracle's brute force over all points, against |y|.  (2) Where the oracle's run over the whole
+    workload is stored (the 10M-point 4-D workload), the log-determinant, quadratic term, LML and
+    gradient of the bench's own evaluation against it.  (3) The same on a 150,000-point sample of
+    the generator.  Stored results live in tests/golden (written by
+    tests/golden/make_oracle_large.py, which calls only the oracle); identical probes."""
     import oracle
     from paper_2512_06143_gb300 import workloads as W
     out = {}
@@ -411,6 +414,23 @@ def oracle_errors(gp, ctx, m: dict) -> dict:
         worst = max(worst, abs(w["y"][r] - float(ov @ a[oc])) / ynorm)
     out["y_residual"] = {"relres_fp64": sinfo["relres"], "max_sampled_row_residual_over_ynorm": worst,
                          "rows": len(rows), "bound": 1e-8}
+    # the workload itself, where the oracle's run over all of its points is stored
+    full = FULL_CASES.get((m["config"]["workload"], int(m["n"])))
+    fpath = os.path.join(GOLDEN_DIR, f"oracle_{full}.json") if full else None
+    if fpath and os.path.exists(fpath):
+        with open(fpath) as f:
+            ref = json.load(f)
+        if np.allclose(W.checksums(w["X"], w["y"]), ref["checksums"], rtol=1e-10, atol=0.0):
+            lml, g, info = ctx.lml_grad(m["X"], m["y"], hyper, m["opts"])
+            gref = np.asarray(ref["grad"])
+            out["full_size"] = {"case": ref["case"], "n": ref["n"], "nnz": int(info["nnz"]), "oracle_nnz": ref["nnz"],
+                                "logdet_rel_err": abs(info["logdet"] - ref["logdet"]) / abs(ref["logdet"]),
+                                "quad_rel_err": abs(info["quad"] - ref["quad"]) / abs(ref["quad"]),
+                                "lml_abs_err": abs(lml - ref["lml"]),
+                                "lml_bar": 0.5e-3 * abs(ref["logdet"]) + 0.5e-7 * abs(ref["quad"]),
+                                "grad_max_err_over_max_abs": float(np.abs(g - gref).max() / np.abs(gref).max()),
+                                "bars": {"logdet": 1e-3, "quad": 1e-7, "grad": 1e-4},
+                                "oracle": f"FP64 CG to {ref['cg_tol']} over all {ref['n']} points, identical probes"}
     case = SAMPLE_CASES.get(m["config"]["workload"])
     if case is None:
         return out

@@ -11,7 +11,9 @@ stored checksums, and runs the GPU with the stored hyperparameters and identical
   * 20,000 points of the same generator at 8 drawn hyperparameter sets (the gradient check at
     random theta);
   * 150,000 points of the 4-D sphere x time x elevation generator (32 probes);
-  * the 10,000,000-point 4-D workload: the y solve's residual on sampled rows of the oracle's A.
+  * the 10,000,000-point 4-D workload itself: log-det, quadratic term, LML and gradient against
+    the oracle's run over all 10M points (its CG to 1e-8), and the y solve's residual on sampled
+    rows of the oracle's A.
 
 Bars (the LML's follows from the other two, since it is a difference of large terms):
   log-determinant 1e-3 relative (identical probes), quadratic term y^T A^{-1} y 1e-7 relative,
@@ -103,6 +105,14 @@ def test_reliable_updates_of_the_y_column_match_oracle(gp, monkeypatch):
 def test_sphere_4d_150k_default_options_match_oracle(gp, ctx):
     info, err = _compare(gp, ctx, "sphere_4d_150k")
     assert info["spmm_seg_tiles"] > 1
+
+
+def test_sphere_4d_10m_full_size_matches_oracle(gp, ctx):
+    """The whole 10M-point evaluation with default options (mixed precision, 32 probes x 100
+    steps, reliable updates of the y column) against the oracle's FP64 run on the same 10M points
+    with identical probes."""
+    info, err = _compare(gp, ctx, "sphere_4d_10m")
+    assert info["n"] == 10_000_000 and info["outer"] == 0
 
 
 def test_solve_sphere_4d_full_size_sampled_residual_rows(gp, ctx):
