@@ -322,7 +322,7 @@ def spmm_roofline(gp, ctx, X, y, hyper, wopts, precision, flush, workload, n, pe
 
 
 def pattern_cached_evals(gp, ctx, X, y, hyper, wopts, precision, steps, flush, stream) -> dict:
-    """The survey's second figure: evaluations where theta changes (bump amplitudes and centers, as
+    """The pattern-cached figure: evaluations where theta changes (bump amplitudes and centers, as
     an MCMC block that leaves r alone would) but X and r do not, so the assembly reuses the
     pattern.  One untimed evaluation sets the pattern, then `steps` timed ones."""
     import torch
