@@ -17,6 +17,9 @@
 #include <cstring>
 #include <type_traits>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "gp2s_internal.cuh"
 
 namespace gp2s {
@@ -696,6 +699,9 @@ struct CGBuffers {
 
 template <int KH, int NG>
 gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts);
+template <int NG>
+gp2s_status launch_rb4(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts, int *err,
+                       bool *done);
 
 // y-only SpMV (the y column after every probe column has stopped, and the refinement solves):
 // one warp per row, lanes over the row's entries, many warps per SM to keep enough independent
@@ -775,7 +781,7 @@ __global__ void k_row_split(const int32_t *__restrict__ rowptr, int64_t n, int n
 
 template <class T, class V>
 gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBuffers &B, double *part,
-                        int pstride, int nb, const int32_t *rsplit, const int *active, int *nparts)
+                        int pstride, int nb, const int32_t *rsplit, const int *active, int *nparts, int *err)
 {
     *nparts = nb;
     const Assembled &A = c->A;
@@ -808,7 +814,17 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
         GP2S_CUDA(c, cudaEventRecord(ev_a, c->stream));
     }
     if (rb_launch<T>(c, m, has_y)) {
-        switch (m) {
+        // 16, 32 and 64 columns take the gather-copy form where the driver can encode its tensor map
+        bool done = false;
+        if (c->spmm_tma && !c->spmm_half) {
+            switch (m) {
+            case 16: GP2S_TRY((launch_rb4<8>(c, B, part, pstride, nb, nparts, err, &done))); break;
+            case 32: GP2S_TRY((launch_rb4<4>(c, B, part, pstride, nb, nparts, err, &done))); break;
+            case 64: GP2S_TRY((launch_rb4<2>(c, B, part, pstride, nb, nparts, err, &done))); break;
+            default: break;
+            }
+        }
+        if (!done) switch (m) {
         // every lane covers KH = 4 columns where the column count allows (groups of 4, 8 or 16
         // lanes per entry); 48 and 96 columns take half-warps with KH = 3 and 6
         case 16:
@@ -951,6 +967,228 @@ struct RBWork {
     unsigned int pad;
 };
 
+// ---------------------------------------------------------------------------------------------
+// mbarrier and bulk-copy helpers.  Every wait is bounded: after about a second without the phase
+// completing the caller sets an error flag that the host turns into GP2S_ETIMEOUT.
+// ---------------------------------------------------------------------------------------------
+constexpr uint32_t kPPMaxSpins = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of bar; false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t spin = 0; spin < kPPMaxSpins; ++spin) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (spin > 32) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Row block bcur of the RB8 SpMM is complete: a butterfly over the warp's NG entry groups (lane
+// masks 16, 8, 4) leaves each group the full sums of 8 / NG rows, which it stores and folds into the
+// tile's dots; the row accumulators go back to zero.
+template <int KH, int NG, bool HAS_Y>
+__device__ __forceinline__ void rb_block_end(float2 (&acc)[kRB / 2][KH], float (&ay)[kRB], Acc32 (&dz)[KH], Acc32 &dy,
+                                             int64_t bcur, int64_t n, const float *__restrict__ py,
+                                             const float *__restrict__ pz, float *__restrict__ qy,
+                                             float *__restrict__ qz, int lane)
+{
+    constexpr int LG = kWarp / NG;
+    constexpr int M = LG * KH;
+    const int gl = lane % LG;
+    const int64_t r0 = bcur * kRB;
+    const int nrows = (int)(n - r0 < kRB ? n - r0 : kRB);
+    const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1;
+    float2 h2[2][KH];   // rows 4 b16 + 2q, 4 b16 + 2q + 1
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int k = 0; k < KH; ++k) {
+            const float2 keep = b16 ? acc[2 + q][k] : acc[q][k];
+            const float2 send = b16 ? acc[q][k] : acc[2 + q][k];
+            float2 got;
+            got.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+            got.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+            h2[q][k] = make_float2(keep.x + got.x, keep.y + got.y);
+        }
+    if constexpr (NG == 2) {
+#pragma unroll
+        for (int rr = 0; rr < kRB / 2; ++rr) {
+            const int r = 4 * b16 + rr;
+            if (r < nrows) {
+                const int64_t i = r0 + r;
+                float qr[KH];
+#pragma unroll
+                for (int k = 0; k < KH; ++k) qr[k] = (rr & 1) ? h2[rr / 2][k].y : h2[rr / 2][k].x;
+                store_k<float, KH>(qz + i * M + gl * KH, qr);
+                float pi[KH];
+                load_k<float, KH>(pz + i * M + gl * KH, pi);
+#pragma unroll
+                for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
+            }
+        }
+    } else {
+        float2 h1[KH];   // rows 4 b16 + 2 b8, + 1
+#pragma unroll
+        for (int k = 0; k < KH; ++k) {
+            const float2 keep = b8 ? h2[1][k] : h2[0][k];
+            const float2 send = b8 ? h2[0][k] : h2[1][k];
+            float2 got;
+            got.x = __shfl_xor_sync(0xffffffffu, send.x, 8);
+            got.y = __shfl_xor_sync(0xffffffffu, send.y, 8);
+            h1[k] = make_float2(keep.x + got.x, keep.y + got.y);
+        }
+        if constexpr (NG == 4) {
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr) {
+                const int r = 4 * b16 + 2 * b8 + rr;
+                if (r < nrows) {
+                    const int64_t i = r0 + r;
+                    float qr[KH];
+#pragma unroll
+                    for (int k = 0; k < KH; ++k) qr[k] = rr ? h1[k].y : h1[k].x;
+                    store_k<float, KH>(qz + i * M + gl * KH, qr);
+                    float pi[KH];
+                    load_k<float, KH>(pz + i * M + gl * KH, pi);
+#pragma unroll
+                    for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
+                }
+            }
+        } else {
+            float qr[KH];   // row 4 b16 + 2 b8 + b4
+#pragma unroll
+            for (int k = 0; k < KH; ++k) {
+                const float keep = b4 ? h1[k].y : h1[k].x;
+                const float send = b4 ? h1[k].x : h1[k].y;
+                qr[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+            }
+            const int r = 4 * b16 + 2 * b8 + b4;
+            if (r < nrows) {
+                const int64_t i = r0 + r;
+                store_k<float, KH>(qz + i * M + gl * KH, qr);
+                float pi[KH];
+                load_k<float, KH>(pz + i * M + gl * KH, pi);
+#pragma unroll
+                for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int rp = 0; rp < kRB / 2; ++rp)
+#pragma unroll
+        for (int k = 0; k < KH; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
+    if (HAS_Y) {
+#pragma unroll
+        for (int r = 0; r < kRB; ++r) {
+            float v = ay[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && r < nrows) {
+                qy[r0 + r] = v;
+                dy.fma2(py[r0 + r], v);
+            }
+            ay[r] = 0.0f;
+        }
+    }
+}
+
+// The tile's dot of each probe column (the groups' rows combined in a fixed order: lane masks 16,
+// then 8, then 4, the lower group first) goes to part directly when every tile is a segment of its
+// own, else to tpart[t], and the segment's last tile sums its tiles in tile order into part.
+template <int KH, int NG, bool HAS_Y>
+__device__ __forceinline__ void rb_tile_end(Acc32 (&dz)[KH], Acc32 &dy, unsigned long long t,
+                                            double *__restrict__ part, int pstride, double *__restrict__ tpart,
+                                            int *__restrict__ seg_cnt, int seg_tiles, int ntiles, int lane)
+{
+    constexpr int LG = kWarp / NG;
+    constexpr int M = LG * KH;
+    const int grp = lane / LG, gl = lane % LG;
+    double dzt[KH];
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+        double v = dz[k].value();
+#pragma unroll
+        for (int o = 16; o >= LG; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = (lane & o) ? w + v : v + w;
+        }
+        dzt[k] = v;
+    }
+    if (seg_tiles == 1) {
+        // every tile is a segment of its own: its partial dots go straight to part
+        if (grp == 0) {
+#pragma unroll
+            for (int k = 0; k < KH; ++k) part[(int64_t)(1 + gl * KH + k) * pstride + (int64_t)t] = dzt[k];
+        }
+        if (lane == 0) part[(int64_t)t] = HAS_Y ? dy.value() : 0.0;
+        return;
+    }
+    // the tile's partial dots, then the segment count; the segment's last tile reduces it
+    double *tp = tpart + (int64_t)t * (M + 1);
+    if (grp == 0) {
+#pragma unroll
+        for (int k = 0; k < KH; ++k) tp[1 + gl * KH + k] = dzt[k];
+    }
+    if (lane == 0) tp[0] = HAS_Y ? dy.value() : 0.0;
+    __threadfence();
+    __syncwarp();
+    const int sg = (int)(t / (unsigned long long)seg_tiles);
+    const int nseg = (ntiles + seg_tiles - 1) / seg_tiles;
+    const int need = sg == nseg - 1 ? ntiles - sg * seg_tiles : seg_tiles;
+    int last = 0;
+    if (lane == 0) last = atomicAdd(&seg_cnt[sg], 1) == need - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+        __threadfence();
+        const double *q = tpart + (int64_t)sg * seg_tiles * (M + 1);
+        // column cc = lane, lane + 32, ...: the segment's tiles in tile order
+        for (int cc = lane; cc < M; cc += kWarp) {
+            double sz = 0.0;
+#pragma unroll 4
+            for (int i = 0; i < need; ++i) sz += __ldcg(q + (int64_t)i * (M + 1) + 1 + cc);
+            part[(int64_t)(1 + cc) * pstride + sg] = sz;
+        }
+        if (lane == 0) {
+            double sy = 0.0;
+            for (int i = 0; i < need; ++i) sy += __ldcg(q + (int64_t)i * (M + 1));
+            part[sg] = sy;
+            seg_cnt[sg] = 0;
+        }
+    }
+}
+
 template <int KH, int NG, bool HAS_Y>
 __global__ void __launch_bounds__(RBCfg<KH>::threads, 1)
 k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, const float *__restrict__ uval,
@@ -1075,165 +1313,255 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
                 }
             }
             __syncwarp();
-            if (block_end) {
-                // row block bcur is complete: a butterfly over the groups (lane masks 16, 8, 4)
-                // leaves each group the full sums of 8 / NG rows, which it stores and folds into
-                // the tile's dots
-                const int64_t r0 = bcur * kRB;
-                const int nrows = (int)(n - r0 < kRB ? n - r0 : kRB);
-                const int b16 = (lane >> 4) & 1, b8 = (lane >> 3) & 1, b4 = (lane >> 2) & 1;
-                float2 h2[2][KH];   // rows 4 b16 + 2q, 4 b16 + 2q + 1
-#pragma unroll
-                for (int q = 0; q < 2; ++q)
-#pragma unroll
-                    for (int k = 0; k < KH; ++k) {
-                        const float2 keep = b16 ? acc[2 + q][k] : acc[q][k];
-                        const float2 send = b16 ? acc[q][k] : acc[2 + q][k];
-                        float2 got;
-                        got.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
-                        got.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
-                        h2[q][k] = make_float2(keep.x + got.x, keep.y + got.y);
-                    }
-                if constexpr (NG == 2) {
-#pragma unroll
-                    for (int rr = 0; rr < kRB / 2; ++rr) {
-                        const int r = 4 * b16 + rr;
-                        if (r < nrows) {
-                            const int64_t i = r0 + r;
-                            float qr[KH];
-#pragma unroll
-                            for (int k = 0; k < KH; ++k) qr[k] = (rr & 1) ? h2[rr / 2][k].y : h2[rr / 2][k].x;
-                            store_k<float, KH>(qz + i * M + gl * KH, qr);
-                            float pi[KH];
-                            load_k<float, KH>(pz + i * M + gl * KH, pi);
-#pragma unroll
-                            for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
-                        }
-                    }
-                } else {
-                    float2 h1[KH];   // rows 4 b16 + 2 b8, + 1
-#pragma unroll
-                    for (int k = 0; k < KH; ++k) {
-                        const float2 keep = b8 ? h2[1][k] : h2[0][k];
-                        const float2 send = b8 ? h2[0][k] : h2[1][k];
-                        float2 got;
-                        got.x = __shfl_xor_sync(0xffffffffu, send.x, 8);
-                        got.y = __shfl_xor_sync(0xffffffffu, send.y, 8);
-                        h1[k] = make_float2(keep.x + got.x, keep.y + got.y);
-                    }
-                    if constexpr (NG == 4) {
-#pragma unroll
-                        for (int rr = 0; rr < 2; ++rr) {
-                            const int r = 4 * b16 + 2 * b8 + rr;
-                            if (r < nrows) {
-                                const int64_t i = r0 + r;
-                                float qr[KH];
-#pragma unroll
-                                for (int k = 0; k < KH; ++k) qr[k] = rr ? h1[k].y : h1[k].x;
-                                store_k<float, KH>(qz + i * M + gl * KH, qr);
-                                float pi[KH];
-                                load_k<float, KH>(pz + i * M + gl * KH, pi);
-#pragma unroll
-                                for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
-                            }
-                        }
-                    } else {
-                        float qr[KH];   // row 4 b16 + 2 b8 + b4
-#pragma unroll
-                        for (int k = 0; k < KH; ++k) {
-                            const float keep = b4 ? h1[k].y : h1[k].x;
-                            const float send = b4 ? h1[k].x : h1[k].y;
-                            qr[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-                        }
-                        const int r = 4 * b16 + 2 * b8 + b4;
-                        if (r < nrows) {
-                            const int64_t i = r0 + r;
-                            store_k<float, KH>(qz + i * M + gl * KH, qr);
-                            float pi[KH];
-                            load_k<float, KH>(pz + i * M + gl * KH, pi);
-#pragma unroll
-                            for (int k = 0; k < KH; ++k) dz[k].fma2(pi[k], qr[k]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int rp = 0; rp < kRB / 2; ++rp)
-#pragma unroll
-                    for (int k = 0; k < KH; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
-                if (HAS_Y) {
-#pragma unroll
-                    for (int r = 0; r < kRB; ++r) {
-                        float v = ay[r];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                        if (lane == 0 && r < nrows) {
-                            qy[r0 + r] = v;
-                            dy.fma2(py[r0 + r], v);
-                        }
-                        ay[r] = 0.0f;
-                    }
-                }
-            }
+            if (block_end) rb_block_end<KH, NG, HAS_Y>(acc, ay, dz, dy, bcur, n, py, pz, qy, qz, lane);
         }
-        // the tile's dot of each probe column: the groups' rows combined in a fixed order (lane
-        // masks 16, then 8, then 4, the lower group first)
-        double dzt[KH];
-#pragma unroll
-        for (int k = 0; k < KH; ++k) {
-            double v = dz[k].value();
-#pragma unroll
-            for (int o = 16; o >= LG; o >>= 1) {
-                const double w = __shfl_xor_sync(0xffffffffu, v, o);
-                v = (lane & o) ? w + v : v + w;
-            }
-            dzt[k] = v;
-        }
-        if (seg_tiles == 1) {
-            // every tile is a segment of its own: its partial dots go straight to part
-            if (grp == 0) {
-#pragma unroll
-                for (int k = 0; k < KH; ++k) part[(int64_t)(1 + gl * KH + k) * pstride + (int64_t)t] = dzt[k];
-            }
-            if (lane == 0) part[(int64_t)t] = HAS_Y ? dy.value() : 0.0;
-            t = __shfl_sync(0xffffffffu, tn, 0);
-            continue;
-        }
-        // the tile's partial dots, then the segment count; the segment's last tile reduces it
-        double *tp = tpart + (int64_t)t * (M + 1);
-        if (grp == 0) {
-#pragma unroll
-            for (int k = 0; k < KH; ++k) tp[1 + gl * KH + k] = dzt[k];
-        }
-        if (lane == 0) tp[0] = HAS_Y ? dy.value() : 0.0;
-        __threadfence();
-        __syncwarp();
-        const int sg = (int)(t / (unsigned long long)seg_tiles);
-        const int nseg = (ntiles + seg_tiles - 1) / seg_tiles;
-        const int need = sg == nseg - 1 ? ntiles - sg * seg_tiles : seg_tiles;
-        int last = 0;
-        if (lane == 0) last = atomicAdd(&seg_cnt[sg], 1) == need - 1;
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-            __threadfence();
-            const double *q = tpart + (int64_t)sg * seg_tiles * (M + 1);
-            // column cc = lane, lane + 32, ...: the segment's tiles in tile order
-            for (int cc = lane; cc < M; cc += kWarp) {
-                double sz = 0.0;
-#pragma unroll 4
-                for (int i = 0; i < need; ++i) sz += __ldcg(q + (int64_t)i * (M + 1) + 1 + cc);
-                part[(int64_t)(1 + cc) * pstride + sg] = sz;
-            }
-            if (lane == 0) {
-                double sy = 0.0;
-                for (int i = 0; i < need; ++i) sy += __ldcg(q + (int64_t)i * (M + 1));
-                part[sg] = sy;
-                seg_cnt[sg] = 0;
-            }
-        }
+        rb_tile_end<KH, NG, HAS_Y>(dz, dy, t, part, pstride, tpart, seg_cnt, seg_tiles, ntiles, lane);
         t = __shfl_sync(0xffffffffu, tn, 0);
     }
     // every warp of this CTA has made its last (failed) grab: count the CTA out, and let the last
     // one reset the counter for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(&work->done, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&work->next, 0ull);
+            atomicExch(&work->done, 0u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// RB8 SpMM with the gathered probe rows brought in by the tensor-memory accelerator.  Row blocks,
+// tiles, entry groups, the order of every FMA and the reductions are those of k_spmm_rb, so the
+// results are the same; what changes is where a gathered row comes from.  A warp's 32-entry batch
+// of P rows is fetched by eight cp.async.bulk.tensor tile::gather4 copies (four rows each, issued
+// by lanes 0, 4, ..., 28) into one of the warp's two shared-memory slots while the previous batch
+// is multiplied, and the lanes read their KH columns of each row from shared memory.  The
+// register-gather form keeps at most eight rows per entry group in flight and waits for them at
+// every run; here a whole batch is in flight during the product of another, in no registers.  The
+// matrix stream runs two batches ahead in registers, so the row indices of a batch are at hand
+// when its gathers are issued.  Every wait on a slot's mbarrier is bounded: a warp whose copies do
+// not land sets err, waits (bounded) for its copies in flight and stops.
+// ---------------------------------------------------------------------------------------------
+template <int NG> struct RB4Cfg {
+    static constexpr int KH = 4;
+    static constexpr int M = kWarp / NG * KH;                      // 64, 32 or 16 probe columns
+    static constexpr uint32_t slot = kWarp * M * sizeof(float);   // one batch of gathered rows
+    static constexpr int warps = 12;                              // 168 registers a thread; two slots a warp
+    static constexpr int threads = warps * kWarp;
+    static constexpr size_t smem =
+        128 + (size_t)warps * (2 * slot + 2 * kWarp * sizeof(float4) + 2 * sizeof(uint64_t));
+};
+
+// Four rows r0..r3, columns x .. x + box - 1 of the tensor map's 2-D tensor, to dst (four boxes
+// back to back); completion is counted in bytes on bar.
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *tm, int x, int r0, int r1, int r2, int r3,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// One 32-entry batch of a row block: the lane's entry (column, 8 values) and where the batch sits.
+struct RB4Batch {
+    int cj;
+    float4 v0, v1;
+    int cnt;                   // entries of the batch (the rest are zero entries on the block's first row)
+    int b;                     // row block
+    int t;                     // tile
+    bool valid, bend, tend;    // a batch at all / the block's last batch / the tile's last batch
+};
+
+template <int NG, bool HAS_Y>
+__global__ void __launch_bounds__(RB4Cfg<NG>::threads, 1)
+k_spmm_rb4(const __grid_constant__ CUtensorMap tmz, const int32_t *__restrict__ bptr,
+           const int32_t *__restrict__ ucol, const float *__restrict__ uval, int64_t n, const float *__restrict__ py,
+           const float *__restrict__ pz, float *__restrict__ qy, float *__restrict__ qz, double *__restrict__ part,
+           int pstride, RBWork *__restrict__ work, int tile_blocks, int ntiles, double *__restrict__ tpart,
+           int *__restrict__ seg_cnt, int seg_tiles, int *__restrict__ err)
+{
+    using C = RB4Cfg<NG>;
+    constexpr int KH = C::KH, M = C::M, W = C::warps, LG = kWarp / NG;
+    extern __shared__ __align__(16) unsigned char rb4_sh[];
+    unsigned char *base = rb4_sh + ((128u - (smem_addr(rb4_sh) & 127u)) & 127u);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int grp = lane / LG, gl = lane % LG;
+    float *ring = reinterpret_cast<float *>(base + (size_t)wid * 2 * C::slot);   // this warp's two slots
+    float4 *s_val = reinterpret_cast<float4 *>(base + (size_t)W * 2 * C::slot) + wid * 2 * kWarp;
+    uint64_t *bar =
+        reinterpret_cast<uint64_t *>(base + (size_t)W * 2 * C::slot + (size_t)W * 2 * kWarp * sizeof(float4)) +
+        wid * 2;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int64_t nblk = (n + kRB - 1) / kRB;
+
+    // The cursor (warp-uniform): the next batch to read from the matrix stream.  The tile after the
+    // cursor's is taken from the counter on entering a tile, and the end of the block after the
+    // cursor's is read on entering a block, so that neither load is waited for at once.
+    unsigned long long ct, ctn = 0;
+    int64_t cb = 0, cbe = 0;
+    int ceb = 0, ce1 = 0, ce2 = 0;
+    bool cval;
+    auto grab = [&]() {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(&work->next, 1ull);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    auto enter = [&]() {
+        ctn = grab();
+        cb = (int64_t)ct * tile_blocks;
+        cbe = cb + tile_blocks < nblk ? cb + tile_blocks : nblk;
+        ceb = bptr[cb];
+        ce1 = bptr[cb + 1];
+        ce2 = cb + 1 < cbe ? bptr[cb + 2] : 0;
+    };
+    auto advance = [&]() {
+        ceb += kWarp;
+        if (ceb >= ce1) {
+            ++cb;
+            if (cb < cbe) {
+                ceb = ce1;
+                ce1 = ce2;
+                ce2 = cb + 1 < cbe ? bptr[cb + 2] : 0;
+            } else {
+                ct = ctn;
+                cval = ct < (unsigned long long)ntiles;
+                if (cval) enter();
+            }
+        }
+    };
+    // the batch at the cursor, then the cursor moves on; lanes past the block's last entry take a
+    // zero entry on the block's first row (evict-first loads: the matrix is read once per launch)
+    auto take = [&]() {
+        RB4Batch q;
+        q.valid = cval;
+        q.cj = 0;
+        q.v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        q.v1 = q.v0;
+        q.cnt = 0;
+        q.b = 0;
+        q.t = 0;
+        q.bend = q.tend = false;
+        if (!cval) return q;
+        q.cj = (int)(cb * kRB);
+        if (ceb + lane < ce1) {
+            q.cj = __ldcs(ucol + ceb + lane);
+            q.v0 = __ldcs(reinterpret_cast<const float4 *>(uval) + (int64_t)(ceb + lane) * 2);
+            q.v1 = __ldcs(reinterpret_cast<const float4 *>(uval) + (int64_t)(ceb + lane) * 2 + 1);
+        }
+        q.cnt = min(kWarp, ce1 - ceb);
+        q.b = (int)cb;
+        q.t = (int)ct;
+        q.bend = ceb + kWarp >= ce1;
+        q.tend = q.bend && cb + 1 >= cbe;
+        advance();
+        return q;
+    };
+    // the gathers of a batch's 32 rows into slot s
+    auto issue = [&](const RB4Batch &q, int s) {
+        const int r1 = __shfl_down_sync(0xffffffffu, q.cj, 1);
+        const int r2 = __shfl_down_sync(0xffffffffu, q.cj, 2);
+        const int r3 = __shfl_down_sync(0xffffffffu, q.cj, 3);
+        if (lane == 0) mbar_expect_tx(&bar[s], C::slot);
+        __syncwarp();
+        if ((lane & 3) == 0) tma_gather4(ring + (size_t)s * kWarp * M + lane * M, &tmz, 0, q.cj, r1, r2, r3, &bar[s]);
+    };
+
+    ct = grab();
+    cval = ct < (unsigned long long)ntiles;
+    if (cval) enter();
+    RB4Batch cur = take();
+    RB4Batch nxt = take();
+    float yj = 0.0f;
+    if (cur.valid) {
+        issue(cur, 0);
+        if (HAS_Y) yj = py[cur.cj];
+    }
+    Acc32 dz[KH];
+    Acc32 dy;
+    float2 acc[kRB / 2][KH];
+    float ay[kRB];
+#pragma unroll
+    for (int r = 0; r < kRB; ++r) ay[r] = 0.0f;
+#pragma unroll
+    for (int rp = 0; rp < kRB / 2; ++rp)
+#pragma unroll
+        for (int k = 0; k < KH; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
+    uint32_t k = 0;
+    bool failed = false;
+    while (cur.valid) {
+        // batch k + 1's gathers go out (its rows were read an iteration ago) and its y values are
+        // fetched; batch k + 2 is read from the matrix stream
+        float yj_n = 0.0f;
+        if (nxt.valid) {
+            issue(nxt, (k + 1) & 1);
+            if (HAS_Y) yj_n = py[nxt.cj];
+        }
+        const RB4Batch nn = take();
+        if (HAS_Y) {
+            ay[0] = fmaf(cur.v0.x, yj, ay[0]); ay[1] = fmaf(cur.v0.y, yj, ay[1]);
+            ay[2] = fmaf(cur.v0.z, yj, ay[2]); ay[3] = fmaf(cur.v0.w, yj, ay[3]);
+            ay[4] = fmaf(cur.v1.x, yj, ay[4]); ay[5] = fmaf(cur.v1.y, yj, ay[5]);
+            ay[6] = fmaf(cur.v1.z, yj, ay[6]); ay[7] = fmaf(cur.v1.w, yj, ay[7]);
+        }
+        s_val[lane * 2] = cur.v0;
+        s_val[lane * 2 + 1] = cur.v1;
+        __syncwarp();
+        const int s = (int)(k & 1);
+        if (!mbar_wait_bounded(&bar[s], (k >> 1) & 1)) {
+            failed = true;
+            break;
+        }
+        // group g takes entries NG u + g, u < ceil(cnt / NG), in order (the staged entries past cnt
+        // are zeros on a valid row)
+        const float *rs = ring + (size_t)s * kWarp * M + gl * KH;
+        const int nrun = (cur.cnt + NG - 1) / NG;
+#pragma unroll 4
+        for (int u = 0; u < nrun; ++u) {
+            const int e = NG * u + grp;
+            const float4 p4 = *reinterpret_cast<const float4 *>(rs + e * M);
+            const float4 a0 = s_val[2 * e], a1 = s_val[2 * e + 1];
+            const float2 vp[kRB / 2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                                        make_float2(a1.z, a1.w)};
+            const float pv[KH] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+            for (int kk = 0; kk < KH; ++kk) {
+                const float2 pk = make_float2(pv[kk], pv[kk]);
+#pragma unroll
+                for (int rp = 0; rp < kRB / 2; ++rp) acc[rp][kk] = __ffma2_rn(vp[rp], pk, acc[rp][kk]);
+            }
+        }
+        // the slot's reads are ordered before the copies that will refill it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (cur.bend) rb_block_end<KH, NG, HAS_Y>(acc, ay, dz, dy, (int64_t)cur.b, n, py, pz, qy, qz, lane);
+        if (cur.tend) {
+            rb_tile_end<KH, NG, HAS_Y>(dz, dy, (unsigned long long)cur.t, part, pstride, tpart, seg_cnt, seg_tiles, ntiles, lane);
+#pragma unroll
+            for (int kk = 0; kk < KH; ++kk) dz[kk] = Acc32();
+            dy = Acc32();
+        }
+        cur = nxt;
+        nxt = nn;
+        yj = yj_n;
+        ++k;
+    }
+    if (failed) {
+        if (lane == 0) atomicExch(err, 1);
+        // the copies this warp still has in flight must land before the CTA's shared memory goes
+        mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1);
+        if (nxt.valid) mbar_wait_bounded(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1);
+    }
+    // every warp of this CTA has made its last grab: count the CTA out, and let the last one reset
+    // the counter for the next launch
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -1295,6 +1623,56 @@ gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride
     GP2S_LAUNCH(c);
     *nparts = tl.nseg;
     c->spmm_seg_tiles = std::max(c->spmm_seg_tiles, tl.seg_tiles);
+    return GP2S_OK;
+}
+
+// The tensor map of the row-major n x M FP32 probe block for the gather copies (one box = one row);
+// false when the driver has no encoder or the block does not fit the map's limits.
+static bool rb4_map(CUtensorMap *tm, const float *p, int64_t n, int M)
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    if (!encode || n <= 0 || n > INT_MAX || (reinterpret_cast<uintptr_t>(p) & 15u) != 0) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)M * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)M, 1u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(p), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The gather-copy form of the RB8 SpMM (M = 16, 32, 64); *done = false when it cannot run here
+// (no tensor-map encoder), and the register-gather form takes the launch.
+template <int NG>
+gp2s_status launch_rb4(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts, int *err,
+                       bool *done)
+{
+    using C = RB4Cfg<NG>;
+    *done = false;
+    CUtensorMap tm;
+    if (!err || !rb4_map(&tm, (const float *)B.pz, c->A.n, C::M)) return GP2S_OK;
+    auto kern = k_spmm_rb4<NG, true>;
+    GP2S_TRY(smem_attr(c, (const void *)kern, C::smem));
+    const RBTiles tl = rb_tiles(ceil_div(c->A.n, kRB), nb);
+    GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (C::M + 1)));
+    RBWork *work = reinterpret_cast<RBWork *>(c->counters.as<char>() + kRBWorkOffset);
+    kern<<<tl.ctas, C::threads, C::smem, c->stream>>>(tm, c->rb_ptr.as<int32_t>(), c->rb_col.as<int32_t>(),
+                                                     c->rb_val.as<float>(), c->A.n, (const float *)B.py,
+                                                     (const float *)B.pz, (float *)B.qy, (float *)B.qz, part,
+                                                     pstride, work, tl.tile_blocks, tl.ntiles,
+                                                     c->rb_tpart.as<double>(), c->rb_seg.as<int>(), tl.seg_tiles, err);
+    GP2S_LAUNCH(c);
+    *nparts = tl.nseg;
+    c->spmm_seg_tiles = std::max(c->spmm_seg_tiles, tl.seg_tiles);
+    *done = true;
     return GP2S_OK;
 }
 
@@ -1665,50 +2043,6 @@ k_pc_step(int64_t n, int m, int64_t nblk, int gz, const float *__restrict__ Minv
 // about a second without the copy completing the kernel sets err and returns.
 // ---------------------------------------------------------------------------------------------
 constexpr int kPPThreads = 512;
-constexpr uint32_t kPPMaxSpins = 1u << 24;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for phase `parity` of bar; false when it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    for (uint32_t spin = 0; spin < kPPMaxSpins; ++spin) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (spin > 32) __nanosleep(64);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
 
 // two stages of (M^{-1} block, residual block), the y column's two staged residual blocks and its
 // split products (WY), the two mbarriers
@@ -2335,7 +2669,7 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
     auto one_iter = [&]() -> gp2s_status {
         const int kc = 1 + mc;
         int np = nb;
-        GP2S_TRY((launch_spmm<T, V>(c, mc, true, val, B, part, pstride, nb, rsplit, active, &np)));
+        GP2S_TRY((launch_spmm<T, V>(c, mc, true, val, B, part, pstride, nb, rsplit, active, &np, dev_err)));
         k_scal_alpha<<<kc, 256, 0, c->stream>>>(part, pstride, np, sc, active, flags, rec, ksteps, lucky);
         GP2S_LAUNCH(c);
         GP2S_CUDA(c, cudaMemsetAsync(flags + 1, 0, sizeof(int) * 2, c->stream));
@@ -2444,7 +2778,14 @@ gp2s_status cg_run(gp2s_ctx *c, int m, const V *val, const CGBuffers &B, const d
         if (rel) GP2S_CUDA(c, cudaMemcpyAsync(hcount + 4, active, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
         GP2S_TRY(flush_profile(c));
-        if (hcount[3]) return set_err(c, GP2S_ETIMEOUT, "a block-Jacobi stage copy did not complete (bounded wait gave up)");
+        if (hcount[3]) {
+            // a warp that gave up left its tiles undone: clear the SpMM's counters for the next solve
+            GP2S_CUDA(c, cudaMemsetAsync(c->counters.as<char>() + kRBWorkOffset, 0, sizeof(RBWork), c->stream));
+            if (c->rb_seg.p) GP2S_CUDA(c, cudaMemsetAsync(c->rb_seg.p, 0, sizeof(int) * kMaxPartBlocks, c->stream));
+            GP2S_CUDA(c, cudaStreamSynchronize(c->stream));
+            return set_err(c, GP2S_ETIMEOUT, "a bulk copy (block-Jacobi stage or SpMM row gather) did not complete "
+                                             "(bounded wait gave up)");
+        }
         bool y_back = false;
         if (rel && !rel->done && hcount[4] == 0 && !hcount[0]) {
             GP2S_TRY(replace_y());
