@@ -295,7 +295,7 @@ gp2s_status gp2s_create(gp2s_ctx **ctx, int device, void *cuda_stream)
     const char *sh = std::getenv("GP2S_SPMM_HALF");
     if (sh && std::strcmp(sh, "1") == 0) c->spmm_half = true;
     const char *st = std::getenv("GP2S_SPMM_TMA");
-    if (st) c->spmm_tma = std::strcmp(st, "1") == 0;
+    if (st) c->spmm_tma = std::atoi(st);
     *ctx = c;
     return GP2S_OK;
 }

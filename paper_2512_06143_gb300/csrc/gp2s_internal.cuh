@@ -126,7 +126,7 @@ struct gp2s_ctx {
     bool pc_async = true;           // probe-group PCG step on the bulk-copy pipelined kernel
     bool pc_async64 = true;         // ... also with 64-row block-Jacobi blocks (two per stage)
     bool spmm_half = false;         // 16 and 32 columns on half-warp entry groups (KH = 1, 2)
-    bool spmm_tma = false;          // 16, 32, 64 columns: gathered rows by tensor-map gather copies
+    int spmm_tma = 0;               // 16, 32, 64 columns: rows per 32 gathered by tensor copies (0: none)
     bool pc_fuse_y = true;          // the y column's PCG update inside the probe kernel
     bool reliable_y = true;         // reliable updates of the y column instead of restarted refinement
     double reliable_delta = 0.03;   // residual replacement at every gain of this factor

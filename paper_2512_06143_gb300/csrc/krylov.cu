@@ -700,8 +700,8 @@ struct CGBuffers {
 template <int KH, int NG>
 gp2s_status launch_rb(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts);
 template <int NG>
-gp2s_status launch_rb4(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts, int *err,
-                       bool *done);
+gp2s_status launch_rb4_et(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts, int *err,
+                          int et, bool *done);
 
 // y-only SpMV (the y column after every probe column has stopped, and the refinement solves):
 // one warp per row, lanes over the row's entries, many warps per SM to keep enough independent
@@ -814,13 +814,14 @@ gp2s_status launch_spmm(gp2s_ctx *c, int m, bool has_y, const V *val, const CGBu
         GP2S_CUDA(c, cudaEventRecord(ev_a, c->stream));
     }
     if (rb_launch<T>(c, m, has_y)) {
-        // 16, 32 and 64 columns take the gather-copy form where the driver can encode its tensor map
+        // 16, 32 and 64 columns can take the gather-copy form (ET copied rows per 32-entry batch)
         bool done = false;
-        if (c->spmm_tma && !c->spmm_half) {
+        if (c->spmm_tma > 0 && !c->spmm_half) {
+            const int et = c->spmm_tma;
             switch (m) {
-            case 16: GP2S_TRY((launch_rb4<8>(c, B, part, pstride, nb, nparts, err, &done))); break;
-            case 32: GP2S_TRY((launch_rb4<4>(c, B, part, pstride, nb, nparts, err, &done))); break;
-            case 64: GP2S_TRY((launch_rb4<2>(c, B, part, pstride, nb, nparts, err, &done))); break;
+            case 16: GP2S_TRY((launch_rb4_et<8>(c, B, part, pstride, nb, nparts, err, et, &done))); break;
+            case 32: GP2S_TRY((launch_rb4_et<4>(c, B, part, pstride, nb, nparts, err, et, &done))); break;
+            case 64: GP2S_TRY((launch_rb4_et<2>(c, B, part, pstride, nb, nparts, err, et, &done))); break;
             default: break;
             }
         }
@@ -1332,26 +1333,31 @@ k_spmm_rb(const int32_t *__restrict__ bptr, const int32_t *__restrict__ ucol, co
 }
 
 // ---------------------------------------------------------------------------------------------
-// RB8 SpMM with the gathered probe rows brought in by the tensor-memory accelerator.  Row blocks,
-// tiles, entry groups, the order of every FMA and the reductions are those of k_spmm_rb, so the
-// results are the same; what changes is where a gathered row comes from.  A warp's 32-entry batch
-// of P rows is fetched by eight cp.async.bulk.tensor tile::gather4 copies (four rows each, issued
-// by lanes 0, 4, ..., 28) into one of the warp's two shared-memory slots while the previous batch
-// is multiplied, and the lanes read their KH columns of each row from shared memory.  The
-// register-gather form keeps at most eight rows per entry group in flight and waits for them at
-// every run; here a whole batch is in flight during the product of another, in no registers.  The
-// matrix stream runs two batches ahead in registers, so the row indices of a batch are at hand
-// when its gathers are issued.  Every wait on a slot's mbarrier is bounded: a warp whose copies do
-// not land sets err, waits (bounded) for its copies in flight and stops.
+// RB8 SpMM with part of the gathered probe rows brought in by the tensor-memory accelerator.  Row
+// blocks, tiles, entry groups, the order of every FMA and the reductions are those of k_spmm_rb,
+// so the results are the same; what changes is where a gathered row comes from.  Of a warp's
+// 32-entry batch, the first ET rows are fetched by tile::gather4 tensor copies (four rows each,
+// issued by lanes 0, 4, ..., ET - 4) into one of the warp's two shared-memory slots during the
+// previous batch; the other rows are gathered into registers at the start of the batch and are
+// in flight while the copied rows are multiplied.  The two paths to memory work side by side: the
+// copy engine's cost per row bounds the copies (all 32 rows by copies measured slower than the
+// register gathers alone), the registers bound the loads in flight.  The matrix stream's columns
+// run two batches ahead (a batch's copies are issued an iteration before it), its values one.
+// Every wait on a slot's mbarrier is bounded: a warp whose copies do not land sets err, waits
+// (bounded) for its copies in flight and stops.
 // ---------------------------------------------------------------------------------------------
-template <int NG> struct RB4Cfg {
+template <int NG, int ET> struct RB4Cfg {
     static constexpr int KH = 4;
     static constexpr int M = kWarp / NG * KH;                      // 64, 32 or 16 probe columns
-    static constexpr uint32_t slot = kWarp * M * sizeof(float);   // one batch of gathered rows
-    static constexpr int warps = 12;                              // 168 registers a thread; two slots a warp
+    static constexpr int RG = (kWarp - ET) / NG;                   // register-gathered entries per group
+    static constexpr uint32_t slot = ET * M * sizeof(float);      // the copied rows of one batch
+    static constexpr int warps = 12;                               // up to 168 registers a thread
     static constexpr int threads = warps * kWarp;
-    static constexpr size_t smem =
-        128 + (size_t)warps * (2 * slot + 2 * kWarp * sizeof(float4) + 2 * sizeof(uint64_t));
+    static constexpr size_t per_warp =
+        2 * slot + 2 * kWarp * sizeof(float4) + kWarp * sizeof(int) + 2 * sizeof(uint64_t);
+    static constexpr size_t smem = 128 + (size_t)warps * per_warp;
+    static_assert(ET > 0 && ET <= kWarp && ET % 4 == 0 && ET % NG == 0,
+                  "copied entries: whole gather4 copies and whole runs of every group");
 };
 
 // Four rows r0..r3, columns x .. x + box - 1 of the tensor map's 2-D tensor, to dst (four boxes
@@ -1366,35 +1372,36 @@ __device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *tm, in
         : "memory");
 }
 
-// One 32-entry batch of a row block: the lane's entry (column, 8 values) and where the batch sits.
+// One 32-entry batch of a row block: the lane's entry's column and where the batch sits.
 struct RB4Batch {
-    int cj;
-    float4 v0, v1;
-    int cnt;                   // entries of the batch (the rest are zero entries on the block's first row)
-    int b;                     // row block
-    int t;                     // tile
-    bool valid, bend, tend;    // a batch at all / the block's last batch / the tile's last batch
+    int cj;                    // column (past the batch's entries: the block's first row)
+    int eb;                    // the batch's first entry
+    int b, t;                  // row block, tile
+    int cnt;                   // entries of the batch; 0: no batch
+    bool bend, tend;           // the block's / the tile's last batch
 };
 
-template <int NG, bool HAS_Y>
-__global__ void __launch_bounds__(RB4Cfg<NG>::threads, 1)
+template <int NG, int ET, bool HAS_Y>
+__global__ void __launch_bounds__(RB4Cfg<NG, ET>::threads, 1)
 k_spmm_rb4(const __grid_constant__ CUtensorMap tmz, const int32_t *__restrict__ bptr,
            const int32_t *__restrict__ ucol, const float *__restrict__ uval, int64_t n, const float *__restrict__ py,
            const float *__restrict__ pz, float *__restrict__ qy, float *__restrict__ qz, double *__restrict__ part,
            int pstride, RBWork *__restrict__ work, int tile_blocks, int ntiles, double *__restrict__ tpart,
            int *__restrict__ seg_cnt, int seg_tiles, int *__restrict__ err)
 {
-    using C = RB4Cfg<NG>;
-    constexpr int KH = C::KH, M = C::M, W = C::warps, LG = kWarp / NG;
+    using C = RB4Cfg<NG, ET>;
+    constexpr int KH = C::KH, M = C::M, W = C::warps, LG = kWarp / NG, RG = C::RG, EC = ET / NG;
     extern __shared__ __align__(16) unsigned char rb4_sh[];
     unsigned char *base = rb4_sh + ((128u - (smem_addr(rb4_sh) & 127u)) & 127u);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int grp = lane / LG, gl = lane % LG;
     float *ring = reinterpret_cast<float *>(base + (size_t)wid * 2 * C::slot);   // this warp's two slots
-    float4 *s_val = reinterpret_cast<float4 *>(base + (size_t)W * 2 * C::slot) + wid * 2 * kWarp;
-    uint64_t *bar =
-        reinterpret_cast<uint64_t *>(base + (size_t)W * 2 * C::slot + (size_t)W * 2 * kWarp * sizeof(float4)) +
-        wid * 2;
+    unsigned char *tail = base + (size_t)W * 2 * C::slot;
+    float4 *s_val = reinterpret_cast<float4 *>(tail) + wid * 2 * kWarp;
+    tail += (size_t)W * 2 * kWarp * sizeof(float4);
+    int *s_col = reinterpret_cast<int *>(tail) + wid * kWarp;
+    tail += (size_t)W * kWarp * sizeof(int);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tail) + wid * 2;
     if (lane == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -1402,6 +1409,7 @@ k_spmm_rb4(const __grid_constant__ CUtensorMap tmz, const int32_t *__restrict__ 
     }
     __syncwarp();
     const int64_t nblk = (n + kRB - 1) / kRB;
+    const float4 *uval4 = reinterpret_cast<const float4 *>(uval);
 
     // The cursor (warp-uniform): the next batch to read from the matrix stream.  The tile after the
     // cursor's is taken from the counter on entering a tile, and the end of the block after the
@@ -1438,25 +1446,20 @@ k_spmm_rb4(const __grid_constant__ CUtensorMap tmz, const int32_t *__restrict__ 
             }
         }
     };
-    // the batch at the cursor, then the cursor moves on; lanes past the block's last entry take a
-    // zero entry on the block's first row (evict-first loads: the matrix is read once per launch)
+    // the batch at the cursor (its columns: evict-first loads, the matrix is read once per
+    // launch), then the cursor moves on
     auto take = [&]() {
         RB4Batch q;
-        q.valid = cval;
         q.cj = 0;
-        q.v0 = make_float4(0.f, 0.f, 0.f, 0.f);
-        q.v1 = q.v0;
-        q.cnt = 0;
+        q.eb = 0;
         q.b = 0;
         q.t = 0;
+        q.cnt = 0;
         q.bend = q.tend = false;
         if (!cval) return q;
         q.cj = (int)(cb * kRB);
-        if (ceb + lane < ce1) {
-            q.cj = __ldcs(ucol + ceb + lane);
-            q.v0 = __ldcs(reinterpret_cast<const float4 *>(uval) + (int64_t)(ceb + lane) * 2);
-            q.v1 = __ldcs(reinterpret_cast<const float4 *>(uval) + (int64_t)(ceb + lane) * 2 + 1);
-        }
+        if (ceb + lane < ce1) q.cj = __ldcs(ucol + ceb + lane);
+        q.eb = ceb;
         q.cnt = min(kWarp, ce1 - ceb);
         q.b = (int)cb;
         q.t = (int)ct;
@@ -1465,14 +1468,24 @@ k_spmm_rb4(const __grid_constant__ CUtensorMap tmz, const int32_t *__restrict__ 
         advance();
         return q;
     };
-    // the gathers of a batch's 32 rows into slot s
+    // the values of the lane's entry of a batch (zeros past its entries)
+    auto values = [&](const RB4Batch &q, float4 &v0, float4 &v1) {
+        v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        v1 = v0;
+        if (lane < q.cnt) {
+            v0 = __ldcs(uval4 + (int64_t)(q.eb + lane) * 2);
+            v1 = __ldcs(uval4 + (int64_t)(q.eb + lane) * 2 + 1);
+        }
+    };
+    // the copies of a batch's first ET rows into slot s
     auto issue = [&](const RB4Batch &q, int s) {
         const int r1 = __shfl_down_sync(0xffffffffu, q.cj, 1);
         const int r2 = __shfl_down_sync(0xffffffffu, q.cj, 2);
         const int r3 = __shfl_down_sync(0xffffffffu, q.cj, 3);
         if (lane == 0) mbar_expect_tx(&bar[s], C::slot);
         __syncwarp();
-        if ((lane & 3) == 0) tma_gather4(ring + (size_t)s * kWarp * M + lane * M, &tmz, 0, q.cj, r1, r2, r3, &bar[s]);
+        if ((lane & 3) == 0 && lane < ET)
+            tma_gather4(ring + (size_t)s * ET * M + lane * M, &tmz, 0, q.cj, r1, r2, r3, &bar[s]);
     };
 
     ct = grab();
@@ -1480,8 +1493,10 @@ k_spmm_rb4(const __grid_constant__ CUtensorMap tmz, const int32_t *__restrict__ 
     if (cval) enter();
     RB4Batch cur = take();
     RB4Batch nxt = take();
+    float4 v0, v1;
+    values(cur, v0, v1);
     float yj = 0.0f;
-    if (cur.valid) {
+    if (cur.cnt) {
         issue(cur, 0);
         if (HAS_Y) yj = py[cur.cj];
     }
@@ -1495,62 +1510,85 @@ k_spmm_rb4(const __grid_constant__ CUtensorMap tmz, const int32_t *__restrict__ 
     for (int rp = 0; rp < kRB / 2; ++rp)
 #pragma unroll
         for (int k = 0; k < KH; ++k) acc[rp][k] = make_float2(0.0f, 0.0f);
+    // acc[rp][.] += (values of rows 2 rp, 2 rp + 1 of staged entry e) x (the lane's KH columns of its row)
+    auto fma_entry = [&](int e, const float (&pv)[KH]) {
+        const float4 a0 = s_val[2 * e], a1 = s_val[2 * e + 1];
+        const float2 vp[kRB / 2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                                    make_float2(a1.z, a1.w)};
+#pragma unroll
+        for (int kk = 0; kk < KH; ++kk) {
+            const float2 pk = make_float2(pv[kk], pv[kk]);
+#pragma unroll
+            for (int rp = 0; rp < kRB / 2; ++rp) acc[rp][kk] = __ffma2_rn(vp[rp], pk, acc[rp][kk]);
+        }
+    };
     uint32_t k = 0;
     bool failed = false;
-    while (cur.valid) {
-        // batch k + 1's gathers go out (its rows were read an iteration ago) and its y values are
-        // fetched; batch k + 2 is read from the matrix stream
-        float yj_n = 0.0f;
-        if (nxt.valid) {
-            issue(nxt, (k + 1) & 1);
-            if (HAS_Y) yj_n = py[nxt.cj];
-        }
-        const RB4Batch nn = take();
+    while (cur.cnt) {
+        // batch k + 1's copies go out (its columns were read an iteration ago)
+        if (nxt.cnt) issue(nxt, (k + 1) & 1);
+        // stage batch k's columns and values
+        s_col[lane] = cur.cj;
+        s_val[lane * 2] = v0;
+        s_val[lane * 2 + 1] = v1;
         if (HAS_Y) {
-            ay[0] = fmaf(cur.v0.x, yj, ay[0]); ay[1] = fmaf(cur.v0.y, yj, ay[1]);
-            ay[2] = fmaf(cur.v0.z, yj, ay[2]); ay[3] = fmaf(cur.v0.w, yj, ay[3]);
-            ay[4] = fmaf(cur.v1.x, yj, ay[4]); ay[5] = fmaf(cur.v1.y, yj, ay[5]);
-            ay[6] = fmaf(cur.v1.z, yj, ay[6]); ay[7] = fmaf(cur.v1.w, yj, ay[7]);
+            ay[0] = fmaf(v0.x, yj, ay[0]); ay[1] = fmaf(v0.y, yj, ay[1]);
+            ay[2] = fmaf(v0.z, yj, ay[2]); ay[3] = fmaf(v0.w, yj, ay[3]);
+            ay[4] = fmaf(v1.x, yj, ay[4]); ay[5] = fmaf(v1.y, yj, ay[5]);
+            ay[6] = fmaf(v1.z, yj, ay[6]); ay[7] = fmaf(v1.w, yj, ay[7]);
         }
-        s_val[lane * 2] = cur.v0;
-        s_val[lane * 2 + 1] = cur.v1;
         __syncwarp();
+        // group g's entries NG u + g: u < EC from the copies, the RG after them gathered into
+        // registers now; entries past cnt are skipped (zero values)
+        const int nrun = (cur.cnt + NG - 1) / NG;
+        float pv[RG > 0 ? RG : 1][KH];
+#pragma unroll
+        for (int d = 0; d < RG; ++d) {
+            const int e = ET + NG * d + grp;
+            if (e < cur.cnt) {
+                load_k<float, KH>(pz + (int64_t)s_col[e] * M + gl * KH, pv[d]);
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < KH; ++kk) pv[d][kk] = 0.0f;
+            }
+        }
+        // batch k + 1's values and y values, batch k + 2's columns
+        float4 v0n, v1n;
+        values(nxt, v0n, v1n);
+        const float yj_n = HAS_Y && nxt.cnt ? py[nxt.cj] : 0.0f;
+        const RB4Batch nn = take();
         const int s = (int)(k & 1);
         if (!mbar_wait_bounded(&bar[s], (k >> 1) & 1)) {
             failed = true;
             break;
         }
-        // group g takes entries NG u + g, u < ceil(cnt / NG), in order (the staged entries past cnt
-        // are zeros on a valid row)
-        const float *rs = ring + (size_t)s * kWarp * M + gl * KH;
-        const int nrun = (cur.cnt + NG - 1) / NG;
+        const float *rs = ring + (size_t)s * ET * M + gl * KH;
 #pragma unroll 4
-        for (int u = 0; u < nrun; ++u) {
-            const int e = NG * u + grp;
-            const float4 p4 = *reinterpret_cast<const float4 *>(rs + e * M);
-            const float4 a0 = s_val[2 * e], a1 = s_val[2 * e + 1];
-            const float2 vp[kRB / 2] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
-                                        make_float2(a1.z, a1.w)};
-            const float pv[KH] = {p4.x, p4.y, p4.z, p4.w};
-#pragma unroll
-            for (int kk = 0; kk < KH; ++kk) {
-                const float2 pk = make_float2(pv[kk], pv[kk]);
-#pragma unroll
-                for (int rp = 0; rp < kRB / 2; ++rp) acc[rp][kk] = __ffma2_rn(vp[rp], pk, acc[rp][kk]);
+        for (int u = 0; u < EC; ++u) {
+            if (u < nrun) {
+                const float4 p4 = *reinterpret_cast<const float4 *>(rs + (NG * u + grp) * M);
+                const float pc[KH] = {p4.x, p4.y, p4.z, p4.w};
+                fma_entry(NG * u + grp, pc);
             }
         }
+#pragma unroll
+        for (int d = 0; d < RG; ++d)
+            if (EC + d < nrun) fma_entry(ET + NG * d + grp, pv[d]);
         // the slot's reads are ordered before the copies that will refill it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (cur.bend) rb_block_end<KH, NG, HAS_Y>(acc, ay, dz, dy, (int64_t)cur.b, n, py, pz, qy, qz, lane);
         if (cur.tend) {
-            rb_tile_end<KH, NG, HAS_Y>(dz, dy, (unsigned long long)cur.t, part, pstride, tpart, seg_cnt, seg_tiles, ntiles, lane);
+            rb_tile_end<KH, NG, HAS_Y>(dz, dy, (unsigned long long)cur.t, part, pstride, tpart, seg_cnt, seg_tiles,
+                                       ntiles, lane);
 #pragma unroll
             for (int kk = 0; kk < KH; ++kk) dz[kk] = Acc32();
             dy = Acc32();
         }
         cur = nxt;
         nxt = nn;
+        v0 = v0n;
+        v1 = v1n;
         yj = yj_n;
         ++k;
     }
@@ -1558,7 +1596,7 @@ k_spmm_rb4(const __grid_constant__ CUtensorMap tmz, const int32_t *__restrict__ 
         if (lane == 0) atomicExch(err, 1);
         // the copies this warp still has in flight must land before the CTA's shared memory goes
         mbar_wait_bounded(&bar[k & 1], (k >> 1) & 1);
-        if (nxt.valid) mbar_wait_bounded(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1);
+        if (nxt.cnt) mbar_wait_bounded(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1);
     }
     // every warp of this CTA has made its last grab: count the CTA out, and let the last one reset
     // the counter for the next launch
@@ -1649,17 +1687,18 @@ static bool rb4_map(CUtensorMap *tm, const float *p, int64_t n, int M)
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The gather-copy form of the RB8 SpMM (M = 16, 32, 64); *done = false when it cannot run here
-// (no tensor-map encoder), and the register-gather form takes the launch.
-template <int NG>
+// The gather-copy form of the RB8 SpMM (M = 16, 32, 64; ET of every 32 gathered rows by copies);
+// *done = false when it cannot run here (no tensor-map encoder, or an ET without a kernel), and
+// the register-gather form takes the launch.
+template <int NG, int ET>
 gp2s_status launch_rb4(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts, int *err,
                        bool *done)
 {
-    using C = RB4Cfg<NG>;
+    using C = RB4Cfg<NG, ET>;
     *done = false;
     CUtensorMap tm;
     if (!err || !rb4_map(&tm, (const float *)B.pz, c->A.n, C::M)) return GP2S_OK;
-    auto kern = k_spmm_rb4<NG, true>;
+    auto kern = k_spmm_rb4<NG, ET, true>;
     GP2S_TRY(smem_attr(c, (const void *)kern, C::smem));
     const RBTiles tl = rb_tiles(ceil_div(c->A.n, kRB), nb);
     GP2S_TRY(ensure(c, c->rb_tpart, sizeof(double) * (size_t)tl.ntiles * (C::M + 1)));
@@ -1674,6 +1713,19 @@ gp2s_status launch_rb4(gp2s_ctx *c, const CGBuffers &B, double *part, int pstrid
     c->spmm_seg_tiles = std::max(c->spmm_seg_tiles, tl.seg_tiles);
     *done = true;
     return GP2S_OK;
+}
+
+template <int NG>
+gp2s_status launch_rb4_et(gp2s_ctx *c, const CGBuffers &B, double *part, int pstride, int nb, int *nparts, int *err,
+                          int et, bool *done)
+{
+    *done = false;
+    // half or all of every batch's rows by copies (8 and 24 measured no faster than 16)
+    switch (et) {
+    case 16: return launch_rb4<NG, 16>(c, B, part, pstride, nb, nparts, err, done);
+    case 32: return launch_rb4<NG, 32>(c, B, part, pstride, nb, nparts, err, done);
+    default: return GP2S_OK;
+    }
 }
 
 // ---------------------------------------------------------------------------------------------

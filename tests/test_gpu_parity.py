@@ -370,23 +370,24 @@ def test_graph_replay_equals_eager_launches(gp, monkeypatch):
 
 @pytest.mark.parametrize("probes,n", [(16, 40_003), (32, 160_003), (64, 40_003)])
 def test_spmm_gather_copies_equal_register_gathers(gp, monkeypatch, probes, n):
-    """The RB8 SpMM's two forms (the gathered probe rows loaded into registers, the default; or
-    brought into shared memory by tensor-map gather copies) run the same FMAs in the same order and
-    reduce every tile's dots in tile order: a whole mixed-precision evaluation of clustered 3-D
-    points (thousands of 8-row blocks, a ragged last block; at 160,003 points the multi-segment dot
-    reduction) gives the same LML, gradient and iteration counts bit for bit in both."""
+    """The RB8 SpMM's forms (the gathered probe rows all loaded into registers; or 16 or all 32 of
+    every batch's rows brought into shared memory by tensor-map gather copies) run the same FMAs in
+    the same order and reduce every tile's dots in tile order: a whole mixed-precision evaluation
+    of clustered 3-D points (thousands of 8-row blocks, a ragged last block; at 160,003 points the
+    multi-segment dot reduction) gives the same LML, gradient and iteration counts bit for bit."""
     w = W.clusters_3d(3, n=n)
     h = gp.Hyper(**w["hyper"])
     X = torch.tensor(w["X"], device="cuda")
     y = torch.tensor(w["y"], device="cuda")
     opts = gp.default_opts(probes=probes, lanczos_steps=30, seed=5)
     out = []
-    for tma in ("0", "1"):
+    for tma in ("0", "16", "32"):
         monkeypatch.setenv("GP2S_SPMM_TMA", tma)
         out.append(gp.Context(0).lml_grad(X, y, h, opts))
-    (l0, g0, i0), (l1, g1, i1) = out
-    assert l1 == l0 and np.array_equal(g1, g0)
-    assert (i1["iters_y"], i1["iters_probes"]) == (i0["iters_y"], i0["iters_probes"])
+    l0, g0, i0 = out[0]
+    for l1, g1, i1 in out[1:]:
+        assert l1 == l0 and np.array_equal(g1, g0)
+        assert (i1["iters_y"], i1["iters_probes"]) == (i0["iters_y"], i0["iters_probes"])
     if n > 100_000:
         assert i0["spmm_seg_tiles"] > 1
 
