@@ -406,7 +406,9 @@ gp2s_status gp2s_mcmc(gp2s_ctx *ctx, int64_t n, const double *X, const double *y
  *   out_dev: DEVICE pointer to 3 doubles receiving {LML, y^T A^{-1} y, log|A|}; NaN if a Cholesky
  *   pivot is not positive.
  *   cuda_stream: the stream all work is issued on (NULL = legacy default stream).  It must belong
- *   to the calling thread's current device: a stream of another device returns GP2S_EINVAL.
+ *   to the calling thread's current device: a stream of another device returns GP2S_EINVAL when
+ *   it is not being captured.  While it is being captured this is not checked (the runtime does
+ *   not permit asking a capturing stream for its device), so the caller answers for it.
  * The call is asynchronous: it returns after queueing the work on cuda_stream.  The first call on
  * each device looks up the scratch array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture begins.  Every call on a device shares

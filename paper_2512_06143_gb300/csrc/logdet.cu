@@ -662,14 +662,23 @@ extern "C" gp2s_status gp2s_lml_exact_noalloc(int64_t n, const double *X_dev, co
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     // the scratch address is per device: a stream of another device would get this device's
     // address, so such a stream is refused (the legacy and per-thread default streams follow the
-    // current device)
+    // current device).  The stream's device is not asked for while the stream is being captured,
+    // where that query invalidates the capture: a capture records on the stream's own device, and
+    // the caller answers for the device being current.
     if (s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread) {
-        int cur = 0, sdev = 0;
-        if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
             cudaGetLastError();
             return GP2S_ECUDA;
         }
-        if (sdev != cur) return GP2S_EINVAL;
+        if (cs == cudaStreamCaptureStatusNone) {
+            int cur = 0, sdev = 0;
+            if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+                cudaGetLastError();
+                return GP2S_ECUDA;
+            }
+            if (sdev != cur) return GP2S_EINVAL;
+        }
     }
     double *base = nullptr;
     gp2s_status st = noalloc_scratch(&base);

@@ -86,3 +86,47 @@ def test_noalloc_rejects_sizes_beyond_the_limit(gp):
     st, out = _noalloc(gp, X, y, h)
     assert st == gp.EINVAL
     assert np.all(np.isnan(out))      # nothing was written
+
+
+def test_noalloc_inside_a_captured_cuda_graph(gp):
+    """What the entry point is for: it is queued while a stream is being captured and allocates
+    nothing.  One eager warm-up call, then the call captured with torch.cuda.graph on a side stream;
+    two replays with new y contents written in place give the eager results for those y bit for bit,
+    and neither torch's allocated bytes nor the device's free bytes change across the replays."""
+    w = W.random_small(404, 300, 2, L=3, sigma2=1e-3, r=0.15)
+    h = gp.Hyper(**w["hyper"])
+    hc = h.c()
+    X = torch.tensor(w["X"], dtype=torch.float64, device="cuda")
+    y = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
+    n = X.shape[0]
+    f = gp.load().gp2s_lml_exact_noalloc
+    rng = np.random.default_rng(5)
+    ys = [torch.tensor(w["y"] + 0.1 * rng.standard_normal(n), dtype=torch.float64, device="cuda") for _ in range(2)]
+    # eager results for the two right-hand sides
+    ref = []
+    out_e = torch.empty(3, dtype=torch.float64, device="cuda")
+    for yk in ys:
+        y.copy_(yk)
+        st = f(n, X.data_ptr(), y.data_ptr(), ctypes.byref(hc), out_e.data_ptr(),
+               torch.cuda.current_stream().cuda_stream)
+        assert st == gp.OK
+        ref.append(out_e.cpu().numpy().copy())
+    # capture on a side stream (torch's default global capture mode: any unsafe call fails it)
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        st = f(n, X.data_ptr(), y.data_ptr(), ctypes.byref(hc), out.data_ptr(),
+               torch.cuda.current_stream().cuda_stream)
+    assert st == gp.OK
+    torch.cuda.synchronize()
+    alloc0 = torch.cuda.memory_allocated()
+    free0 = torch.cuda.mem_get_info()[0]
+    for yk, rk in zip(ys, ref):
+        y.copy_(yk)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), rk)
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0
