@@ -49,8 +49,6 @@ __global__ void k_probe_bits(const int32_t *__restrict__ perm, int64_t n, int m,
     }
 }
 
-__device__ __forceinline__ float flip(float x, uint32_t bit) { return __int_as_float(__float_as_int(x) ^ (int)(bit << 31)); }
-
 __device__ __forceinline__ double warp_sum_adj(double v)
 {
 #pragma unroll

@@ -177,7 +177,7 @@ k_spmm(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col, cons
     using Acc = typename AccOf<T>::type;
     // K columns per lane; with M < 32 (or not a multiple of 32) the last lanes hold none
     constexpr int K = (M + 31) / 32;
-    const bool lon = (threadIdx.x & 31) * K < M;
+    const bool lon = (int)(threadIdx.x & 31) * K < M;
     __shared__ Staged<T> stage[kSpmmWarps][kWarp];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t r_begin = row_split[blockIdx.x];
