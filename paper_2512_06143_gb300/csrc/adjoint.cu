@@ -13,9 +13,11 @@
 // derivatives of Eq. 7.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "gp2s_kernel_math.cuh"
+
 #include "gp2s_internal.cuh"
 
 namespace gp2s {
@@ -46,6 +48,17 @@ __global__ void k_probe_bits(const int32_t *__restrict__ perm, int64_t n, int m,
             word |= (uint32_t)(sm64_first(key) >> 63) << b;
         }
         bits[e] = word;
+    }
+}
+
+// The same signs as FP32 +-1, row-major n x m (for the FP32 gradient's vectorised probe sums).
+__global__ void k_probe_signs(const uint32_t *__restrict__ bits, int64_t n, int m, float *__restrict__ zf)
+{
+    const int W = (m + 31) / 32;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / m;
+        const int s = (int)(e - i * m);
+        zf[e] = (bits[i * W + s / 32] >> (s % 32)) & 1u ? -1.0f : 1.0f;
     }
 }
 
@@ -83,6 +96,27 @@ __device__ __forceinline__ T probe_cross(const T *__restrict__ xa, const uint32_
     return acc;
 }
 
+// The same sum in FP32 with four probes per step: row i's solutions and signs staged in shared
+// memory (ui, zi), row j's read as float4 from U and the +-1 signs zf, two packed FP32x2
+// accumulators (multiplying by +-1 is exact, so only the order of the additions differs).
+template <int M>
+__device__ __forceinline__ float probe_cross4(const float4 *__restrict__ ui, const float4 *__restrict__ zi,
+                                              const float *__restrict__ uj, const float *__restrict__ zj)
+{
+    float2 s0 = make_float2(0.0f, 0.0f), s1 = s0;
+    const float4 *uj4 = reinterpret_cast<const float4 *>(uj);
+    const float4 *zj4 = reinterpret_cast<const float4 *>(zj);
+#pragma unroll 4
+    for (int k = 0; k < M / 4; ++k) {
+        const float4 a = ui[k], za = zi[k], b = __ldg(uj4 + k), zb = __ldg(zj4 + k);
+        s0 = __ffma2_rn(make_float2(a.x, a.y), make_float2(zb.x, zb.y), s0);
+        s1 = __ffma2_rn(make_float2(a.z, a.w), make_float2(zb.z, zb.w), s1);
+        s0 = __ffma2_rn(make_float2(b.x, b.y), make_float2(za.x, za.y), s0);
+        s1 = __ffma2_rn(make_float2(b.z, b.w), make_float2(za.z, za.w), s1);
+    }
+    return (s0.x + s0.y) + (s1.x + s1.y);
+}
+
 struct AdjArgs {
     const int32_t *rowptr, *col;
     const float4 *Xhi, *Xlo;
@@ -91,6 +125,7 @@ struct AdjArgs {
     const double *s64;         // n
     const void *U;             // n x m probe solutions of Ah (FP32 or FP64)
     const uint32_t *zbits;     // n x (m/32)
+    const float *zf;           // n x m signs as +-1 (FP32 form, m a multiple of 4)
     int64_t n;
     int m;
     float *H;                  // n x L
@@ -112,15 +147,27 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
     const bool ff = kp.family == 2;
     const float lc = ff ? (float)kp.ell[0] : 1.0f;
     const float inv2lc2 = 0.5f / (lc * lc);
+    // FP32 form: row i's probe solutions and signs in shared memory for the vectorised sums
+    constexpr bool V4 = std::is_same<T, float>::value && M > 0 && M % 4 == 0 && M <= 128;
+    __shared__ float4 s_uz[V4 ? 8 : 1][2][V4 ? M / 4 : 1];
+    const int wl = (int)(threadIdx.x >> 5);
     double gr = 0.0, gs = 0.0, glc = 0.0, gw0 = 0.0;
     for (int64_t i = w0; i < g.n; i += nw) {
         const float4 hi_i = g.Xhi[i], lo_i = g.Xlo[i];
         const float ai = (float)g.a[i];
         const float si = (float)g.s64[i];
         const T *Ui = U + i * M;
+        if constexpr (V4) {
+            __syncwarp();
+            for (int k = lane; k < M / 4; k += 32) {
+                s_uz[wl][0][k] = reinterpret_cast<const float4 *>(Ui)[k];
+                s_uz[wl][1][k] = reinterpret_cast<const float4 *>(g.zf + i * M)[k];
+            }
+            __syncwarp();
+        }
         uint32_t zi[WZ];
 #pragma unroll
-        for (int w = 0; w < WZ; ++w) zi[w] = M > 0 ? g.zbits[i * WZ + w] : 0u;
+        for (int w = 0; w < WZ; ++w) zi[w] = M > 0 && !V4 ? g.zbits[i * WZ + w] : 0u;
         float Hacc[kMaxBumps];
         for (int l = 0; l < L; ++l) Hacc[l] = 0.0f;
         float grr = 0.0f, gss = 0.0f, glcr = 0.0f, gw0r = 0.0f;
@@ -130,7 +177,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs g, KernelParams kp)
             const float aj = (float)g.a[j];
             const float sj = (float)g.s64[j];
             float tr = 0.0f;
-            if (M > 0) {
+            if constexpr (V4) {
+                tr = probe_cross4<M>(s_uz[wl][0], s_uz[wl][1], reinterpret_cast<const float *>(U) + (int64_t)j * M,
+                                     g.zf + (int64_t)j * M);
+            } else if (M > 0) {
                 uint32_t zj[WZ];
 #pragma unroll
                 for (int w = 0; w < WZ; ++w) zj[w] = g.zbits[(int64_t)j * WZ + w];
@@ -531,6 +581,12 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
         unsigned gb = (unsigned)std::min<int64_t>(ceil_div(n * W, 256), 152 * 8);
         k_probe_bits<<<gb, 256, 0, c->stream>>>(c->perm.as<int32_t>(), n, m, A.opts.seed, c->Z.as<uint32_t>());
         GP2S_LAUNCH(c);
+        if (mixed && m % 4 == 0) {
+            GP2S_TRY(ensure(c, c->Zf, sizeof(float) * (size_t)n * m + 64));
+            const unsigned gs = (unsigned)std::min<int64_t>(ceil_div(n * m, 256), 152 * 16);
+            k_probe_signs<<<gs, 256, 0, c->stream>>>(c->Z.as<uint32_t>(), n, m, c->Zf.as<float>());
+            GP2S_LAUNCH(c);
+        }
     }
     AdjArgs g;
     std::memset(&g, 0, sizeof(g));
@@ -543,6 +599,7 @@ gp2s_status adjoint_gradient(gp2s_ctx *c, int m, double *grad_host)
     g.s64 = c->s64.as<double>();
     g.U = c->vec.p;          // probe-group x (first block of the Krylov vectors)
     g.zbits = c->Z.as<uint32_t>();
+    g.zf = mixed && m > 0 && m % 4 == 0 ? c->Zf.as<float>() : nullptr;
     g.n = n;
     g.m = m;
     g.H = c->H.as<float>();

@@ -310,7 +310,7 @@ void gp2s_destroy(gp2s_ctx *c)
                       &c->scan_tmp, &c->scan_tmp2, &c->cell_start, &c->cell_flag, &c->items, &c->item_cnt,
                       &c->B64, &c->B32, &c->D64, &c->s64, &c->s32, &c->rowcnt, &c->rowptr, &c->col,
                       &c->val32, &c->val64, &c->counters, &c->vec, &c->vec64, &c->partials, &c->scal,
-                      &c->Z, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
+                      &c->Z, &c->Zf, &c->rec, &c->rsplit, &c->dense, &c->H, &c->gpart,
                       &c->rb_cnt, &c->rb_ptr, &c->rb_col, &c->rb_val, &c->rb_tpart, &c->rb_seg,
                       &c->bj_Minv, &c->bj_ld, &c->bj_Minv_y, &c->post_X, &c->post_B, &c->post_cnt,
                       &c->post_part, &c->mr_vec, &c->mc_X, &c->mc_y, &c->wc_lam, &c->wc_sig, &c->ff_mask,

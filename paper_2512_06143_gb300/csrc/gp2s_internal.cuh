@@ -110,7 +110,7 @@ struct gp2s_ctx {
     // CSR
     gp2s::DevBuf rowcnt, rowptr, col, val32, val64, counters;
     // Krylov
-    gp2s::DevBuf vec, vec64, partials, scal, Z, rec, rsplit;
+    gp2s::DevBuf vec, vec64, partials, scal, Z, Zf, rec, rsplit;   // Zf: probe signs as FP32 +-1 (gradient)
     // row-block (8 rows) copy of the FP32 matrix for the multi-RHS SpMM
     gp2s::DevBuf rb_cnt, rb_ptr, rb_col, rb_val, rb_tpart, rb_seg;
     bool rb_valid = false;
